@@ -1,0 +1,184 @@
+"""CPU oracle for the Da Vinci Code MCTS of arXiv 2403.10720 (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  The plain single-threaded C statement of the method
+lives in dvc_oracle.c; this module only loads it and marshals arguments.  Only
+tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import it.
+
+States cross this wrapper as 32-byte records in the boundary format (see the
+comment above pack() in dvc_oracle.c), as numpy uint8 arrays of shape (n, 32).
+
+Pin status per function:
+  philox4x32_10 ..... pinned (published known-answer vectors)
+  ln ................ pinned (libm within 2 ulp)
+  init_states ....... pinned (rule invariants, deal sizes, history bounds)
+  legal_count ....... pinned (88 root guesses of Sec. III-A, closed form I7)
+  rollout / trace ... pinned (invariants, closed-form 1/k endgame, exact
+                      win probabilities of tiny endgames by enumeration)
+  det_count ......... pinned (brute-force enumeration of consistent deals)
+  determinize ....... pinned (chi-square against uniform over those deals)
+  mcts .............. pinned (UCB1 forced-win toy sequence, count invariants)
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [
+        ("nplayers", ctypes.c_int32),
+        ("ntiles", ctypes.c_int32),
+        ("deal", ctypes.c_int32),
+        ("max_predraw", ctypes.c_int32),
+        ("max_revealed", ctypes.c_int32),
+        ("cont_thr", ctypes.c_uint32),
+        ("c_uct", ctypes.c_double),
+        ("d_max", ctypes.c_int32),
+        ("playouts", ctypes.c_int32),
+    ]
+
+
+@dataclass
+class OracleConfig:
+    nplayers: int = 2
+    ntiles: int = 24
+    deal: int = 4
+    max_predraw: int = 0
+    max_revealed: int = 5
+    cont_thr: int = 1 << 31
+    c_uct: float = 1.4142135623730951
+    d_max: int = 8
+    playouts: int = 1
+
+    def c(self) -> _Cfg:
+        return _Cfg(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
+                    self.cont_thr, self.c_uct, self.d_max, self.playouts)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        cfgp = ctypes.POINTER(_Cfg)
+        L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.or_philox4x32_10.restype = None
+        L.or_ln.argtypes = [ctypes.c_double]
+        L.or_ln.restype = ctypes.c_double
+        L.or_init_states.argtypes = [cfgp, ctypes.c_uint64, ctypes.c_int, u8p]
+        L.or_init_states.restype = ctypes.c_int
+        L.or_legal_count.argtypes = [u8p]
+        L.or_legal_count.restype = ctypes.c_int
+        L.or_det_count.argtypes = [u8p, ctypes.c_int]
+        L.or_det_count.restype = ctypes.c_uint64
+        L.or_determinize.argtypes = [cfgp, u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_uint32, u8p]
+        L.or_determinize.restype = ctypes.c_int
+        L.or_rollout.argtypes = [cfgp, u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                 i32p, i64p]
+        L.or_rollout.restype = ctypes.c_int
+        L.or_playout_trace.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint32, u8p, ctypes.c_int]
+        L.or_playout_trace.restype = ctypes.c_int
+        L.or_mcts.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i32p,
+                              ctypes.POINTER(ctypes.c_int), i32p]
+        L.or_mcts.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _u8(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def _i32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _state(s):
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.uint8).reshape(32))
+    return s
+
+
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def ln(x: float) -> float:
+    return lib().or_ln(float(x))
+
+
+def init_states(cfg: OracleConfig, seed: int, n: int) -> np.ndarray:
+    out = np.zeros((n, 32), dtype=np.uint8)
+    c = cfg.c()
+    rc = lib().or_init_states(ctypes.byref(c), seed, n, _u8(out))
+    if rc:
+        raise ValueError(f"or_init_states rc={rc}")
+    return out
+
+
+def legal_count(state) -> int:
+    s = _state(state)
+    return lib().or_legal_count(_u8(s))
+
+
+def det_count(state, observer: int = -1) -> int:
+    s = _state(state)
+    return int(lib().or_det_count(_u8(s), observer))
+
+
+def determinize(cfg: OracleConfig, state, observer: int, seed: int, tree: int, it: int) -> np.ndarray:
+    s = _state(state)
+    out = np.zeros(32, dtype=np.uint8)
+    c = cfg.c()
+    rc = lib().or_determinize(ctypes.byref(c), _u8(s), observer, seed, tree, it, _u8(out))
+    if rc:
+        raise ValueError(f"or_determinize rc={rc}")
+    return out
+
+
+def rollout(cfg: OracleConfig, leaf, playouts: int, seed: int, tree: int, leaf_id: int):
+    """Returns (wins per player (4,), RNG words consumed)."""
+    s = _state(leaf)
+    wins = np.zeros(4, dtype=np.int32)
+    words = ctypes.c_int64(0)
+    c = cfg.c()
+    rc = lib().or_rollout(ctypes.byref(c), _u8(s), playouts, seed, tree, leaf_id, _i32(wins), ctypes.byref(words))
+    if rc:
+        raise ValueError(f"or_rollout rc={rc}")
+    return wins, int(words.value)
+
+
+def playout_trace(cfg: OracleConfig, leaf, seed: int, tree: int, j: int, leaf_id: int, maxlen: int = 256):
+    s = _state(leaf)
+    out = np.zeros((maxlen, 32), dtype=np.uint8)
+    c = cfg.c()
+    n = lib().or_playout_trace(ctypes.byref(c), _u8(s), seed, tree, j, leaf_id, _u8(out), maxlen)
+    return out[:n]
+
+
+def mcts(cfg: OracleConfig, root, seed: int, tree: int, budget: int):
+    """Returns (nodes (n, 4) int32 [action, parent, visits, wins] in creation
+    order, best (4,) int32 [action, visits, wins, root visits])."""
+    s = _state(root)
+    nodes = np.zeros((budget + 1, 4), dtype=np.int32)
+    n = ctypes.c_int(0)
+    best = np.zeros(4, dtype=np.int32)
+    c = cfg.c()
+    rc = lib().or_mcts(ctypes.byref(c), _u8(s), seed, tree, budget, _i32(nodes), ctypes.byref(n), _i32(best))
+    if rc:
+        raise ValueError(f"or_mcts rc={rc}")
+    return nodes[: n.value].copy(), best

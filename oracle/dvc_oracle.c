@@ -1,0 +1,944 @@
+/*
+ * dvc_oracle.c -- CPU oracle for the Da Vinci Code Monte Carlo Tree Search of
+ * arXiv 2403.10720 ("Development and Application of a Monte Carlo Tree Search
+ * Algorithm for Simulating Da Vinci Code Game Strategies").
+ *
+ * TEST INFRASTRUCTURE.  This is the plain, slow, single-threaded statement of
+ * what the GPU engine computes.  Only the test suite, the package smoke check
+ * and the benchmark's CPU-baseline leg load it; the product path never does.
+ * It shares no code, header, table or helper with the CUDA library: hands are
+ * explicit left-to-right tile sequences here (the GPU keeps bitmasks), every
+ * choice is made by building the full candidate list in canonical order and
+ * indexing it, and Philox is restated from its published definition.
+ *
+ * Passages followed (paper sections):
+ *   rules of the game ............ Sec. II-A (tile set, deal, draw + sorted
+ *                                  insertion, guess, correct guess -> reveal and
+ *                                  optional extra guess, wrong guess -> reveal
+ *                                  the drawn tile, last player standing wins)
+ *   random playout ............... Sec. II-B (game played out by random choices)
+ *   node = (position, number) .... Sec. III-A, simplification 1
+ *   plausible numbers sampled .... Sec. III-A (determinization per simulation)
+ *   stop after a correct guess ... Sec. III-A, simplification 2 (inside the tree)
+ *   expansion depth limit ........ Sec. III-A, simplification 3
+ *   root-parallel merge .......... Sec. III-B
+ *   Philox-4x32-10 ............... Salmon, Moraes, Dror, Shaw, "Parallel Random
+ *                                  Numbers: As Easy as 1, 2, 3", SC'11
+ *   ln for UCT ................... argument reduction to [sqrt(1/2), sqrt(2))
+ *                                  and ln m = 2 atanh((m-1)/(m+1)) by its
+ *                                  Taylor series (classic Cody-Waite style)
+ *
+ * Pins (tests/test_oracle_*.py): Philox known-answer vectors; ln against libm;
+ * rule invariants on traced playouts; the 88-guess root count of Sec. III-A;
+ * a closed-form 1/k endgame; exact win probabilities of tiny endgames by an
+ * independent exhaustive enumerator; determinizer counts against brute-force
+ * enumeration plus a chi-square test; UCB1 selection on a forced-win toy tree;
+ * visit-count invariants.  The value-network functions are pinned by finite
+ * differences and by a closed-form single-layer case.
+ *
+ * Readings of points the paper leaves open are listed in the design doc; the ones
+ * that shape code are repeated beside that code.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NUMBERED 24          /* tiles 0..23: value v = t/2, colour c = t%2 */
+#define JOKER_BLACK 24
+#define JOKER_WHITE 25
+#define MAXT 26
+#define MAXP 4
+#define MAXLEGAL (3 * MAXT * MAXT)
+
+enum { TAG_INIT = 1, TAG_DET = 2, TAG_TREE = 3, TAG_ROLL = 4 };
+
+typedef struct {
+    int32_t nplayers, ntiles, deal, max_predraw, max_revealed;
+    uint32_t cont_thr; /* after a correct guess in a playout: guess again iff word < cont_thr; 0 = never, no word */
+    double c_uct;
+    int32_t d_max, playouts;
+} or_config;
+
+/* ------------------------------------------------------------------ Philox */
+
+/* Philox-4x32 with 10 rounds (Salmon et al., SC'11): each round multiplies
+ * words 0 and 2 by fixed odd constants, swaps the halves, and xors in the
+ * round key; the key is bumped by the Weyl constants between rounds. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One random stream: key = (low word of seed, tree id), counter =
+ * (block, playout, iteration or leaf, tag + 16 * high word of seed).
+ * Words of a block are used in order, then the block index advances. */
+typedef struct {
+    uint32_t key[2], ctr[4], buf[4];
+    int used;
+    int64_t words; /* words consumed so far (statistics only) */
+} stream;
+
+static void stream_open(stream* s, uint64_t seed, uint32_t tree, uint32_t j, uint32_t i, uint32_t tag) {
+    s->key[0] = (uint32_t)seed;
+    s->key[1] = tree;
+    s->ctr[0] = 0;
+    s->ctr[1] = j;
+    s->ctr[2] = i;
+    s->ctr[3] = tag + 16u * (uint32_t)(seed >> 32);
+    s->used = 4;
+    s->words = 0;
+}
+
+static uint32_t next_word(stream* s) {
+    if (s->used == 4) {
+        or_philox4x32_10(s->ctr, s->key, s->buf);
+        s->ctr[0]++;
+        s->used = 0;
+    }
+    s->words++;
+    return s->buf[s->used++];
+}
+
+/* A uniform choice among n candidates from one 32-bit word: floor(w*n/2^32). */
+static int pick(uint32_t w, int n) { return (int)(((uint64_t)w * (uint64_t)n) >> 32); }
+
+/* A choice among W candidates from a 64-bit value r: floor(r*W/2^64). */
+static uint64_t pick64(uint64_t r, uint64_t W) {
+    return (uint64_t)(((unsigned __int128)r * (unsigned __int128)W) >> 64);
+}
+
+static uint64_t next_word64(stream* s) {
+    uint64_t lo = next_word(s);
+    uint64_t hi = next_word(s);
+    return (hi << 32) | lo;
+}
+
+/* ------------------------------------------------------------------- state */
+
+typedef struct {
+    int P, T;
+    int seq[MAXP][MAXT]; /* each hand left to right */
+    int len[MAXP];
+    int rev[MAXT];   /* 1 = face up */
+    int owner[MAXT]; /* -1 = in the pool */
+    int alive[MAXP];
+    int cur, drawn, winner; /* drawn: tile drawn this turn or -1; winner -1 while running */
+} ost;
+
+/* Boundary format (32 bytes, little endian): hand[4] u32 tile bitmasks at 0,
+ * revealed u32 at 16, joker gaps u8[2] at 20 (numbered tiles left of each
+ * joker in its owner's hand, 0 when in the pool), flags u8 at 22 (bit 0: both
+ * jokers share an owner and a gap and the white one is first), cur at 23,
+ * drawn at 24 (0xFF none), alive mask at 25, players at 26, tiles at 27,
+ * winner at 28 (0xFF while running), zero padding 29..31. */
+static uint32_t rd32(const uint8_t* p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+static void wr32(uint8_t* p, uint32_t v) {
+    p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
+}
+
+static int numbered_before(const ost* s, int p, int pos) {
+    int n = 0;
+    for (int i = 0; i < pos; i++) n += s->seq[p][i] < NUMBERED;
+    return n;
+}
+
+static void pack(const ost* s, uint8_t* out) {
+    memset(out, 0, 32);
+    for (int p = 0; p < s->P; p++) {
+        uint32_t m = 0;
+        for (int i = 0; i < s->len[p]; i++) m |= 1u << s->seq[p][i];
+        wr32(out + 4 * p, m);
+    }
+    uint32_t rv = 0;
+    for (int t = 0; t < s->T; t++) if (s->rev[t]) rv |= 1u << t;
+    wr32(out + 16, rv);
+    int jpos[2] = {-1, -1}, jown[2] = {-1, -1};
+    for (int j = 0; j < 2; j++) {
+        int t = JOKER_BLACK + j;
+        if (t >= s->T || s->owner[t] < 0) continue;
+        int p = s->owner[t];
+        for (int i = 0; i < s->len[p]; i++) if (s->seq[p][i] == t) jpos[j] = i;
+        jown[j] = p;
+        out[20 + j] = (uint8_t)numbered_before(s, p, jpos[j]);
+    }
+    if (jown[0] >= 0 && jown[0] == jown[1] && out[20] == out[21] && jpos[1] < jpos[0]) out[22] = 1;
+    out[23] = (uint8_t)s->cur;
+    out[24] = s->drawn < 0 ? 0xFF : (uint8_t)s->drawn;
+    uint8_t al = 0;
+    for (int p = 0; p < s->P; p++) if (s->alive[p]) al |= (uint8_t)(1u << p);
+    out[25] = al;
+    out[26] = (uint8_t)s->P;
+    out[27] = (uint8_t)s->T;
+    out[28] = s->winner < 0 ? 0xFF : (uint8_t)s->winner;
+}
+
+static void unpack(const uint8_t* in, ost* s) {
+    memset(s, 0, sizeof(*s));
+    s->P = in[26];
+    s->T = in[27];
+    for (int t = 0; t < MAXT; t++) s->owner[t] = -1;
+    uint32_t rv = rd32(in + 16);
+    for (int t = 0; t < s->T; t++) s->rev[t] = (rv >> t) & 1u;
+    for (int p = 0; p < s->P; p++) {
+        uint32_t m = rd32(in + 4 * p);
+        int num[NUMBERED], nn = 0;
+        for (int t = 0; t < NUMBERED; t++) if ((m >> t) & 1u) num[nn++] = t;
+        int hasj[2] = {(int)((m >> JOKER_BLACK) & 1u), (int)((m >> JOKER_WHITE) & 1u)};
+        int white_first = in[22] & 1;
+        for (int g = 0; g <= nn; g++) {
+            int order[2] = {0, 1};
+            if (white_first) { order[0] = 1; order[1] = 0; }
+            for (int k = 0; k < 2; k++) {
+                int j = order[k];
+                if (hasj[j] && in[20 + j] == g) {
+                    s->seq[p][s->len[p]++] = JOKER_BLACK + j;
+                    s->owner[JOKER_BLACK + j] = p;
+                }
+            }
+            if (g < nn) {
+                s->seq[p][s->len[p]++] = num[g];
+                s->owner[num[g]] = p;
+            }
+        }
+        s->alive[p] = (in[25] >> p) & 1u;
+    }
+    s->cur = in[23];
+    s->drawn = in[24] == 0xFF ? -1 : in[24];
+    s->winner = in[28] == 0xFF ? -1 : in[28];
+}
+
+static int nalive(const ost* s) {
+    int n = 0;
+    for (int p = 0; p < s->P; p++) n += s->alive[p];
+    return n;
+}
+
+static int hidden_of(const ost* s, int p) {
+    int n = 0;
+    for (int i = 0; i < s->len[p]; i++) n += !s->rev[s->seq[p][i]];
+    return n;
+}
+
+static int revealed_of(const ost* s, int p) { return s->len[p] - hidden_of(s, p); }
+
+/* ------------------------------------------------------------------- rules */
+
+static void put_at(ost* s, int p, int pos, int t) {
+    for (int i = s->len[p]; i > pos; i--) s->seq[p][i] = s->seq[p][i - 1];
+    s->seq[p][pos] = t;
+    s->len[p]++;
+    s->owner[t] = p;
+}
+
+/* Sorted insertion (Sec. II-A).  A numbered tile goes immediately before the
+ * first numbered tile with a larger id (black before white on equal values),
+ * so jokers already in that gap stay on its left.  A joker may stand anywhere:
+ * its position is uniform over the len+1 insertion points (one word). */
+static void insert_tile(ost* s, int p, int t, stream* rng) {
+    int pos = s->len[p];
+    if (t < NUMBERED) {
+        for (int i = 0; i < s->len[p]; i++) {
+            int u = s->seq[p][i];
+            if (u < NUMBERED && u > t) { pos = i; break; }
+        }
+    } else {
+        pos = pick(next_word(rng), s->len[p] + 1);
+    }
+    put_at(s, p, pos, t);
+}
+
+static int pool_list(const ost* s, int* out) {
+    int n = 0;
+    for (int t = 0; t < s->T; t++) if (s->owner[t] < 0) out[n++] = t;
+    return n;
+}
+
+/* Draw phase: a uniform tile of the pool (ascending id order), inserted. */
+static void draw_for(ost* s, int p, stream* rng) {
+    int pool[MAXT];
+    int n = pool_list(s, pool);
+    if (n == 0) { s->drawn = -1; return; }
+    int t = pool[pick(next_word(rng), n)];
+    insert_tile(s, p, t, rng);
+    s->drawn = t;
+}
+
+/* Every guess the player to move may make, in canonical order: opponents in
+ * seat order from cur+1, their face-down slots left to right, then every tile
+ * identity that is neither in the guesser's own hand nor face up. */
+static int legal_list(const ost* s, int* lq, int* ls, int* lx) {
+    int n = 0;
+    for (int off = 1; off < s->P; off++) {
+        int q = (s->cur + off) % s->P;
+        if (!s->alive[q]) continue;
+        for (int i = 0; i < s->len[q]; i++) {
+            if (s->rev[s->seq[q][i]]) continue;
+            for (int x = 0; x < s->T; x++) {
+                if (s->owner[x] == s->cur || s->rev[x]) continue;
+                lq[n] = q; ls[n] = i; lx[n] = x;
+                n++;
+            }
+        }
+    }
+    return n;
+}
+
+static int guess_is_legal(const ost* s, int q, int slot, int x) {
+    if (q == s->cur || q >= s->P || !s->alive[q]) return 0;
+    if (slot >= s->len[q] || s->rev[s->seq[q][slot]]) return 0;
+    if (x >= s->T || s->owner[x] == s->cur || s->rev[x]) return 0;
+    return 1;
+}
+
+enum { TURN_OVER = 0, GUESS_AGAIN = 1, GAME_OVER = 2 };
+
+/* Guess resolution (Sec. II-A).  A correct guess turns the target face up;
+ * a player with nothing face down is out; the last player standing wins.
+ * After a correct guess a playout guesses again iff the next word is below
+ * cont_thr; inside the tree the turn always ends (Sec. III-A, simplification
+ * 2).  A wrong guess turns the guesser's drawn tile face up, or the leftmost
+ * face-down tile when the pool was empty at the draw. */
+static int resolve(ost* s, int q, int slot, int x, int in_tree, uint32_t cont_thr, stream* rng) {
+    int t = s->seq[q][slot];
+    if (t == x) {
+        s->rev[t] = 1;
+        if (hidden_of(s, q) == 0) s->alive[q] = 0;
+        if (nalive(s) == 1) { s->winner = s->cur; return GAME_OVER; }
+        if (!in_tree && cont_thr != 0u && next_word(rng) < cont_thr) return GUESS_AGAIN;
+        return TURN_OVER;
+    }
+    int c = s->cur;
+    if (s->drawn >= 0) {
+        s->rev[s->drawn] = 1;
+    } else {
+        for (int i = 0; i < s->len[c]; i++) {
+            if (!s->rev[s->seq[c][i]]) { s->rev[s->seq[c][i]] = 1; break; }
+        }
+    }
+    if (hidden_of(s, c) == 0) s->alive[c] = 0;
+    if (nalive(s) == 1) {
+        for (int p = 0; p < s->P; p++) if (s->alive[p]) s->winner = p;
+        return GAME_OVER;
+    }
+    return TURN_OVER;
+}
+
+/* The turn passes to the next player still in, who draws. */
+static void next_turn(ost* s, stream* rng) {
+    int p = s->cur;
+    do { p = (p + 1) % s->P; } while (!s->alive[p]);
+    s->cur = p;
+    draw_for(s, p, rng);
+}
+
+static _Thread_local int legal_q[MAXLEGAL], legal_s[MAXLEGAL], legal_x[MAXLEGAL];
+
+/* One random playout from a state where the player to move is about to guess
+ * (Sec. II-B): uniform guesses among the legal ones until one player is left. */
+static int playout(ost s, uint32_t cont_thr, stream* rng, uint8_t* trace, int* ntrace, int maxtrace) {
+    for (;;) {
+        int n = legal_list(&s, legal_q, legal_s, legal_x);
+        int k = pick(next_word(rng), n);
+        int r = resolve(&s, legal_q[k], legal_s[k], legal_x[k], 0, cont_thr, rng);
+        if (r == TURN_OVER) next_turn(&s, rng);
+        if (trace && *ntrace < maxtrace) pack(&s, trace + 32 * (*ntrace)++);
+        if (r == GAME_OVER) return s.winner;
+    }
+}
+
+/* -------------------------------------------------------------- root states */
+
+/* Seeded root state (one per index): a deal of cfg->deal tiles to each
+ * player in seat order, then a random-policy history of d post-deal draws with
+ * d uniform in 0..max_predraw, then the player to move draws.  Histories that
+ * end the game or leave some player with more than max_revealed tiles face up
+ * are rejected and retried on the same stream; the last attempt uses d = 0. */
+#define INIT_ATTEMPTS 16
+static void init_one(const or_config* cfg, uint64_t seed, uint32_t index, ost* out) {
+    stream rng;
+    stream_open(&rng, seed, index, 0, 0, TAG_INIT);
+    for (int attempt = 0; attempt < INIT_ATTEMPTS; attempt++) {
+        ost s;
+        memset(&s, 0, sizeof(s));
+        s.P = cfg->nplayers;
+        s.T = cfg->ntiles;
+        for (int t = 0; t < MAXT; t++) s.owner[t] = -1;
+        for (int p = 0; p < s.P; p++) s.alive[p] = 1;
+        s.winner = -1;
+        for (int p = 0; p < s.P; p++)
+            for (int d = 0; d < cfg->deal; d++) draw_for(&s, p, &rng);
+        s.drawn = -1;
+        s.cur = 0;
+        int target = pick(next_word(&rng), cfg->max_predraw + 1);
+        int last = attempt == INIT_ATTEMPTS - 1;
+        if (last) target = 0;
+        int draws = 0, over = 0, pool[MAXT];
+        while (draws < target && pool_list(&s, pool) > 0) {
+            draw_for(&s, s.cur, &rng);
+            draws++;
+            for (;;) {
+                int n = legal_list(&s, legal_q, legal_s, legal_x);
+                int k = pick(next_word(&rng), n);
+                int r = resolve(&s, legal_q[k], legal_s[k], legal_x[k], 0, cfg->cont_thr, &rng);
+                if (r == GAME_OVER) { over = 1; break; }
+                if (r == TURN_OVER) break;
+            }
+            if (over) break;
+            int p = s.cur;
+            do { p = (p + 1) % s.P; } while (!s.alive[p]);
+            s.cur = p;
+        }
+        if (over) continue;
+        int bad = 0;
+        for (int p = 0; p < s.P; p++) bad |= revealed_of(&s, p) > cfg->max_revealed;
+        if (bad && !last) continue;
+        draw_for(&s, s.cur, &rng);
+        *out = s;
+        return;
+    }
+}
+
+int or_init_states(const or_config* cfg, uint64_t seed, int n, uint8_t* out) {
+    if (!cfg || n < 0 || cfg->nplayers < 2 || cfg->nplayers > MAXP) return -1;
+    if (cfg->ntiles != 24 && cfg->ntiles != 26) return -1;
+    if (cfg->deal < 1 || cfg->nplayers * cfg->deal >= cfg->ntiles) return -1;
+    for (int i = 0; i < n; i++) {
+        ost s;
+        init_one(cfg, seed, (uint32_t)i, &s);
+        pack(&s, out + 32 * (size_t)i);
+    }
+    return 0;
+}
+
+/* ----------------------------------------------------------- determinizing */
+
+/* Sec. III-A: each simulation draws a set of plausible values for the tiles
+ * the observer cannot see.  Reading: uniform over every assignment of the
+ * unknown tiles (all tiles minus the observer's hand minus face-up tiles) to
+ * the opponents' face-down slots and the pool that is consistent with what
+ * the observer sees: each opponent's slot count, the order of numbered tiles
+ * (ascending by id), the face-up numbered tiles as anchors, and jokers free to
+ * stand in any slot.
+ *
+ * Counting: the unknown numbered tiles are taken in ascending id order.  For
+ * each opponent, the face-down slots between two consecutive face-up numbered
+ * anchors form a gap that numbered tiles from that id interval fill in order;
+ * slots of a gap left unfilled when the tiles pass its right anchor must hold
+ * jokers.  count(i, r, J) is the number of completions when tile u_i is next,
+ * r[k] slots of opponent k's current gap are still open, and J unknown jokers
+ * are unplaced.  Closing a gap of c slots with r open ones multiplies by
+ * C(c, r) * J!/(J-r)! (which slots, which jokers).  Sampling walks the tiles
+ * in the same order, choosing the destination (pool first, then opponents
+ * from observer+1) in proportion to the completions each leaves, with
+ * floor(r64 * total / 2^64) from two words; each close with r > 0 draws one
+ * more such index over its C(c, r) * J!/(J-r)! options. */
+
+typedef struct {
+    int nq, q[3];
+    int nanch[3], anch[3][MAXT];
+    int gapsz[3][MAXT + 1];
+    int gap_of_slot[3][MAXT]; /* gap index of each face-down slot, -1 for face-up */
+    int m, u[NUMBERED];
+    int J0, jok[2];
+    int G[3][NUMBERED + 1];
+    int dim[3];
+    uint64_t* memo;
+    uint8_t* known;
+    size_t stride_i, stride_J;
+} detctx;
+
+static uint64_t choose(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; i++) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+    return r;
+}
+
+static uint64_t joker_close_mult(int c, int r, int J) {
+    if (r == 0) return 1;
+    if (r > J) return 0;
+    uint64_t perm = 1;
+    for (int i = 0; i < r; i++) perm *= (uint64_t)(J - i);
+    return choose(c, r) * perm;
+}
+
+static int det_setup(const ost* s, int obs, detctx* d) {
+    memset(d, 0, sizeof(*d));
+    d->nq = s->P - 1;
+    for (int k = 0; k < d->nq; k++) {
+        int q = (obs + 1 + k) % s->P;
+        d->q[k] = q;
+        int g = 0;
+        for (int i = 0; i < s->len[q]; i++) {
+            int t = s->seq[q][i];
+            if (s->rev[t]) {
+                d->gap_of_slot[k][i] = -1;
+                if (t < NUMBERED) { d->anch[k][d->nanch[k]++] = t; g++; }
+            } else {
+                d->gap_of_slot[k][i] = g;
+                d->gapsz[k][g]++;
+            }
+        }
+    }
+    for (int t = 0; t < s->T; t++) {
+        if (s->owner[t] == obs || s->rev[t]) continue;
+        if (t < NUMBERED) d->u[d->m++] = t;
+        else d->jok[d->J0++] = t;
+    }
+    for (int k = 0; k < d->nq; k++) {
+        for (int i = 0; i < d->m; i++) {
+            int g = 0;
+            while (g < d->nanch[k] && d->anch[k][g] < d->u[i]) g++;
+            d->G[k][i] = g;
+        }
+        d->G[k][d->m] = d->nanch[k];
+        int mx = 0;
+        for (int g = 0; g <= d->nanch[k]; g++) if (d->gapsz[k][g] > mx) mx = d->gapsz[k][g];
+        d->dim[k] = mx + 1;
+    }
+    for (int k = d->nq; k < 3; k++) d->dim[k] = 1;
+    d->stride_J = (size_t)d->dim[0] * d->dim[1] * d->dim[2];
+    d->stride_i = d->stride_J * (size_t)(d->J0 + 1);
+    size_t cells = d->stride_i * (size_t)(d->m + 1);
+    d->memo = (uint64_t*)calloc(cells, sizeof(uint64_t));
+    d->known = (uint8_t*)calloc(cells, 1);
+    return d->memo && d->known ? 0 : -1;
+}
+
+static void det_free(detctx* d) {
+    free(d->memo);
+    free(d->known);
+}
+
+/* Moving on from layer i (u_i placed or i = -1 at the start) to layer i+1:
+ * close every gap the tiles pass.  Returns the multiplier (0 if impossible),
+ * and updates r and J.  With rng non-NULL the closes also choose joker slots,
+ * recording them in jslot (per opponent, per face-down slot: joker id or -1). */
+static uint64_t advance(const detctx* d, int i, int* r, int* J, stream* rng, int jslot[3][MAXT]);
+
+static void place_jokers(const detctx* d, int k, int g, int c, int rr, int* J, int* jleft, stream* rng,
+                         int jslot[3][MAXT]) {
+    uint64_t opts = joker_close_mult(c, rr, *J);
+    uint64_t z = pick64(next_word64(rng), opts);
+    uint64_t perms = 1;
+    for (int i = 0; i < rr; i++) perms *= (uint64_t)(*J - i);
+    uint64_t posidx = z / perms, perm = z % perms;
+    int pos[2] = {-1, -1};
+    if (rr == 1) {
+        pos[0] = (int)posidx;
+    } else { /* rr == 2: pairs (a, b), a < b, in lexicographic order */
+        uint64_t left = posidx;
+        for (int a = 0; a < c && pos[0] < 0; a++) {
+            uint64_t cnt = (uint64_t)(c - 1 - a);
+            if (left < cnt) { pos[0] = a; pos[1] = a + 1 + (int)left; }
+            else left -= cnt;
+        }
+    }
+    int chosen[2];
+    if (rr == 1) {
+        chosen[0] = jleft[perm];
+    } else {
+        chosen[0] = jleft[perm == 0 ? 0 : 1];
+        chosen[1] = jleft[perm == 0 ? 1 : 0];
+    }
+    /* map gap-local slot numbers to hand slots */
+    int q = d->q[k];
+    (void)q;
+    for (int e = 0; e < rr; e++) {
+        int local = 0;
+        for (int i = 0; i < MAXT; i++) {
+            if (d->gap_of_slot[k][i] != g) continue;
+            if (local == pos[e]) { jslot[k][i] = chosen[e]; break; }
+            local++;
+        }
+    }
+    /* remove the chosen jokers from the unplaced list (kept ascending) */
+    int nl = 0, keep[2];
+    for (int a = 0; a < *J; a++) {
+        int used = 0;
+        for (int e = 0; e < rr; e++) used |= jleft[a] == chosen[e];
+        if (!used) keep[nl++] = jleft[a];
+    }
+    for (int a = 0; a < nl; a++) jleft[a] = keep[a];
+    *J = nl;
+}
+
+static _Thread_local int jleft_buf[2];
+
+static uint64_t advance(const detctx* d, int i, int* r, int* J, stream* rng, int jslot[3][MAXT]) {
+    uint64_t mult = 1;
+    for (int k = 0; k < d->nq; k++) {
+        int from = i < 0 ? -1 : d->G[k][i];
+        int to = d->G[k][i + 1];
+        if (to == from) continue;
+        for (int g = from < 0 ? 0 : from; g < to; g++) {
+            int open = (g == from) ? r[k] : d->gapsz[k][g];
+            uint64_t f = joker_close_mult(d->gapsz[k][g], open, *J);
+            if (f == 0) return 0;
+            if (rng && open > 0) place_jokers(d, k, g, d->gapsz[k][g], open, J, jleft_buf, rng, jslot);
+            else *J -= open;
+            mult *= f;
+        }
+        r[k] = d->gapsz[k][to];
+    }
+    return mult;
+}
+
+static uint64_t finish_mult(const detctx* d, const int* r, int J) {
+    uint64_t mult = 1;
+    for (int k = 0; k < d->nq; k++) {
+        int g = d->nanch[k];
+        uint64_t f = joker_close_mult(d->gapsz[k][g], r[k], J);
+        if (f == 0) return 0;
+        J -= r[k];
+        mult *= f;
+    }
+    return mult;
+}
+
+static uint64_t det_count(detctx* d, int i, const int* r, int J) {
+    size_t cell = (size_t)i * d->stride_i + (size_t)J * d->stride_J +
+                  ((size_t)r[0] * d->dim[1] + (size_t)r[1]) * d->dim[2] + (size_t)r[2];
+    if (d->known[cell]) return d->memo[cell];
+    uint64_t total = 0;
+    if (i == d->m) {
+        total = finish_mult(d, r, J);
+    } else {
+        for (int dest = -1; dest < d->nq; dest++) {
+            int r2[3] = {r[0], r[1], r[2]};
+            int J2 = J;
+            if (dest >= 0) {
+                if (r2[dest] == 0) continue;
+                r2[dest]--;
+            }
+            uint64_t f = advance(d, i, r2, &J2, NULL, NULL);
+            if (f) total += f * det_count(d, i + 1, r2, J2);
+        }
+    }
+    d->known[cell] = 1;
+    d->memo[cell] = total;
+    return total;
+}
+
+static uint64_t det_total(detctx* d) {
+    int r[3] = {0, 0, 0};
+    int J = d->J0;
+    uint64_t f = advance(d, -1, r, &J, NULL, NULL);
+    if (!f) return 0;
+    return f * det_count(d, 0, r, J);
+}
+
+uint64_t or_det_count(const uint8_t* root, int observer) {
+    ost s;
+    unpack(root, &s);
+    if (observer < 0) observer = s.cur;
+    detctx d;
+    if (det_setup(&s, observer, &d)) return 0;
+    uint64_t n = det_total(&d);
+    det_free(&d);
+    return n;
+}
+
+static int determinize(const ost* root, int obs, stream* rng, ost* out) {
+    detctx d;
+    if (det_setup(root, obs, &d)) return -1;
+    if (det_total(&d) == 0) { det_free(&d); return -2; }
+    int jslot[3][MAXT];
+    for (int k = 0; k < 3; k++) for (int i = 0; i < MAXT; i++) jslot[k][i] = -1;
+    int assigned[3][MAXT], nassigned[3] = {0, 0, 0};
+    int r[3] = {0, 0, 0};
+    int J = d.J0;
+    jleft_buf[0] = d.jok[0];
+    jleft_buf[1] = d.jok[1];
+    advance(&d, -1, r, &J, rng, jslot);
+    for (int i = 0; i < d.m; i++) {
+        uint64_t w[4] = {0, 0, 0, 0}, W = 0;
+        for (int dest = -1; dest < d.nq; dest++) {
+            int r2[3] = {r[0], r[1], r[2]};
+            int J2 = J;
+            if (dest >= 0) {
+                if (r2[dest] == 0) continue;
+                r2[dest]--;
+            }
+            uint64_t f = advance(&d, i, r2, &J2, NULL, NULL);
+            if (f) w[dest + 1] = f * det_count(&d, i + 1, r2, J2);
+            W += w[dest + 1];
+        }
+        uint64_t x = pick64(next_word64(rng), W);
+        int dest = -1;
+        for (int e = 0; e < 4; e++) {
+            if (x < w[e]) { dest = e - 1; break; }
+            x -= w[e];
+        }
+        if (dest >= 0) {
+            assigned[dest][nassigned[dest]++] = d.u[i];
+            r[dest]--;
+        }
+        advance(&d, i, r, &J, rng, jslot);
+    }
+    /* the last gaps of each opponent */
+    for (int k = 0; k < d.nq; k++) {
+        int g = d.nanch[k];
+        if (r[k] > 0) place_jokers(&d, k, g, d.gapsz[k][g], r[k], &J, jleft_buf, rng, jslot);
+    }
+    /* rebuild the opponents' hands */
+    *out = *root;
+    for (int t = 0; t < out->T; t++)
+        if (out->owner[t] >= 0 && out->owner[t] != obs && !out->rev[t]) out->owner[t] = -1;
+    for (int k = 0; k < d.nq; k++) {
+        int q = d.q[k];
+        int next = 0;
+        for (int i = 0; i < out->len[q]; i++) {
+            if (d.gap_of_slot[k][i] < 0) continue;
+            int t = jslot[k][i] >= 0 ? jslot[k][i] : assigned[k][next++];
+            out->seq[q][i] = t;
+            out->owner[t] = q;
+        }
+    }
+    det_free(&d);
+    return 0;
+}
+
+int or_determinize(const or_config* cfg, const uint8_t* root, int observer, uint64_t seed, uint32_t tree,
+                   uint32_t iter, uint8_t* out) {
+    (void)cfg;
+    ost s, o;
+    unpack(root, &s);
+    if (observer < 0) observer = s.cur;
+    stream rng;
+    stream_open(&rng, seed, tree, 0, iter, TAG_DET);
+    int rc = determinize(&s, observer, &rng, &o);
+    if (rc) return rc;
+    pack(&o, out);
+    return 0;
+}
+
+/* ----------------------------------------------------------------- rollouts */
+
+/* Per-leaf playouts (Sec. II-B; leaf parallelism): playout j of leaf i of
+ * tree t runs on the stream keyed (seed, t) with counter (., j, i, ROLL). */
+int or_rollout(const or_config* cfg, const uint8_t* leaf, int P, uint64_t seed, uint32_t tree, uint32_t leaf_id,
+               int32_t* wins, int64_t* words) {
+    ost s;
+    unpack(leaf, &s);
+    for (int p = 0; p < 4; p++) wins[p] = 0;
+    int64_t total = 0;
+    if (s.winner >= 0) {
+        wins[s.winner] = P;
+        if (words) *words = 0;
+        return 0;
+    }
+    for (int j = 0; j < P; j++) {
+        stream rng;
+        stream_open(&rng, seed, tree, (uint32_t)j, leaf_id, TAG_ROLL);
+        int w = playout(s, cfg->cont_thr, &rng, NULL, NULL, 0);
+        wins[w]++;
+        total += rng.words;
+    }
+    if (words) *words = total;
+    return 0;
+}
+
+int or_playout_trace(const or_config* cfg, const uint8_t* leaf, uint64_t seed, uint32_t tree, uint32_t j,
+                     uint32_t leaf_id, uint8_t* trace, int maxtrace) {
+    ost s;
+    unpack(leaf, &s);
+    stream rng;
+    stream_open(&rng, seed, tree, j, leaf_id, TAG_ROLL);
+    int n = 0;
+    playout(s, cfg->cont_thr, &rng, trace, &n, maxtrace);
+    return n;
+}
+
+int or_legal_count(const uint8_t* state) {
+    ost s;
+    unpack(state, &s);
+    return legal_list(&s, legal_q, legal_s, legal_x);
+}
+
+/* --------------------------------------------------------------------- UCT */
+
+/* Natural log: x = m * 2^e with m in [sqrt(1/2), sqrt(2)); ln x = e ln 2 +
+ * 2 atanh(z), z = (m-1)/(m+1), the series z + z^3/3 + ... evaluated by Horner
+ * from the 23rd power down.  Plain IEEE double operations in a fixed order. */
+double or_ln(double x) {
+    union { double d; uint64_t u; } v;
+    v.d = x;
+    int e = (int)((v.u >> 52) & 0x7FF) - 1023;
+    v.u = (v.u & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    double m = v.d;
+    if (m > 1.4142135623730951) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    double z = (m - 1.0) / (m + 1.0);
+    double z2 = z * z;
+    double p = 1.0 / 23.0;
+    for (int k = 10; k >= 0; k--) p = p * z2 + 1.0 / (double)(2 * k + 1);
+    double lnm = 2.0 * (z * p);
+    return (double)e * 0.6931471805599453 + lnm;
+}
+
+/* Score of a child (UCB1 with visits counted in playouts):
+ *   mean = wins / n;  explore = (c * sqrt(ln N)) * (1 / sqrt(n));  score = mean + explore
+ * with N the parent's visits, evaluated in exactly this order. */
+static double uct_score(double c_sqrt_lnN, int32_t w, int32_t n) {
+    double mean = (double)w / (double)n;
+    double rs = 1.0 / sqrt((double)n);
+    return mean + c_sqrt_lnN * rs;
+}
+
+static int canon_rank(int code, int cur, int P) {
+    int q = code >> 10;
+    return ((((q - cur - 1) % P + P) % P) << 10) | (code & 1023);
+}
+
+typedef struct {
+    int n, cap;
+    int32_t *action, *parent, *visits, *wins, *child, *sib, *last;
+} otree;
+
+static int tree_new_node(otree* t, int parent, int code) {
+    int id = t->n++;
+    t->action[id] = code;
+    t->parent[id] = parent;
+    t->visits[id] = 0;
+    t->wins[id] = 0;
+    t->child[id] = -1;
+    t->sib[id] = -1;
+    t->last[id] = -1;
+    if (parent >= 0) {
+        if (t->child[parent] < 0) t->child[parent] = id;
+        else t->sib[t->last[parent]] = id;
+        t->last[parent] = id;
+    }
+    return id;
+}
+
+/* One search of `budget` iterations from `root` (observer = player to move):
+ * determinize, descend by UCT among children legal in this determinization,
+ * expand the first legal action without a child (canonical order) while the
+ * depth is below d_max, run `playouts` random playouts from the leaf, and add
+ * the playout count to every visit and the wins of each node's mover. */
+int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
+            int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
+    ost root;
+    unpack(root_packed, &root);
+    int obs = root.cur;
+    int P = cfg->playouts;
+    otree t;
+    t.cap = budget + 1;
+    t.n = 0;
+    int32_t* mem = (int32_t*)malloc(sizeof(int32_t) * 7 * (size_t)t.cap);
+    if (!mem) return -1;
+    t.action = mem; t.parent = mem + t.cap; t.visits = mem + 2 * t.cap; t.wins = mem + 3 * t.cap;
+    t.child = mem + 4 * t.cap; t.sib = mem + 5 * t.cap; t.last = mem + 6 * t.cap;
+    tree_new_node(&t, -1, 0);
+    int rc = 0;
+    for (int it = 0; it < budget && rc == 0; it++) {
+        ost s;
+        stream drng, trng;
+        stream_open(&drng, seed, tree_id, 0, (uint32_t)it, TAG_DET);
+        stream_open(&trng, seed, tree_id, 0, (uint32_t)it, TAG_TREE);
+        if (determinize(&root, obs, &drng, &s)) { rc = -2; break; }
+        int path[64], mover[64], np = 0;
+        path[np] = 0;
+        mover[np++] = obs;
+        int node = 0, depth = 0;
+        while (s.winner < 0 && depth < cfg->d_max) {
+            int n = legal_list(&s, legal_q, legal_s, legal_x);
+            int fresh = -1;
+            for (int a = 0; a < n && fresh < 0; a++) {
+                int code = (legal_q[a] << 10) | (legal_s[a] << 5) | legal_x[a];
+                int found = 0;
+                for (int c = t.child[node]; c >= 0; c = t.sib[c]) found |= t.action[c] == code;
+                if (!found) fresh = a;
+            }
+            int who = s.cur;
+            if (fresh >= 0) {
+                int code = (legal_q[fresh] << 10) | (legal_s[fresh] << 5) | legal_x[fresh];
+                int c = tree_new_node(&t, node, code);
+                if (resolve(&s, legal_q[fresh], legal_s[fresh], legal_x[fresh], 1, 0, NULL) != GAME_OVER)
+                    next_turn(&s, &trng);
+                path[np] = c;
+                mover[np++] = who;
+                break;
+            }
+            double lnN = or_ln((double)t.visits[node]);
+            double csl = cfg->c_uct * sqrt(lnN);
+            int best = -1, best_rank = 0;
+            double best_score = 0.0;
+            for (int c = t.child[node]; c >= 0; c = t.sib[c]) {
+                int code = t.action[c];
+                if (!guess_is_legal(&s, code >> 10, (code >> 5) & 31, code & 31)) continue;
+                double sc = uct_score(csl, t.wins[c], t.visits[c]);
+                int rank = canon_rank(code, s.cur, s.P);
+                if (best < 0 || sc > best_score || (sc == best_score && rank < best_rank)) {
+                    best = c; best_score = sc; best_rank = rank;
+                }
+            }
+            int code = t.action[best];
+            if (resolve(&s, code >> 10, (code >> 5) & 31, code & 31, 1, 0, NULL) != GAME_OVER) next_turn(&s, &trng);
+            path[np] = best;
+            mover[np++] = who;
+            node = best;
+            depth++;
+        }
+        int32_t wins[4] = {0, 0, 0, 0};
+        if (s.winner >= 0) {
+            wins[s.winner] = P;
+        } else {
+            uint8_t leaf[32];
+            pack(&s, leaf);
+            or_rollout(cfg, leaf, P, seed, tree_id, (uint32_t)it, wins, NULL);
+        }
+        for (int k = 0; k < np; k++) {
+            t.visits[path[k]] += P;
+            t.wins[path[k]] += wins[mover[k]];
+        }
+    }
+    if (rc == 0) {
+        if (nodes_out) {
+            for (int i = 0; i < t.n; i++) {
+                nodes_out[4 * i + 0] = t.action[i];
+                nodes_out[4 * i + 1] = t.parent[i];
+                nodes_out[4 * i + 2] = t.visits[i];
+                nodes_out[4 * i + 3] = t.wins[i];
+            }
+        }
+        if (n_nodes_out) *n_nodes_out = t.n;
+        if (best_out) {
+            /* decision: most visits, ties to the lowest canonical rank */
+            int best = -1;
+            for (int c = t.child[0]; c >= 0; c = t.sib[c]) {
+                if (best < 0 || t.visits[c] > t.visits[best] ||
+                    (t.visits[c] == t.visits[best] &&
+                     canon_rank(t.action[c], obs, root.P) < canon_rank(t.action[best], obs, root.P)))
+                    best = c;
+            }
+            best_out[0] = best < 0 ? -1 : t.action[best];
+            best_out[1] = best < 0 ? 0 : t.visits[best];
+            best_out[2] = best < 0 ? 0 : t.wins[best];
+            best_out[3] = t.visits[0];
+        }
+    }
+    free(mem);
+    return rc;
+}
