@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark: Da Vinci Code MCTS decisions on GB300.
+
+One step = one full decision batch of the 2-player/24-tile workload: 4,096
+mid-game roots, each searched with 4,096 UCT iterations x 256 leaf playouts
+(1,048,576 playouts per decision, 4.29e9 per step).  The step runs
+dvc_forest_reset (re-plan and re-fill the determinization tables, reset the
+trees), dvc_mcts_step (the fused select/expand/rollout/backprop kernel) and
+dvc_root_stats (decisions).
+
+Prints one JSON line.  `value` is playouts/s over all ranks (device-timed,
+roots resident in HBM); `e2e` is the same metric through the public API with
+host buffers: root states copied in from pinned memory and decisions copied
+back inside each timed step.  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload on the host cores.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under
+torch.distributed.run (one rank per GPU, weak scaling: each rank searches its
+own 4,096 trees).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2403_10720_gb300.workloads import BATCHED  # noqa: E402
+
+PHILOX_OPS_PER_WORD = 25  # Philox-4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) per 4 words
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(w, n_trees, threads):
+    """Search n_trees roots of the workload with the oracle, `threads` trees at a time."""
+    import oracle
+    cfg = oracle.OracleConfig(**w.config_kwargs())
+    roots = oracle.init_states(cfg, w.root_seed, n_trees)
+    budgets = w.budgets(n_trees)
+    nxt = [0]
+    lock = threading.Lock()
+
+    def worker():
+        while True:
+            with lock:
+                t = nxt[0]
+                nxt[0] += 1
+            if t >= n_trees:
+                return
+            oracle.mcts(cfg, roots[t], w.seed, t, int(budgets[t]))
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    dt = time.perf_counter() - t0
+    playouts = int(budgets.sum()) * w.playouts
+    return playouts, dt
+
+
+def run_reference(args, w):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    n = cores  # one full tree per core per step: about 5 s of host work per step
+    for _ in range(args.warmup):
+        oracle_sample(w, min(n, 2), min(cores, 2))
+    times, total = [], 0
+    for _ in range(args.steps):
+        p, dt = oracle_sample(w, n, cores)
+        times.append(dt)
+        total += p
+    value = total / sum(times)
+    sample = f"{n} of {w.n_trees} trees per step, each the full {w.budget} iterations x {w.playouts} playouts"
+    line = {
+        "impl": "reference", "metric": "playouts/s", "value": value, "unit": "playouts/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "trees": w.n_trees, "iterations": w.budget, "playouts_per_leaf": w.playouts,
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "playouts/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "playouts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "decisions_per_s": n * args.steps / sum(times),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    if local == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    ctx = dvc.Context(dvc.Config(**w.config_kwargs()), local)
+    n = w.n_trees
+    roots = ctx.dvc_init_states(w.root_seed + 1000003 * rank, n)
+    budgets = w.budgets()
+    forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=np.arange(rank * n, (rank + 1) * n, dtype=np.uint32))
+    stats = torch.empty((n, 8), dtype=torch.int32, device=dev)
+    words = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    budget = int(budgets.max())
+    playouts_per_step = int(budgets.sum()) * w.playouts
+
+    def step(k0=None, k1=None):
+        forest.dvc_forest_reset()
+        if k0 is not None:
+            k0.record(stream)
+        forest.dvc_mcts_step(budget)
+        if k1 is not None:
+            k1.record(stream)
+        forest.dvc_root_stats(out=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.dvc_check()
+    forest.dvc_forest_counters(out=words)  # zero the counter
+
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ev = [(E(), E(), E(), E()) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k)  # L2 flush between timed steps (outside the step's events)
+        s0, k0, k1, s1 = ev[k]
+        s0.record(stream)
+        step(k0, k1)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ctx.dvc_check()
+    step_ms = [a.elapsed_time(b) for a, _, _, b in ev]
+    kern_ms = [a.elapsed_time(b) for _, a, b, _ in ev]
+    forest.dvc_forest_counters(out=words)
+    words_per_step = int(words.item()) / args.steps
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = playouts_per_step * world * args.steps / total_s
+
+    # end to end through the public API: host roots in, host decisions out
+    host_roots = roots.cpu().pin_memory()
+    host_stats = torch.empty((n, 8), dtype=torch.int32).pin_memory()
+    dev_roots = torch.empty_like(roots)
+    e2e_ms = []
+    for k in range(max(1, args.steps)):
+        flush.fill_(k)
+        a, b = E(), E()
+        a.record(stream)
+        dev_roots.copy_(host_roots, non_blocking=True)
+        forest.dvc_forest_reset(dev_roots)
+        forest.dvc_mcts_step(budget)
+        forest.dvc_root_stats(out=stats)
+        host_stats.copy_(stats, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_s = sum(e2e_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = playouts_per_step * world * len(e2e_ms) / e2e_s
+    ctx.dvc_check()
+    decisions = host_stats.numpy()
+
+    peaks, peak_kind = _measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e9
+    kern_mean_s = sum(kern_ms) / len(kern_ms) / 1e3
+    achieved_gops = PHILOX_OPS_PER_WORD * words_per_step / kern_mean_s / 1e9
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "playouts/s", "value": value, "unit": "playouts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "trees": n, "iterations": w.budget, "playouts_per_leaf": w.playouts,
+                   "players": w.nplayers, "tiles": w.ntiles, "d_max": w.d_max,
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+        "decisions_per_s": n * world * args.steps / total_s,
+        "kernel_ms": sum(kern_ms) / len(kern_ms),
+        "words_per_playout": words_per_step / playouts_per_step,
+        "e2e": {"value": e2e_value, "unit": "playouts/s", "h2d_bytes_per_step": int(host_roots.numel()),
+                "d2h_bytes_per_step": int(host_stats.numel() * 4)},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved_gops / peak_gops, "traffic": None,
+                     "peak_kind": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind})",
+                     "work": "Philox-4x32-10 integer ops of the random words the playouts consume"},
+        "clocks": clk,
+        "first_decision": int(decisions[0][0]),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        p, dt = oracle_sample(w, cores, cores)
+        line["cpu_baseline"] = {"value": p / dt, "unit": "playouts/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{cores} of {w.n_trees} trees, full {w.budget} iterations x "
+                                          f"{w.playouts} playouts each, one tree per host thread"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = BATCHED
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * dvc.h -- C ABI of libdvc, a GB300 (sm_103a) engine for the Da Vinci Code
+ * Monte Carlo Tree Search of arXiv 2403.10720.
+ *
+ * What it computes (paper sections):
+ *   Sec. II-A   the game: 24 numbered tiles (values 0-11, black and white) plus
+ *               two jokers in the 26-tile variant; each player holds a hidden
+ *               row kept in ascending order; a turn is a draw with sorted
+ *               insertion, then guesses at opponents' face-down tiles; a
+ *               correct guess turns the tile face up and allows another
+ *               guess, a wrong one turns the guesser's drawn tile face up and
+ *               ends the turn; the last player with face-down tiles wins.
+ *   Sec. II-B   MCTS: select, expand, simulate by random playout, backpropagate.
+ *   Sec. III-A  the simplified tree: a node is a guess (slot, identity); the
+ *               unseen tiles are re-sampled per simulation (determinization);
+ *               inside the tree a correct guess ends the turn; expansion stops
+ *               at a fixed depth.
+ *   Sec. III-B  many searches run in parallel and their root statistics merge.
+ *
+ * Conventions, for every entry point:
+ *   - returns 0 on success or a negative DVC_E_* code; dvc_last_error() gives
+ *     a message.  No C++ exception crosses this boundary.
+ *   - pointers named d_* are DEVICE memory owned by the caller (for example
+ *     PyTorch tensors passed as raw pointers); h_* are host memory owned by
+ *     the caller.  The library owns only its context, forests and workspace.
+ *   - work is enqueued on the given CUDA stream (cudaStream_t passed as void*;
+ *     NULL = legacy default stream); outputs are valid after that stream is
+ *     synchronised.  Arguments are validated on the host before anything is
+ *     enqueued: a call that returns an error has enqueued nothing.
+ *   - errors found by a kernel (a determinization table larger than its
+ *     capacity, a node arena exhausted) are latched in a device flag of the
+ *     context; dvc_check() synchronises the device and reports them.
+ *   - a context is bound to the device given at creation; calls that enqueue
+ *     work make that device current on the calling thread.
+ *   - calls on one context or forest from several host threads at once are
+ *     not supported.
+ *
+ * Random numbers: Philox-4x32-10 (Salmon et al., SC'11).  A stream is keyed
+ * (low 32 bits of seed, tree id) with counter (block, playout j, iteration or
+ * leaf i, tag + 16 * high 32 bits of seed), tag 1 = root-state generation,
+ * 2 = determinization, 3 = draws inside the tree, 4 = playouts.  Words of a
+ * block are consumed in order.  Every result is therefore a pure function of
+ * (seed, tree id, iteration, playout index) and does not depend on the thread
+ * mapping, the launch shape or the order in which playouts finish.
+ */
+#ifndef DVC_H
+#define DVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DVC_OK 0
+#define DVC_E_INVALID (-1)     /* bad argument: size, null pointer, host pointer where device is needed */
+#define DVC_E_OOM (-2)         /* device allocation failed, or a forest arena is full */
+#define DVC_E_CUDA (-3)        /* a CUDA runtime call failed */
+#define DVC_E_TIMEOUT (-4)     /* a bounded device wait gave up */
+#define DVC_E_UNSUPPORTED (-5) /* a size beyond a documented capacity */
+
+#define DVC_MODE_ROLLOUT 0 /* leaves are scored by random playouts (Sec. II-B) */
+#define DVC_MODE_VALUE 1   /* leaves are scored by the value network */
+
+/*
+ * One game position, 32 bytes, identical on host and device.
+ * Tile ids: numbered tile t = 2*value + colour (colour 0 black, 1 white),
+ * 0..23; jokers 24 (black) and 25 (white).  A hand is the set of tiles a
+ * player holds; its left-to-right order is derived: numbered tiles ascend by
+ * id (black before white on equal values), each joker stands after joker_gap
+ * numbered tiles, and two jokers of one hand with the same gap are ordered
+ * black first unless bit 0 of flags is set.  The pool is every tile of the
+ * game held by nobody.
+ */
+typedef struct dvc_state {
+    uint32_t hand[4];     /* tile bitmask per seat (unused seats 0) */
+    uint32_t revealed;    /* face-up tiles */
+    uint8_t joker_gap[2]; /* numbered tiles left of joker 24 / 25 in its owner's hand; 0 in the pool */
+    uint8_t flags;        /* bit 0: both jokers share owner and gap and the white one is first */
+    uint8_t cur;          /* seat to move; it has drawn and is about to guess */
+    uint8_t drawn;        /* tile drawn this turn, 0xFF if the pool was empty */
+    uint8_t alive;        /* bitmask of seats with a face-down tile */
+    uint8_t nplayers;     /* 2..4 */
+    uint8_t ntiles;       /* 24 or 26 */
+    uint8_t winner;       /* 0xFF while the game runs */
+    uint8_t pad[3];       /* zero */
+} dvc_state;
+
+/*
+ * Game and search parameters.  Readings of what the paper leaves open:
+ * cont_thr -- after a correct guess a playout guesses again iff the next
+ * random word is below cont_thr (2^31 = probability 1/2; 0 = never, and no
+ * word is drawn); inside the tree the turn always ends (Sec. III-A).
+ * d_max -- the expansion depth limit of Sec. III-A, in guess plies below the
+ * root.  c_uct -- the UCB1 exploration constant.
+ */
+typedef struct dvc_config {
+    int32_t nplayers;         /* 2..4 */
+    int32_t ntiles;           /* 24 (no jokers) or 26 */
+    int32_t deal;             /* tiles dealt to each player (Sec. II-A: 4) */
+    int32_t max_predraw;      /* root generation: post-deal draws uniform in 0..max_predraw */
+    int32_t max_revealed;     /* root generation: reject histories with more face-up tiles per player */
+    uint32_t cont_thr;        /* see above */
+    double c_uct;             /* sqrt(2) */
+    int32_t d_max;            /* 8 */
+    int32_t playouts;         /* playouts per leaf in dvc_mcts_step (leaf parallelism) */
+} dvc_config;
+
+typedef struct dvc_ctx dvc_ctx;
+typedef struct dvc_forest dvc_forest;
+
+/* Create a context on CUDA device `device` with a copy of *cfg.  Validates
+ * the configuration (DVC_E_INVALID).  Owns nothing on the device until a
+ * call needs workspace. */
+int dvc_create(dvc_ctx** out, const dvc_config* cfg, int device);
+void dvc_destroy(dvc_ctx* ctx);
+const char* dvc_last_error(const dvc_ctx* ctx);
+
+/* Synchronise the context's device and report (then clear) any error a
+ * kernel latched: DVC_E_UNSUPPORTED, DVC_E_OOM or DVC_E_TIMEOUT. */
+int dvc_check(dvc_ctx* ctx);
+
+/*
+ * Root states (Sec. II-A deal; the workload's mid-game roots).  State i is
+ * generated on its own stream (seed, tree id i, tag 1): a deal of cfg->deal
+ * tiles to each seat in order, a random-policy history of d post-deal draws
+ * with d uniform in 0..max_predraw, then the seat to move draws.  Histories
+ * that end the game or leave a seat with more than max_revealed face-up
+ * tiles are retried on the same stream (16 attempts; the last uses d = 0).
+ * d_states: n records, written.  n = 0 is a no-op.
+ */
+int dvc_init_states(dvc_ctx* ctx, uint64_t seed, int n, dvc_state* d_states, void* stream);
+
+/*
+ * Determinization (Sec. III-A, plausible numbers): for each root r, a fresh
+ * assignment of the tiles `observer` cannot see, drawn uniformly among all
+ * assignments consistent with its view -- each opponent's slot count, face-up
+ * tiles in place, numbered tiles ascending, jokers free -- on the stream
+ * (seed, d_tree_ids[r], iteration d_iter_ids[r], tag 2).  observer < 0 means
+ * each root's seat to move.  d_roots and d_out: n records (may not overlap);
+ * d_tree_ids, d_iter_ids: n uint32 each.  A view whose counting table exceeds
+ * 32768 cells latches DVC_E_UNSUPPORTED (see dvc_check) and leaves that
+ * output equal to its root.
+ */
+int dvc_determinize(dvc_ctx* ctx, const dvc_state* d_roots, int n, int observer, uint64_t seed,
+                    const uint32_t* d_tree_ids, const uint32_t* d_iter_ids, dvc_state* d_out, void* stream);
+
+/*
+ * Leaf-parallel random playouts (Sec. II-B simulation; Sec. III-D: every GPU
+ * thread plays games out to a win or loss).  For leaf l and j in
+ * 0..playouts_per_leaf-1, playout j runs on stream (seed, d_tree_ids[l],
+ * playout j, leaf d_leaf_ids[l], tag 4) from d_leaves[l] (seat to move about
+ * to guess) with uniform guesses, cfg->cont_thr, until one seat is left.
+ * d_wins: n_leaves x 4 int32, OVERWRITTEN with the number of playouts each
+ * seat won (a finished leaf credits all playouts to its winner).
+ * d_words (optional, may be NULL): one uint64, overwritten with the number of
+ * random words the playouts consumed (the work count behind the roofline).
+ */
+int dvc_rollout_batch(dvc_ctx* ctx, const dvc_state* d_leaves, int n_leaves, int playouts_per_leaf, uint64_t seed,
+                      const uint32_t* d_tree_ids, const uint32_t* d_leaf_ids, int32_t* d_wins, uint64_t* d_words,
+                      void* stream);
+
+/*
+ * A forest of independent UCT trees (Sec. II-B; Sec. III-B runs many at
+ * once).  Tree t searches from d_roots[t] for the seat to move there, with
+ * h_budgets[t] iterations (one node per iteration at most; 0..2^24) and
+ * streams keyed (seed, h_tree_ids ? h_tree_ids[t] : t).  d_roots is copied
+ * on `stream`; h_budgets and h_tree_ids are host arrays read during the call.
+ * Device memory per tree: a node arena of 641 + 4 * budget 24-byte slots and
+ * a determinization table of 2,048 cells (2 players) or 32,768 cells (3-4
+ * players) of 8 bytes.  The root views are planned on the device without a
+ * host synchronisation; a view whose table does not fit latches
+ * DVC_E_UNSUPPORTED and its tree does no work.  DVC_E_OOM if memory runs out.
+ */
+int dvc_forest_create(dvc_ctx* ctx, int n_trees, const dvc_state* d_roots, const int32_t* h_budgets,
+                      const uint32_t* h_tree_ids, uint64_t seed, dvc_forest** out, void* stream);
+void dvc_forest_destroy(dvc_forest* f);
+
+/* Start every tree of the forest afresh (budgets, tree ids and seed kept):
+ * with d_roots non-NULL the forest first copies n_trees new roots from it.
+ * Asynchronous on `stream`; allocates nothing. */
+int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream);
+
+/*
+ * Fused search step: every tree runs min(n_iterations, budget - done)
+ * iterations of: determinize the root view (tag 2, iteration i), descend by
+ * UCB1 -- score = wins/n + (c_uct * sqrt(ln N)) * (1/sqrt(n)), N the parent's
+ * visits, ln by the library's own argument-reduced atanh series, ties to the
+ * lowest canonical action -- among children legal in this determinization,
+ * expand the first legal action without a child (canonical order: opponents
+ * from cur+1, slots left to right, identities ascending) while the depth is
+ * below d_max, draw in-tree tiles on tag 3, score the leaf (mode ROLLOUT:
+ * cfg->playouts playouts on tag 4 keyed by iteration; mode VALUE: the value
+ * network, see dvc_value_eval), and add cfg->playouts visits and each node's
+ * mover's wins along the path.  One launch; bit-exact with the split steps.
+ */
+int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
+
+/*
+ * The same iteration split into launches, for callers that score leaves
+ * themselves: dvc_mcts_select determinizes and descends, dvc_mcts_expand adds
+ * the new child and writes each tree's leaf state (dvc_forest_leaves gives
+ * the device pointer, n_trees records; trees whose budget is spent are
+ * marked finished with winner = 0xFE), the caller fills n_trees x 4 int32
+ * wins (e.g. with dvc_rollout_batch, tree ids and leaf ids from
+ * dvc_forest_leaf_ids), and dvc_mcts_backprop adds them.
+ */
+int dvc_mcts_select(dvc_forest* f, void* stream);
+int dvc_mcts_expand(dvc_forest* f, void* stream);
+int dvc_mcts_backprop(dvc_forest* f, const int32_t* d_wins, void* stream);
+int dvc_forest_leaves(dvc_forest* f, dvc_state** d_leaves, uint32_t** d_tree_ids, uint32_t** d_leaf_ids);
+
+/*
+ * Root statistics and decision (Sec. III-B merge, one tree): per tree 8 int32
+ * -- best action (most visits, ties to the lowest canonical action; -1 if
+ * none), its visits, its wins, root visits, root children, nodes used,
+ * iterations done, 0.  Action code = seat << 10 | slot << 5 | identity.
+ * d_out: n_trees x 8 int32.
+ */
+int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream);
+
+/* Work counters of the forest since creation or the last call: d_out[0] =
+ * random words consumed by its playouts (each word is one uniform choice of
+ * the method: a draw, a joker position, a guess or a continue coin).  Copies
+ * then zeroes the counter, on `stream`.  d_out: one uint64. */
+int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream);
+
+/* Nodes of tree t in creation order, 4 int32 each: action, parent (-1 for
+ * the root), visits, wins.  d_out holds h_budgets[t] + 1 rows; rows past the
+ * nodes used are set to -1. */
+int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream);
+
+/* Test hook for the random-number generator: out[4k..4k+3] = Philox-4x32-10
+ * of counter d_ctr[4k..], key d_key[2k..], by this library's generator
+ * (use_reference = 0) or by cuRAND's device function (use_reference = 1). */
+int dvc_philox(dvc_ctx* ctx, int n, const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out,
+               int use_reference, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVC_H */

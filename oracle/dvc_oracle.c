@@ -536,6 +536,7 @@ static uint64_t advance(const detctx* d, int i, int* r, int* J, stream* rng, int
 static void place_jokers(const detctx* d, int k, int g, int c, int rr, int* J, int* jleft, stream* rng,
                          int jslot[3][MAXT]) {
     uint64_t opts = joker_close_mult(c, rr, *J);
+    if (opts == 0 || rr > 2) return; /* only for a view with no consistent deal */
     uint64_t z = pick64(next_word64(rng), opts);
     uint64_t perms = 1;
     for (int i = 0; i < rr; i++) perms *= (uint64_t)(*J - i);

@@ -1,0 +1,417 @@
+// dvc_device.cuh -- device-side game core of the Da Vinci Code MCTS engine
+// (arXiv 2403.10720): counter-based random streams, the packed game state,
+// the rules of Sec. II-A and the random playout of Sec. II-B.
+//
+// State lives in registers as tile bitmasks.  A hand's left-to-right order is
+// derived: numbered tiles by id, each joker after `gap` numbered tiles, two
+// jokers with the same gap ordered by one flag bit.  Every random choice is a
+// uniform index floor(w * n / 2^32) over a canonical enumeration, taken from
+// the next word of the playout's own Philox stream, so results depend only
+// on (seed, tree, iteration, playout) and never on thread placement.
+#pragma once
+#include <stdint.h>
+
+#include "../../include/dvc.h"
+
+namespace dvc {
+
+constexpr uint32_t kNumMask = 0x00FFFFFFu;  // numbered tiles 0..23
+constexpr uint32_t kJokerMask = 0x03000000u;
+constexpr uint32_t kNone = 0xFFu;
+constexpr uint32_t kTagInit = 1, kTagDet = 2, kTagTree = 3, kTagRoll = 4;
+
+// ------------------------------------------------------------------ Philox
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with the halves crossed and the round key xored in;
+// the key advances by the two Weyl constants between rounds.
+__device__ __forceinline__ void philox10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint32_t k0,
+                                         uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+        const uint32_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+        x0 = n0;
+        x1 = lo1;
+        x2 = n2;
+        x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// A stream: key (seed low word, tree), counter (block, j, i, tag word).  The
+// four words of a block are handed out in order through a small shift queue.
+struct Rng {
+    uint32_t k0, k1, blk, j, i, tw;
+    uint32_t w0, w1, w2, w3;
+    uint32_t left;   // words left in the queue
+    uint32_t count;  // words handed out (work statistics)
+
+    __device__ __forceinline__ void open(uint64_t seed, uint32_t tree, uint32_t jj, uint32_t ii, uint32_t tag) {
+        k0 = (uint32_t)seed;
+        k1 = tree;
+        blk = 0;
+        j = jj;
+        i = ii;
+        tw = tag + 16u * (uint32_t)(seed >> 32);
+        left = 0;
+        count = 0;
+    }
+    __device__ __forceinline__ void refill() {
+        uint32_t a = blk, b = j, c = i, d = tw;
+        philox10(a, b, c, d, k0, k1);
+        w0 = a;
+        w1 = b;
+        w2 = c;
+        w3 = d;
+        left = 4;
+        ++blk;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        if (left == 0) refill();
+        const uint32_t r = w0;
+        w0 = w1;
+        w1 = w2;
+        w2 = w3;
+        --left;
+        ++count;
+        return r;
+    }
+    __device__ __forceinline__ uint64_t next64() {
+        const uint64_t lo = next();
+        const uint64_t hi = next();
+        return (hi << 32) | lo;
+    }
+};
+
+__device__ __forceinline__ uint32_t pick(uint32_t w, uint32_t n) { return __umulhi(w, n); }
+__device__ __forceinline__ uint64_t pick64(uint64_t r, uint64_t n) { return __umul64hi(r, n); }
+
+// Index of the n-th (0-based) set bit of m; n < popc(m).
+__device__ __forceinline__ uint32_t nth_set(uint32_t m, uint32_t n) {
+    uint32_t pos = 0, c;
+    c = __popc(m & 0xFFFFu);
+    if (n >= c) { n -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xFFu);
+    if (n >= c) { n -= c; m >>= 8; pos += 8; }
+    c = __popc(m & 0xFu);
+    if (n >= c) { n -= c; m >>= 4; pos += 4; }
+    c = __popc(m & 0x3u);
+    if (n >= c) { n -= c; m >>= 2; pos += 2; }
+    c = m & 1u;
+    if (n >= c) pos += 1;
+    return pos;
+}
+
+// The k lowest set bits of m (k <= popc(m)).
+__device__ __forceinline__ uint32_t low_bits(uint32_t m, uint32_t k) {
+    if (k == 0) return 0u;
+    const uint32_t p = nth_set(m, k - 1);
+    return m & (p >= 31 ? 0xFFFFFFFFu : ((2u << p) - 1u));
+}
+
+// ------------------------------------------------------------------- state
+struct G {
+    uint32_t h0, h1, h2, h3;  // hands
+    uint32_t rev;
+    uint32_t jg0, jg1, jflag;  // joker gaps, white-first flag
+    uint32_t cur, drawn, alive, winner;
+    uint32_t np, tmask;
+
+    __device__ __forceinline__ uint32_t hand(uint32_t p) const {
+        uint32_t v = h0;
+        v = p == 1 ? h1 : v;
+        v = p == 2 ? h2 : v;
+        v = p == 3 ? h3 : v;
+        return v;
+    }
+    __device__ __forceinline__ void add(uint32_t p, uint32_t bits) {
+        h0 |= p == 0 ? bits : 0u;
+        h1 |= p == 1 ? bits : 0u;
+        h2 |= p == 2 ? bits : 0u;
+        h3 |= p == 3 ? bits : 0u;
+    }
+    __device__ __forceinline__ uint32_t pool() const { return tmask & ~(h0 | h1 | h2 | h3); }
+};
+
+// Load a record into registers.  Fields are clamped to their ranges (seats
+// 2..4, tiles of the variant, seat indices below the player count) so that a
+// malformed record can never index memory out of bounds; valid records pass
+// through unchanged.
+__device__ __forceinline__ G load_state(const dvc_state& s) {
+    G g;
+    g.np = (s.nplayers >= 2 && s.nplayers <= 4) ? s.nplayers : 2u;
+    g.tmask = s.ntiles >= 26 ? 0x03FFFFFFu : 0x00FFFFFFu;
+    g.h0 = s.hand[0] & g.tmask;
+    g.h1 = s.hand[1] & g.tmask;
+    g.h2 = g.np > 2 ? s.hand[2] & g.tmask : 0u;
+    g.h3 = g.np > 3 ? s.hand[3] & g.tmask : 0u;
+    g.rev = s.revealed & g.tmask;
+    g.jg0 = s.joker_gap[0] <= 24 ? s.joker_gap[0] : 24u;
+    g.jg1 = s.joker_gap[1] <= 24 ? s.joker_gap[1] : 24u;
+    g.jflag = s.flags & 1u;
+    g.cur = s.cur < g.np ? s.cur : 0u;
+    g.drawn = s.drawn < 26 ? s.drawn : kNone;
+    g.alive = s.alive & ((1u << g.np) - 1u);
+    g.winner = s.winner < g.np ? s.winner : kNone;
+    return g;
+}
+
+__device__ __forceinline__ void store_state(const G& g, dvc_state& s) {
+    s.hand[0] = g.h0;
+    s.hand[1] = g.h1;
+    s.hand[2] = g.h2;
+    s.hand[3] = g.h3;
+    s.revealed = g.rev;
+    s.joker_gap[0] = (uint8_t)g.jg0;
+    s.joker_gap[1] = (uint8_t)g.jg1;
+    s.flags = (uint8_t)g.jflag;
+    s.cur = (uint8_t)g.cur;
+    s.drawn = (uint8_t)g.drawn;
+    s.alive = (uint8_t)g.alive;
+    s.nplayers = (uint8_t)g.np;
+    s.ntiles = g.tmask == 0x03FFFFFFu ? 26 : 24;
+    s.winner = (uint8_t)g.winner;
+    s.pad[0] = s.pad[1] = s.pad[2] = 0;
+}
+
+// Sequence position of joker j (0 black, 1 white) within its owner's hand hp.
+__device__ __forceinline__ uint32_t joker_pos(const G& g, uint32_t hp, uint32_t j) {
+    const uint32_t gj = j ? g.jg1 : g.jg0, go = j ? g.jg0 : g.jg1;
+    const bool other_here = (hp >> (24u + (j ^ 1u))) & 1u;
+    // the other joker is first in a shared gap iff (flag ? other is white : other is black)
+    const bool other_first = g.jflag ? (j == 0) : (j == 1);
+    return gj + ((other_here && (go < gj || (go == gj && other_first))) ? 1u : 0u);
+}
+
+// Tile at sequence position s of hand p.
+__device__ __forceinline__ uint32_t seq_tile(const G& g, uint32_t p, uint32_t s) {
+    const uint32_t hp = g.hand(p);
+    const uint32_t jk = hp & kJokerMask;
+    if (!jk) return nth_set(hp, s);
+    uint32_t before = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < 2; ++j) {
+        if ((jk >> (24u + j)) & 1u) {
+            const uint32_t pj = joker_pos(g, hp, j);
+            if (pj == s) return 24u + j;
+            before += pj < s;
+        }
+    }
+    return nth_set(hp & kNumMask, s - before);
+}
+
+// Sequence position of tile t held in hand p.
+__device__ __forceinline__ uint32_t seq_pos(const G& g, uint32_t p, uint32_t t) {
+    const uint32_t hp = g.hand(p);
+    if (t >= 24u) return joker_pos(g, hp, t - 24u);
+    const uint32_t k = __popc(hp & kNumMask & ((1u << t) - 1u));
+    uint32_t pos = k;
+    if ((hp >> 24) & 1u) pos += g.jg0 <= k;
+    if ((hp >> 25) & 1u) pos += g.jg1 <= k;
+    return pos;
+}
+
+// Tile in the h-th face-down slot (left to right) of hand p.
+__device__ __forceinline__ uint32_t hidden_slot(const G& g, uint32_t p, uint32_t h) {
+    const uint32_t hp = g.hand(p);
+    const uint32_t hid = hp & ~g.rev;
+    const uint32_t hj = hid & kJokerMask;
+    const uint32_t hn = hid & kNumMask;
+    if (!hj) return nth_set(hn, h);
+    // face-down index of each face-down joker
+    uint32_t idx[2] = {0xFFu, 0xFFu};
+#pragma unroll
+    for (uint32_t j = 0; j < 2; ++j) {
+        if ((hj >> (24u + j)) & 1u) {
+            const uint32_t gj = j ? g.jg1 : g.jg0;
+            uint32_t n = __popc(hn & low_bits(hp & kNumMask, gj));
+            const uint32_t o = j ^ 1u;
+            if ((hj >> (24u + o)) & 1u) n += joker_pos(g, hp, o) < joker_pos(g, hp, j);
+            idx[j] = n;
+        }
+    }
+    if (idx[0] == h) return 24u;
+    if (idx[1] == h) return 25u;
+    const uint32_t skip = (idx[0] < h) + (idx[1] < h);
+    return nth_set(hn, h - skip);
+}
+
+// Sorted insertion of tile t into hand p (Sec. II-A).  Numbered: immediately
+// before the first larger numbered tile, so jokers of that gap stay left.
+// Joker: uniform over the len+1 insertion points (one word).
+__device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, Rng& r) {
+    const uint32_t hp = g.hand(p);
+    if (t < 24u) {
+        const uint32_t k = __popc(hp & kNumMask & ((1u << t) - 1u));
+        if ((hp >> 24) & 1u) g.jg0 += g.jg0 > k;
+        if ((hp >> 25) & 1u) g.jg1 += g.jg1 > k;
+    } else {
+        const uint32_t j = t - 24u, o = j ^ 1u;
+        const uint32_t pos = pick(r.next(), __popc(hp) + 1u);
+        uint32_t gap = pos, flag = 0u;
+        if ((hp >> (24u + o)) & 1u) {
+            const uint32_t po = joker_pos(g, hp, o);
+            const bool new_first = pos <= po;
+            gap = new_first ? pos : pos - 1u;
+            const uint32_t go = o ? g.jg1 : g.jg0;
+            if (gap == go) flag = (new_first ? j : o) == 1u ? 1u : 0u;
+        }
+        if (j) g.jg1 = gap; else g.jg0 = gap;
+        g.jflag = flag;
+    }
+    g.add(p, 1u << t);
+}
+
+__device__ __forceinline__ void draw(G& g, Rng& r) {
+    const uint32_t pool = g.pool();
+    if (!pool) {
+        g.drawn = kNone;
+        return;
+    }
+    const uint32_t t = nth_set(pool, pick(r.next(), __popc(pool)));
+    insert_tile(g, g.cur, t, r);
+    g.drawn = t;
+}
+
+__device__ __forceinline__ uint32_t next_alive(uint32_t alive, uint32_t cur, uint32_t np) {
+    const uint32_t dup = alive | (alive << np);
+    const uint32_t m = dup >> (cur + 1u);
+    const uint32_t q = cur + (uint32_t)__ffs(m);
+    return q >= np ? q - np : q;
+}
+
+enum : int { kTurnOver = 0, kGuessAgain = 1, kGameOver = 2 };
+
+// Resolve guess `x` at the tile `target` of seat q (Sec. II-A).  In a playout
+// a correct guess continues iff the next word < cont_thr; in the tree it ends
+// the turn (Sec. III-A, simplification 2).
+__device__ __forceinline__ int resolve(G& g, uint32_t q, uint32_t target, uint32_t x, bool in_tree, uint32_t cont_thr,
+                                       Rng& r) {
+    if (x == target) {
+        g.rev |= 1u << target;
+        if (!(g.hand(q) & ~g.rev)) g.alive &= ~(1u << q);
+        if (__popc(g.alive) == 1) {
+            g.winner = g.cur;
+            return kGameOver;
+        }
+        if (!in_tree && cont_thr != 0u && r.next() < cont_thr) return kGuessAgain;
+        return kTurnOver;
+    }
+    const uint32_t c = g.cur;
+    const uint32_t t = g.drawn != kNone ? g.drawn : hidden_slot(g, c, 0);
+    g.rev |= 1u << t;
+    if (!(g.hand(c) & ~g.rev)) g.alive &= ~(1u << c);
+    if (__popc(g.alive) == 1) {
+        g.winner = (uint32_t)__ffs(g.alive) - 1u;
+        return kGameOver;
+    }
+    return kTurnOver;
+}
+
+__device__ __forceinline__ void next_turn(G& g, Rng& r) {
+    g.cur = next_alive(g.alive, g.cur, g.np);
+    draw(g, r);
+}
+
+// A uniform random guess among the legal ones (canonical order: opponents
+// from cur+1, face-down slots left to right, identities ascending; the set is
+// the product of face-down slots and identities outside own hand and face-up).
+__device__ __forceinline__ int random_guess(G& g, Rng& r, uint32_t cont_thr) {
+    const uint32_t U = g.tmask & ~g.hand(g.cur) & ~g.rev;
+    const uint32_t nid = __popc(U);
+    uint32_t cnt[3], qs[3], nslots = 0;
+#pragma unroll
+    for (uint32_t off = 1; off < 4; ++off) {
+        uint32_t q = g.cur + off;
+        q = q >= g.np ? q - g.np : q;
+        const uint32_t c = (off < g.np) ? __popc(g.hand(q) & ~g.rev) : 0u;
+        cnt[off - 1] = c;
+        qs[off - 1] = q;
+        nslots += c;
+    }
+    const uint32_t k = pick(r.next(), nslots * nid);
+    uint32_t s = k / nid;
+    const uint32_t i = k - s * nid;
+    uint32_t q = qs[0];
+    if (s >= cnt[0]) {
+        s -= cnt[0];
+        q = qs[1];
+        if (s >= cnt[1]) {
+            s -= cnt[1];
+            q = qs[2];
+        }
+    }
+    const uint32_t target = hidden_slot(g, q, s);
+    const uint32_t x = nth_set(U, i);
+    return resolve(g, q, target, x, false, cont_thr, r);
+}
+
+// One playout to the end (Sec. II-B); returns the winner.  Every guess turns
+// one tile face up, so a game has at most 26 guesses; the cap only stops a
+// malformed record (result kNone, credited to nobody).
+__device__ __forceinline__ uint32_t playout(G g, Rng& r, uint32_t cont_thr) {
+    for (int guard = 0; guard < 128; ++guard) {
+        const int res = random_guess(g, r, cont_thr);
+        if (res == kGameOver) return g.winner;
+        if (res == kTurnOver) next_turn(g, r);
+    }
+    return kNone;
+}
+
+// Is action (q, slot s, identity x) legal for the seat to move?
+__device__ __forceinline__ bool guess_legal(const G& g, uint32_t q, uint32_t s, uint32_t x) {
+    if (q == g.cur || q >= g.np || !((g.alive >> q) & 1u)) return false;
+    const uint32_t hq = g.hand(q);
+    if (s >= (uint32_t)__popc(hq)) return false;
+    if ((g.rev >> seq_tile(g, q, s)) & 1u) return false;
+    if (!((g.tmask >> x) & 1u)) return false;
+    if (((g.hand(g.cur) | g.rev) >> x) & 1u) return false;
+    return true;
+}
+
+// In-tree transition for action code (q << 10 | s << 5 | x): resolve with no
+// extra guess, then the next seat draws on the tree stream.
+__device__ __forceinline__ void tree_apply(G& g, uint32_t code, Rng& tr) {
+    const uint32_t q = code >> 10, s = (code >> 5) & 31u, x = code & 31u;
+    const uint32_t target = seq_tile(g, q, s);
+    if (resolve(g, q, target, x, true, 0u, tr) != kGameOver) next_turn(g, tr);
+}
+
+__device__ __forceinline__ uint32_t canon_rank(uint32_t code, uint32_t cur, uint32_t np) {
+    const uint32_t q = code >> 10;
+    uint32_t d = q + np - cur - 1u;
+    d = d >= np ? d - np : d;
+    return (d << 10) | (code & 1023u);
+}
+
+// ------------------------------------------------------------------- UCT
+// ln(x), x >= 1: x = m 2^e with m in [sqrt(1/2), sqrt(2)); ln x = e ln2 +
+// 2 atanh(z), z = (m-1)/(m+1), by the atanh series up to z^23 in Horner form.
+// Every operation is an explicitly rounded IEEE double op (no contraction).
+__device__ __forceinline__ double ln_series(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((bits >> 52) & 0x7FFull) - 1023;
+    double m = __longlong_as_double((long long)((bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+    if (m > 1.4142135623730951) {
+        m = __dmul_rn(m, 0.5);
+        e += 1;
+    }
+    const double z = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double z2 = __dmul_rn(z, z);
+    double p = __ddiv_rn(1.0, 23.0);
+#pragma unroll
+    for (int k = 10; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z2), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    const double lnm = __dmul_rn(2.0, __dmul_rn(z, p));
+    return __dadd_rn(__dmul_rn((double)e, 0.6931471805599453), lnm);
+}
+
+// UCB1 score: wins/n + (c sqrt(ln N)) * (1/sqrt(n)).
+__device__ __forceinline__ double uct_score(double c_sqrt_lnN, int32_t w, int32_t n) {
+    const double mean = __ddiv_rn((double)w, (double)n);
+    const double rs = __ddiv_rn(1.0, __dsqrt_rn((double)n));
+    return __dadd_rn(mean, __dmul_rn(c_sqrt_lnN, rs));
+}
+
+}  // namespace dvc

@@ -1,0 +1,901 @@
+// dvc_lib.cu -- kernels and the C ABI of libdvc (see include/dvc.h).
+#include <cuda_runtime.h>
+#include <curand_philox4x32_x.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dvc_tree.cuh"
+
+using namespace dvc;
+
+struct dvc_ctx {
+    dvc_config cfg;
+    int device;
+    std::string err;
+    int32_t* d_flags;  // [0]: latched error code (0 = none)
+    unsigned long long* d_ws;  // determinization workspace
+    size_t ws_cells;
+};
+
+struct dvc_forest {
+    dvc_ctx* ctx;
+    int n;
+    uint64_t seed;
+    std::vector<int32_t> h_budgets;
+    dvc_state* roots;
+    TreeMeta* meta;
+    DetPlan* plans;
+    unsigned long long* tables;
+    Node* nodes;
+    int32_t* link;
+    int32_t* created;
+    long long total_slots;
+    uint32_t table_cap;
+    // split-step state
+    Descent* work;
+    int32_t* paths;   // n x 20
+    uint8_t* movers;  // n x 20
+    dvc_state* leaves;
+    uint32_t* leaf_tree;
+    uint32_t* leaf_iter;
+    unsigned long long* d_words;
+    int32_t* export_scratch;
+    int32_t export_cap;
+};
+
+namespace {
+
+constexpr int kPathMax = 20;
+constexpr int kDetChunk = 256;
+
+int fail(dvc_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(dvc_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, DVC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+__device__ __forceinline__ void latch(int32_t* flags, int32_t code) { atomicCAS(&flags[0], 0, code); }
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void philox_kernel(int n, const uint32_t* ctr, const uint32_t* key, uint32_t* out, int ref) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t a = ctr[4 * i], b = ctr[4 * i + 1], c = ctr[4 * i + 2], d = ctr[4 * i + 3];
+    if (ref) {
+        uint4 cc = make_uint4(a, b, c, d);
+        uint2 kk = make_uint2(key[2 * i], key[2 * i + 1]);
+        uint4 r = curand_Philox4x32_10(cc, kk);
+        a = r.x; b = r.y; c = r.z; d = r.w;
+    } else {
+        philox10(a, b, c, d, key[2 * i], key[2 * i + 1]);
+    }
+    out[4 * i] = a;
+    out[4 * i + 1] = b;
+    out[4 * i + 2] = c;
+    out[4 * i + 3] = d;
+}
+
+// Root generation: deal, random history of d draws, then the mover draws.
+__global__ void init_kernel(dvc_config cfg, uint64_t seed, int n, dvc_state* out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    Rng r;
+    r.open(seed, (uint32_t)idx, 0u, 0u, kTagInit);
+    const uint32_t np = (uint32_t)cfg.nplayers;
+    const uint32_t tmask = cfg.ntiles >= 26 ? 0x03FFFFFFu : 0x00FFFFFFu;
+    for (int attempt = 0; attempt < 16; ++attempt) {
+        G g;
+        g.h0 = g.h1 = g.h2 = g.h3 = 0u;
+        g.rev = 0u;
+        g.jg0 = g.jg1 = g.jflag = 0u;
+        g.drawn = kNone;
+        g.alive = (1u << np) - 1u;
+        g.winner = kNone;
+        g.np = np;
+        g.tmask = tmask;
+        for (uint32_t p = 0; p < np; ++p) {
+            g.cur = p;
+            for (int d = 0; d < cfg.deal; ++d) draw(g, r);
+        }
+        g.drawn = kNone;
+        g.cur = 0;
+        uint32_t target = pick(r.next(), (uint32_t)cfg.max_predraw + 1u);
+        const bool last = attempt == 15;
+        if (last) target = 0;
+        uint32_t draws = 0;
+        bool over = false;
+        while (draws < target && g.pool()) {
+            draw(g, r);
+            ++draws;
+            for (;;) {
+                const int res = random_guess(g, r, cfg.cont_thr);
+                if (res == kGameOver) {
+                    over = true;
+                    break;
+                }
+                if (res == kTurnOver) break;
+            }
+            if (over) break;
+            g.cur = next_alive(g.alive, g.cur, np);
+        }
+        if (over) continue;
+        bool bad = false;
+        for (uint32_t p = 0; p < np; ++p) bad |= __popc(g.hand(p) & g.rev) > cfg.max_revealed;
+        if (bad && !last) continue;
+        draw(g, r);
+        store_state(g, out[idx]);
+        return;
+    }
+}
+
+// One thread per root: plan, fill its table in a private workspace slot, sample.
+__global__ void determinize_kernel(const dvc_state* roots, int n, int observer, uint64_t seed,
+                                   const uint32_t* tree_ids, const uint32_t* iter_ids, dvc_state* out,
+                                   unsigned long long* ws, int32_t* flags) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const G g = load_state(roots[idx]);
+    const uint32_t obs = observer < 0 ? g.cur : (uint32_t)observer;
+    DetPlan pl;
+    det_plan(g, obs, pl);
+    if (!pl.ok) {
+        latch(flags, DVC_E_UNSUPPORTED);
+        out[idx] = roots[idx];
+        return;
+    }
+    unsigned long long* F = ws + (size_t)(idx % kDetChunk) * kDetMaxCells;
+    det_fill(pl, F, 0u, 1u, [] {});
+    Rng r;
+    r.open(seed, tree_ids[idx], 0u, iter_ids[idx], kTagDet);
+    G o;
+    det_sample(pl, F, g, r, o);
+    store_state(o, out[idx]);
+}
+
+// Leaf-parallel playouts: thread -> (leaf, playout).  Win counts are summed
+// with integer atomics, so the result is independent of scheduling.
+__global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uint64_t seed,
+                               const uint32_t* tree_ids, const uint32_t* leaf_ids, uint32_t cont_thr, int32_t* wins,
+                               unsigned long long* words) {
+    const long long total = (long long)n_leaves * P;
+    unsigned long long my_words = 0ull;
+    for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
+         gid += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(gid / P);
+        const int j = (int)(gid - (long long)l * P);
+        const dvc_state ls = leaves[l];
+        uint32_t winner;
+        if (ls.winner != kNone) {
+            winner = ls.winner;
+        } else {
+            const G g = load_state(ls);
+            Rng r;
+            r.open(seed, tree_ids[l], (uint32_t)j, leaf_ids[l], kTagRoll);
+            winner = playout(g, r, cont_thr);
+            my_words += r.count;
+        }
+        if (winner < 4u) atomicAdd(&wins[4 * l + (int)winner], 1);
+    }
+    if (words) {
+        const unsigned long long s = warp_sum_u64(my_words);
+        if ((threadIdx.x & 31u) == 0 && s) atomicAdd(words, s);
+    }
+}
+
+struct ForestDev {
+    const dvc_state* roots;
+    TreeMeta* meta;
+    const DetPlan* plans;
+    const unsigned long long* tables;
+    Node* nodes;
+    int32_t* link;
+    int32_t* created;
+    int32_t* flags;
+    unsigned long long* words;
+};
+
+// Fused search step: one CTA per tree.  Warp 0 determinizes, descends and
+// expands; every thread of the CTA runs playouts of the leaf; warp 0
+// backpropagates.  The table of small views is staged in shared memory.
+__global__ void mcts_fused_kernel(ForestDev F, SearchParams sp, int n_iter, uint32_t smem_cells) {
+    extern __shared__ unsigned long long s_tab[];
+    __shared__ DetPlan s_pl;
+    __shared__ dvc_state s_leaf;
+    __shared__ int32_t s_path[kPathMax];
+    __shared__ uint8_t s_mover[kPathMax];
+    __shared__ int32_t s_np;
+    __shared__ int32_t s_wins[4];
+    __shared__ uint32_t s_E[104];
+    __shared__ int32_t s_stop;
+
+    const int t = blockIdx.x;
+    TreeMeta tm = F.meta[t];
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (tid == 0) s_pl = F.plans[t];
+    __syncthreads();
+    const unsigned long long* tab = F.tables + tm.table_off;
+    if (s_pl.cells <= smem_cells) {
+        for (uint32_t c = tid; c < s_pl.cells; c += blockDim.x) s_tab[c] = tab[c];
+        tab = s_tab;
+    }
+    __syncthreads();
+    Node* nodes = F.nodes + tm.node_off;
+    int32_t* link = F.link + tm.node_off;
+    int32_t* created = F.created + tm.node_off;
+    const G root = load_state(F.roots[t]);
+    const uint32_t obs = root.cur;
+    int32_t next_free = tm.next_free;
+    int32_t used = tm.used;
+    const int32_t it0 = tm.done;
+    const int32_t it1 = (s_pl.ok && s_pl.total && !tm.failed) ? min(tm.budget, it0 + n_iter) : it0;
+    unsigned long long words = 0ull;
+    int32_t it = it0;
+    for (; it < it1; ++it) {
+        if (warp == 0) {
+            Rng dr;
+            dr.open(sp.seed, tm.tree_id, 0u, (uint32_t)it, kTagDet);
+            G det;
+            det_sample(s_pl, tab, root, dr, det);
+            Descent d;
+            descend(det, obs, nodes, link, tm, sp, (uint32_t)it, s_path, s_mover, s_E, d);
+            bool ok = true;
+            if (d.found)
+                ok = expand_child(d, nodes, link, created, tm, next_free, used, (uint32_t)it, s_path, s_mover);
+            if (lane == 0) {
+                s_stop = ok ? 0 : 1;
+                s_np = d.np;
+                store_state(d.s, s_leaf);
+                s_wins[0] = s_wins[1] = s_wins[2] = s_wins[3] = 0;
+                if (!ok) latch(F.flags, DVC_E_OOM);
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        if (s_leaf.winner != kNone) {
+            if (tid == 0 && s_leaf.winner < 4) s_wins[s_leaf.winner] = sp.playouts;
+        } else {
+            const G g = load_state(s_leaf);
+            uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+            for (int j = (int)tid; j < sp.playouts; j += (int)blockDim.x) {
+                Rng r;
+                r.open(sp.seed, tm.tree_id, (uint32_t)j, (uint32_t)it, kTagRoll);
+                const uint32_t w = playout(g, r, sp.cont_thr);
+                c0 += w == 0;
+                c1 += w == 1;
+                c2 += w == 2;
+                c3 += w == 3;
+                words += r.count;
+            }
+            c0 = __reduce_add_sync(0xFFFFFFFFu, c0);
+            c1 = __reduce_add_sync(0xFFFFFFFFu, c1);
+            c2 = __reduce_add_sync(0xFFFFFFFFu, c2);
+            c3 = __reduce_add_sync(0xFFFFFFFFu, c3);
+            if (lane == 0) {
+                if (c0) atomicAdd(&s_wins[0], (int)c0);
+                if (c1) atomicAdd(&s_wins[1], (int)c1);
+                if (c2) atomicAdd(&s_wins[2], (int)c2);
+                if (c3) atomicAdd(&s_wins[3], (int)c3);
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            backprop(nodes, s_path, s_mover, s_np, s_wins, sp.playouts);
+            __syncwarp();
+        }
+    }
+    if (tid == 0) {
+        F.meta[t].done = it;
+        F.meta[t].next_free = next_free;
+        F.meta[t].used = used;
+        if (s_stop && it < it1) F.meta[t].failed = 1;
+    }
+    if (F.words) {
+        const unsigned long long s = warp_sum_u64(words);
+        if (lane == 0 && s) atomicAdd(F.words, s);
+    }
+}
+
+// Split steps: one warp per tree for select and expand, results kept in
+// global memory between launches.
+__global__ void mcts_select_kernel(ForestDev F, SearchParams sp, int n, Descent* work, int32_t* paths,
+                                   uint8_t* movers) {
+    __shared__ uint32_t s_E[4][104];
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t wl = (threadIdx.x >> 5) & 3u;
+    if (t >= n) return;
+    const TreeMeta tm = F.meta[t];
+    Descent& d = work[t];
+    const uint32_t lane = threadIdx.x & 31u;
+    if (tm.done >= tm.budget || tm.failed || !F.plans[t].ok || !F.plans[t].total) {
+        if (lane == 0) d.np = -1;
+        return;
+    }
+    const G root = load_state(F.roots[t]);
+    Rng dr;
+    dr.open(sp.seed, tm.tree_id, 0u, (uint32_t)tm.done, kTagDet);
+    G det;
+    det_sample(F.plans[t], F.tables + tm.table_off, root, dr, det);
+    Descent dd;
+    descend(det, root.cur, F.nodes + tm.node_off, F.link + tm.node_off, tm, sp, (uint32_t)tm.done,
+            paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, s_E[wl], dd);
+    if (lane == 0) d = dd;
+}
+
+__global__ void mcts_expand_kernel(ForestDev F, int n, Descent* work, int32_t* paths, uint8_t* movers,
+                                   dvc_state* leaves, uint32_t* leaf_tree, uint32_t* leaf_iter) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= n) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    TreeMeta& tmr = F.meta[t];
+    const TreeMeta tm = tmr;
+    Descent d = work[t];
+    if (d.np < 0) {
+        if (lane == 0) {
+            dvc_state s = {};
+            s.winner = 0xFE;
+            leaves[t] = s;
+            leaf_tree[t] = tm.tree_id;
+            leaf_iter[t] = (uint32_t)tm.done;
+        }
+        return;
+    }
+    int32_t next_free = tm.next_free;
+    int32_t used = tm.used;
+    bool ok = true;
+    if (d.found)
+        ok = expand_child(d, F.nodes + tm.node_off, F.link + tm.node_off, F.created + tm.node_off, tm, next_free,
+                          used, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax);
+    if (lane == 0) {
+        tmr.next_free = next_free;
+        tmr.used = used;
+        if (!ok) {
+            tmr.failed = 1;
+            latch(F.flags, DVC_E_OOM);
+            d.np = -1;
+        }
+        work[t] = d;
+        dvc_state s;
+        store_state(d.s, s);
+        if (!ok) s.winner = 0xFE;
+        leaves[t] = s;
+        leaf_tree[t] = tm.tree_id;
+        leaf_iter[t] = (uint32_t)tm.done;
+    }
+}
+
+__global__ void mcts_backprop_kernel(ForestDev F, SearchParams sp, int n, const Descent* work, const int32_t* paths,
+                                     const uint8_t* movers, const int32_t* wins) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= n) return;
+    const Descent& d = work[t];
+    if (d.np < 0) return;
+    TreeMeta& tm = F.meta[t];
+    backprop(F.nodes + tm.node_off, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, d.np,
+             wins + 4 * t, sp.playouts);
+    __syncwarp();
+    if ((threadIdx.x & 31u) == 0) tm.done += 1;
+}
+
+__global__ void root_stats_kernel(ForestDev F, int n, int32_t* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const TreeMeta tm = F.meta[t];
+    const Node* nodes = F.nodes + tm.node_off;
+    const G root = load_state(F.roots[t]);
+    const Node r = nodes[0];
+    const uint32_t nchild = (r.meta >> 12) & 0xFFFu;
+    int32_t best = -1, bv = 0, bw = 0;
+    uint32_t brank = 0xFFFFFFFFu;
+    int32_t blk = r.child;
+    uint32_t seen = 0, k = 0;
+    while (seen < nchild) {
+        const uint32_t size = block_size(k, true, (uint32_t)tm.root_legal);
+        const uint32_t cnt = min(size, nchild - seen);
+        for (uint32_t e = 0; e < cnt; ++e) {
+            const Node c = nodes[blk + (int32_t)e];
+            const uint32_t code = c.meta & 0xFFFu;
+            const uint32_t rk = canon_rank(code, root.cur, root.np);
+            if (best < 0 || c.visits > bv || (c.visits == bv && rk < brank)) {
+                best = (int32_t)code;
+                bv = c.visits;
+                bw = c.wins;
+                brank = rk;
+            }
+        }
+        seen += cnt;
+        ++k;
+        if (seen < nchild) blk = F.link[tm.node_off + blk];
+    }
+    int32_t* o = out + 8 * t;
+    o[0] = best;
+    o[1] = bv;
+    o[2] = bw;
+    o[3] = r.visits;
+    o[4] = (int32_t)nchild;
+    o[5] = tm.used;
+    o[6] = tm.done;
+    o[7] = tm.failed;
+}
+
+// Export of one tree in creation order (row 0 = root).  Nodes carry the
+// iteration that created them; at most one node is created per iteration, so
+// a node's row is 1 + the number of iterations before its own that created a
+// node.  iter_rank holds one int per iteration of the tree's budget.
+__global__ void export_flag_kernel(ForestDev F, int t, int32_t* iter_rank) {
+    const TreeMeta tm = F.meta[t];
+    const int32_t* created = F.created + tm.node_off;
+    for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < tm.next_free; s += gridDim.x * blockDim.x)
+        if (s > 0 && created[s] >= 0) iter_rank[created[s]] = 1;
+}
+
+__global__ void export_scan_kernel(int32_t n, int32_t* iter_rank) {
+    int32_t acc = 1;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t f = iter_rank[i];
+        iter_rank[i] = f ? acc : -1;
+        acc += f;
+    }
+}
+
+__global__ void export_rows_kernel(ForestDev F, int t, const int32_t* iter_rank, int32_t rows, int32_t* out) {
+    const TreeMeta tm = F.meta[t];
+    const Node* nodes = F.nodes + tm.node_off;
+    const int32_t* link = F.link + tm.node_off;
+    const int32_t* created = F.created + tm.node_off;
+    for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < tm.next_free; p += gridDim.x * blockDim.x) {
+        if (p != 0 && created[p] < 0) continue;
+        const int32_t prow = p == 0 ? 0 : iter_rank[created[p]];
+        const Node nd = nodes[p];
+        if (prow < rows) {
+            out[4 * prow + 0] = p == 0 ? 0 : (int32_t)(nd.meta & 0xFFFu);
+            if (p == 0) out[1] = -1;
+            out[4 * prow + 2] = nd.visits;
+            out[4 * prow + 3] = nd.wins;
+        }
+        const uint32_t nchild = (nd.meta >> 12) & 0xFFFu;
+        int32_t blk = nd.child;
+        uint32_t seen = 0, k = 0;
+        while (seen < nchild) {
+            const uint32_t size = block_size(k, p == 0, (uint32_t)tm.root_legal);
+            const uint32_t cnt = min(size, nchild - seen);
+            for (uint32_t e = 0; e < cnt; ++e) {
+                const int32_t crow = iter_rank[created[blk + (int32_t)e]];
+                if (crow < rows) out[4 * crow + 1] = prow;
+            }
+            seen += cnt;
+            ++k;
+            if (seen < nchild) blk = link[blk];
+        }
+    }
+}
+
+// (Re)initialise every tree: optionally take new roots, plan the root view's
+// determinization and fill its counting table (one warp per tree), count the
+// root's legal guesses, and reset the tree to a lone root.
+__global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_roots, DetPlan* plans,
+                                   unsigned long long* tables, uint32_t table_cap) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (t >= n) return;
+    dvc_state* roots = const_cast<dvc_state*>(F.roots);
+    if (new_roots && lane == 0) roots[t] = new_roots[t];
+    __syncwarp();
+    const G g = load_state(roots[t]);
+    DetPlan& pl = plans[t];
+    if (lane == 0) {
+        det_plan(g, g.cur, pl);
+        pl.ok = pl.cells <= table_cap ? 1u : 0u;
+    }
+    __syncwarp();
+    TreeMeta& tm = F.meta[t];
+    if (pl.ok) det_fill(pl, tables + tm.table_off, lane, 32u, [] { __syncwarp(); });
+    if (lane == 0) {
+        const bool usable = pl.ok && pl.total != 0ull;
+        if (!pl.ok) latch(F.flags, DVC_E_UNSUPPORTED);
+        else if (!pl.total) latch(F.flags, DVC_E_INVALID);
+        const uint32_t U = g.tmask & ~g.hand(g.cur) & ~g.rev;
+        uint32_t slots = 0;
+        for (uint32_t q = 0; q < g.np; ++q)
+            if (q != g.cur && ((g.alive >> q) & 1u)) slots += __popc(g.hand(q) & ~g.rev);
+        tm.root_legal = (int32_t)(slots * __popc(U));
+        tm.done = 0;
+        tm.next_free = 1;
+        tm.used = 1;
+        tm.failed = usable ? 0 : 1;
+        Node* nodes = F.nodes + tm.node_off;
+        Node r;
+        r.visits = 0;
+        r.wins = 0;
+        r.child = -1;
+        r.meta = 0u;
+        nodes[0] = r;
+        F.link[tm.node_off] = -1;
+        F.created[tm.node_off] = -1;
+    }
+}
+
+ForestDev dev_of(dvc_forest* f) {
+    ForestDev d;
+    d.roots = f->roots;
+    d.meta = f->meta;
+    d.plans = f->plans;
+    d.tables = f->tables;
+    d.nodes = f->nodes;
+    d.link = f->link;
+    d.created = f->created;
+    d.flags = f->ctx->d_flags;
+    d.words = f->d_words;
+    return d;
+}
+
+SearchParams params_of(const dvc_forest* f) {
+    SearchParams sp;
+    sp.seed = f->seed;
+    sp.c_uct = f->ctx->cfg.c_uct;
+    sp.d_max = f->ctx->cfg.d_max;
+    sp.playouts = f->ctx->cfg.playouts;
+    sp.cont_thr = f->ctx->cfg.cont_thr;
+    return sp;
+}
+
+int check_launch(dvc_ctx* c, const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return DVC_OK;
+}
+
+int set_device(dvc_ctx* c) {
+    const cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return DVC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int dvc_create(dvc_ctx** out, const dvc_config* cfg, int device) {
+    if (!out || !cfg) return DVC_E_INVALID;
+    *out = nullptr;
+    if (cfg->nplayers < 2 || cfg->nplayers > 4) return DVC_E_INVALID;
+    if (cfg->ntiles != 24 && cfg->ntiles != 26) return DVC_E_INVALID;
+    if (cfg->deal < 1 || cfg->nplayers * cfg->deal >= cfg->ntiles) return DVC_E_INVALID;
+    if (cfg->max_predraw < 0 || cfg->max_predraw > 24 || cfg->max_revealed < 0) return DVC_E_INVALID;
+    if (cfg->d_max < 0 || cfg->d_max > kPathMax - 2 || cfg->playouts < 1 || cfg->playouts > (1 << 20))
+        return DVC_E_INVALID;
+    if (!(cfg->c_uct >= 0.0)) return DVC_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DVC_E_CUDA;
+    }
+    dvc_ctx* c = new (std::nothrow) dvc_ctx();
+    if (!c) return DVC_E_OOM;
+    c->cfg = *cfg;
+    c->device = device;
+    c->d_flags = nullptr;
+    c->d_ws = nullptr;
+    c->ws_cells = 0;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c->d_flags, 16) != cudaSuccess ||
+        cudaMemset(c->d_flags, 0, 16) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->d_flags) cudaFree(c->d_flags);
+        delete c;
+        return DVC_E_CUDA;
+    }
+    *out = c;
+    return DVC_OK;
+}
+
+void dvc_destroy(dvc_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->d_flags) cudaFree(c->d_flags);
+    if (c->d_ws) cudaFree(c->d_ws);
+    delete c;
+}
+
+const char* dvc_last_error(const dvc_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int dvc_check(dvc_ctx* c) {
+    if (!c) return DVC_E_INVALID;
+    if (int rc = set_device(c)) return rc;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "dvc_check");
+    int32_t flag = 0;
+    e = cudaMemcpy(&flag, c->d_flags, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dvc_check");
+    if (flag) {
+        cudaMemset(c->d_flags, 0, 16);
+        return fail(c, flag, "a kernel latched error " + std::to_string(flag));
+    }
+    return DVC_OK;
+}
+
+int dvc_philox(dvc_ctx* c, int n, const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, int use_reference,
+               void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (n < 0) return fail(c, DVC_E_INVALID, "dvc_philox: n < 0");
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_ctr) || !is_device_ptr(d_key) || !is_device_ptr(d_out))
+        return fail(c, DVC_E_INVALID, "dvc_philox: pointers must be device memory");
+    if (int rc = set_device(c)) return rc;
+    philox_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, d_ctr, d_key, d_out, use_reference);
+    return check_launch(c, "philox_kernel");
+}
+
+int dvc_init_states(dvc_ctx* c, uint64_t seed, int n, dvc_state* d_states, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (n < 0) return fail(c, DVC_E_INVALID, "dvc_init_states: n < 0");
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_states)) return fail(c, DVC_E_INVALID, "dvc_init_states: d_states must be device memory");
+    if (int rc = set_device(c)) return rc;
+    init_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(c->cfg, seed, n, d_states);
+    return check_launch(c, "init_kernel");
+}
+
+int dvc_determinize(dvc_ctx* c, const dvc_state* d_roots, int n, int observer, uint64_t seed,
+                    const uint32_t* d_tree_ids, const uint32_t* d_iter_ids, dvc_state* d_out, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (n < 0 || observer >= c->cfg.nplayers) return fail(c, DVC_E_INVALID, "dvc_determinize: bad n or observer");
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_roots) || !is_device_ptr(d_tree_ids) || !is_device_ptr(d_iter_ids) ||
+        !is_device_ptr(d_out))
+        return fail(c, DVC_E_INVALID, "dvc_determinize: pointers must be device memory");
+    if (d_roots == d_out) return fail(c, DVC_E_INVALID, "dvc_determinize: d_out may not alias d_roots");
+    if (int rc = set_device(c)) return rc;
+    if (!c->d_ws) {
+        const size_t cells = (size_t)kDetChunk * kDetMaxCells;
+        if (cudaMalloc(&c->d_ws, cells * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            c->d_ws = nullptr;
+            return fail(c, DVC_E_OOM, "dvc_determinize: workspace");
+        }
+        c->ws_cells = cells;
+    }
+    for (int base = 0; base < n; base += kDetChunk) {
+        const int m = std::min(kDetChunk, n - base);
+        determinize_kernel<<<(m + 63) / 64, 64, 0, (cudaStream_t)stream>>>(
+            d_roots + base, m, observer, seed, d_tree_ids + base, d_iter_ids + base, d_out + base, c->d_ws,
+            c->d_flags);
+        if (int rc = check_launch(c, "determinize_kernel")) return rc;
+    }
+    return DVC_OK;
+}
+
+int dvc_rollout_batch(dvc_ctx* c, const dvc_state* d_leaves, int n_leaves, int playouts_per_leaf, uint64_t seed,
+                      const uint32_t* d_tree_ids, const uint32_t* d_leaf_ids, int32_t* d_wins, uint64_t* d_words,
+                      void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (n_leaves < 0 || playouts_per_leaf < 1) return fail(c, DVC_E_INVALID, "dvc_rollout_batch: bad sizes");
+    if (n_leaves == 0) return DVC_OK;
+    if (!is_device_ptr(d_leaves) || !is_device_ptr(d_tree_ids) || !is_device_ptr(d_leaf_ids) ||
+        !is_device_ptr(d_wins) || (d_words && !is_device_ptr(d_words)))
+        return fail(c, DVC_E_INVALID, "dvc_rollout_batch: pointers must be device memory");
+    if (int rc = set_device(c)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_wins, 0, sizeof(int32_t) * 4 * (size_t)n_leaves, st);
+    if (e == cudaSuccess && d_words) e = cudaMemsetAsync(d_words, 0, sizeof(uint64_t), st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dvc_rollout_batch memset");
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const long long total = (long long)n_leaves * playouts_per_leaf;
+    const int block = 256;
+    long long blocks = (total + block - 1) / block;
+    blocks = std::min<long long>(blocks, (long long)dev_sms * 64);
+    rollout_kernel<<<(unsigned)blocks, block, 0, st>>>(d_leaves, n_leaves, playouts_per_leaf, seed, d_tree_ids,
+                                                       d_leaf_ids, c->cfg.cont_thr, d_wins,
+                                                       (unsigned long long*)d_words);
+    return check_launch(c, "rollout_kernel");
+}
+
+void dvc_forest_destroy(dvc_forest* f) {
+    if (!f) return;
+    cudaSetDevice(f->ctx->device);
+    void* ptrs[] = {f->roots,  f->meta,   f->plans,     f->tables,    f->nodes,   f->link,
+                    f->created, f->work,  f->paths,     f->movers,    f->leaves,  f->leaf_tree,
+                    f->leaf_iter, f->d_words, f->export_scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete f;
+}
+
+int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t* h_budgets,
+                      const uint32_t* h_tree_ids, uint64_t seed, dvc_forest** out, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (!out || n < 1 || !h_budgets) return fail(c, DVC_E_INVALID, "dvc_forest_create: bad arguments");
+    *out = nullptr;
+    if (!is_device_ptr(d_roots)) return fail(c, DVC_E_INVALID, "dvc_forest_create: d_roots must be device memory");
+    for (int i = 0; i < n; ++i)
+        if (h_budgets[i] < 0 || h_budgets[i] > (1 << 24))
+            return fail(c, DVC_E_INVALID, "dvc_forest_create: budgets must be in 0..2^24");
+    if (int rc = set_device(c)) return rc;
+    dvc_forest* f = new (std::nothrow) dvc_forest();
+    if (!f) return fail(c, DVC_E_OOM, "dvc_forest_create: host allocation");
+    f->h_budgets.assign(h_budgets, h_budgets + n);
+    f->ctx = c;
+    f->n = n;
+    f->seed = seed;
+    f->table_cap = c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<TreeMeta> hm(n);
+    long long slots = 0;
+    for (int t = 0; t < n; ++t) {
+        TreeMeta& m = hm[t];
+        std::memset(&m, 0, sizeof(m));
+        m.node_off = slots;
+        m.table_off = (long long)t * f->table_cap;
+        m.cap = 1 + kRootReserve + 4 * f->h_budgets[t];
+        m.budget = f->h_budgets[t];
+        m.tree_id = h_tree_ids ? h_tree_ids[t] : (uint32_t)t;
+        slots += m.cap;
+    }
+    f->total_slots = slots;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        return true;
+    };
+    const bool ok =
+        alloc((void**)&f->roots, sizeof(dvc_state) * n) && alloc((void**)&f->meta, sizeof(TreeMeta) * n) &&
+        alloc((void**)&f->plans, sizeof(DetPlan) * n) && alloc((void**)&f->work, sizeof(Descent) * n) &&
+        alloc((void**)&f->paths, sizeof(int32_t) * kPathMax * n) && alloc((void**)&f->movers, kPathMax * (size_t)n) &&
+        alloc((void**)&f->leaves, sizeof(dvc_state) * n) && alloc((void**)&f->leaf_tree, sizeof(uint32_t) * n) &&
+        alloc((void**)&f->leaf_iter, sizeof(uint32_t) * n) && alloc((void**)&f->d_words, sizeof(unsigned long long)) &&
+        alloc((void**)&f->tables, sizeof(unsigned long long) * (size_t)f->table_cap * n) &&
+        alloc((void**)&f->nodes, sizeof(Node) * (size_t)slots) && alloc((void**)&f->link, sizeof(int32_t) * (size_t)slots) &&
+        alloc((void**)&f->created, sizeof(int32_t) * (size_t)slots);
+    if (!ok) {
+        dvc_forest_destroy(f);
+        return fail(c, DVC_E_OOM, "dvc_forest_create: device allocation of " + std::to_string(slots) + " node slots");
+    }
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    cudaError_t e = cudaMemcpyAsync(f->meta, hm.data(), sizeof(TreeMeta) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->roots, d_roots, sizeof(dvc_state) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+        dvc_forest_destroy(f);
+        return cuda_fail(c, e, "dvc_forest_create copy");
+    }
+    forest_init_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), n, nullptr, f->plans, f->tables, f->table_cap);
+    if (int rc = check_launch(c, "forest_init_kernel")) {
+        dvc_forest_destroy(f);
+        return rc;
+    }
+    *out = f;
+    return DVC_OK;
+}
+
+int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (d_roots && !is_device_ptr(d_roots))
+        return fail(f->ctx, DVC_E_INVALID, "dvc_forest_reset: d_roots must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    forest_init_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_roots, f->plans,
+                                                                                  f->tables, f->table_cap);
+    return check_launch(f->ctx, "forest_init_kernel");
+}
+
+int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    dvc_ctx* c = f->ctx;
+    if (n_iterations < 0) return fail(c, DVC_E_INVALID, "dvc_mcts_step: n_iterations < 0");
+    if (mode != DVC_MODE_ROLLOUT) return fail(c, DVC_E_UNSUPPORTED, "dvc_mcts_step: mode not available");
+    if (n_iterations == 0) return DVC_OK;
+    if (int rc = set_device(c)) return rc;
+    // two-player tables are small: stage them in shared memory
+    const uint32_t smem_cells = c->cfg.nplayers == 2 ? (c->cfg.ntiles == 24 ? 640u : kDetMaxCells2p) : 0u;
+    int block = c->cfg.playouts >= 256 ? 256 : ((c->cfg.playouts + 31) / 32) * 32;
+    block = std::max(block, 32);
+    mcts_fused_kernel<<<f->n, block, smem_cells * sizeof(unsigned long long), (cudaStream_t)stream>>>(
+        dev_of(f), params_of(f), n_iterations, smem_cells);
+    return check_launch(c, "mcts_fused_kernel");
+}
+
+int dvc_mcts_select(dvc_forest* f, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (int rc = set_device(f->ctx)) return rc;
+    mcts_select_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dev_of(f), params_of(f), f->n,
+                                                                                  f->work, f->paths, f->movers);
+    return check_launch(f->ctx, "mcts_select_kernel");
+}
+
+int dvc_mcts_expand(dvc_forest* f, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (int rc = set_device(f->ctx)) return rc;
+    mcts_expand_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        dev_of(f), f->n, f->work, f->paths, f->movers, f->leaves, f->leaf_tree, f->leaf_iter);
+    return check_launch(f->ctx, "mcts_expand_kernel");
+}
+
+int dvc_mcts_backprop(dvc_forest* f, const int32_t* d_wins, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (!is_device_ptr(d_wins)) return fail(f->ctx, DVC_E_INVALID, "dvc_mcts_backprop: d_wins must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    mcts_backprop_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        dev_of(f), params_of(f), f->n, f->work, f->paths, f->movers, d_wins);
+    return check_launch(f->ctx, "mcts_backprop_kernel");
+}
+
+int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_counters: d_out must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_out, f->d_words, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, sizeof(uint64_t), st);
+    if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_counters");
+    return DVC_OK;
+}
+
+int dvc_forest_leaves(dvc_forest* f, dvc_state** d_leaves, uint32_t** d_tree_ids, uint32_t** d_leaf_ids) {
+    if (!f || !d_leaves || !d_tree_ids || !d_leaf_ids) return DVC_E_INVALID;
+    *d_leaves = f->leaves;
+    *d_tree_ids = f->leaf_tree;
+    *d_leaf_ids = f->leaf_iter;
+    return DVC_OK;
+}
+
+int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_root_stats: d_out must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    root_stats_kernel<<<(f->n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_out);
+    return check_launch(f->ctx, "root_stats_kernel");
+}
+
+int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (tree < 0 || tree >= f->n) return fail(f->ctx, DVC_E_INVALID, "dvc_tree_export: tree out of range");
+    if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_tree_export: d_out must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    const int32_t budget = f->h_budgets[tree];
+    if (budget > f->export_cap) {
+        if (f->export_scratch) cudaFree(f->export_scratch);
+        f->export_scratch = nullptr;
+        f->export_cap = 0;
+        if (cudaMalloc(&f->export_scratch, sizeof(int32_t) * (size_t)std::max(budget, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            f->export_scratch = nullptr;
+            return fail(f->ctx, DVC_E_OOM, "dvc_tree_export: scratch");
+        }
+        f->export_cap = budget;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t rows = budget + 1;
+    cudaError_t e = cudaMemsetAsync(d_out, 0xFF, sizeof(int32_t) * 4 * (size_t)rows, st);
+    if (e == cudaSuccess && budget > 0)
+        e = cudaMemsetAsync(f->export_scratch, 0, sizeof(int32_t) * (size_t)budget, st);
+    if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_tree_export memset");
+    const ForestDev fd = dev_of(f);
+    export_flag_kernel<<<64, 256, 0, st>>>(fd, tree, f->export_scratch);
+    export_scan_kernel<<<1, 1, 0, st>>>(budget, f->export_scratch);
+    export_rows_kernel<<<64, 256, 0, st>>>(fd, tree, f->export_scratch, rows, d_out);
+    return check_launch(f->ctx, "export kernels");
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// dvc_tree.cuh -- device-resident UCT trees and one search iteration
+// (Sec. II-B: select, expand, simulate, backpropagate; Sec. III-A: node =
+// guess (slot, identity), determinized root per simulation, no extra guess in
+// the tree, expansion depth limit).
+//
+// Arena layout, per tree: a slice of 16-byte node slots.  Slot 0 is the root.
+// The children of a node live in blocks of consecutive slots -- the root's
+// first block is sized to its legal-guess count (fixed for the whole search),
+// other nodes' blocks grow 4, 8, 16, 32, 32, ... -- so a warp reads a block
+// with one coalesced load.  A block's successor is recorded in `link` at the
+// block's first slot.  With blocks no larger than four times the children
+// they hold, root block + 4 * budget slots always suffice.
+#pragma once
+#include "dvc_det.cuh"
+
+namespace dvc {
+
+struct Node {
+    int32_t visits;
+    int32_t wins;
+    int32_t child;  // slot of the first child block, -1 if none
+    uint32_t meta;  // action code (bits 0-11) | number of children (bits 12-23)
+};
+
+struct TreeMeta {
+    long long node_off;   // first slot of this tree in the arena
+    long long table_off;  // first cell of its determinization table
+    int32_t cap;          // slots
+    int32_t budget;       // iterations allowed in total
+    int32_t done;         // iterations done
+    int32_t next_free;    // next unused slot
+    int32_t root_legal;   // legal guesses at the root
+    uint32_t tree_id;     // stream key
+    int32_t failed;       // arena exhausted, or view too large to determinize
+    int32_t used;         // nodes in the tree
+};
+
+// Slots reserved for the root's child block: its legal-guess count is
+// (face-down slots of opponents) x (unknown identities) <= 25 * 25.
+constexpr int32_t kRootReserve = 640;
+
+struct SearchParams {
+    uint64_t seed;
+    double c_uct;
+    int32_t d_max;
+    int32_t playouts;
+    uint32_t cont_thr;
+};
+
+__device__ __forceinline__ uint32_t block_size(uint32_t k, bool is_root, uint32_t root_legal) {
+    if (is_root && k == 0) return root_legal > 0u ? root_legal : 1u;
+    return k >= 3 ? 32u : (4u << k);
+}
+
+// What a descent produced: either a node to expand (found = 1, action act)
+// or a leaf to score (found = 0).
+struct Descent {
+    G s;              // state at the node reached
+    Rng tr;           // tree stream after the in-tree draws so far
+    int32_t node;     // slot reached
+    int32_t found;    // 1: expand `act` below `node`
+    uint32_t act;
+    int32_t nchild;   // children of `node`
+    int32_t last_blk, last_size, last_cnt, nblocks;
+    int32_t np;       // path length
+};
+
+// Warp-cooperative descent from the root for iteration `it`.  All 32 lanes
+// of the calling warp enter with the same arguments and leave with the same
+// Descent; lane 0 records the path in path[] / mover[] (shared or global).
+// E is a 4 x 26 word scratch (shared memory) for expanded-identity masks.
+__device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* nodes, const int32_t* link,
+                                        const TreeMeta& tm, const SearchParams& sp, uint32_t it, int32_t* path,
+                                        uint8_t* mover, uint32_t* E, Descent& d) {
+    const uint32_t lane = threadIdx.x & 31u;
+    d.s = det;
+    d.tr.open(sp.seed, tm.tree_id, 0u, it, kTagTree);
+    d.node = 0;
+    d.found = 0;
+    d.np = 1;
+    if (lane == 0) {
+        path[0] = 0;
+        mover[0] = (uint8_t)obs;
+    }
+    uint32_t depth = 0;
+    while (d.s.winner == kNone && depth < (uint32_t)sp.d_max) {
+        const Node nd = nodes[d.node];
+        const uint32_t nchild = (nd.meta >> 12) & 0xFFFu;
+        const uint32_t cur = d.s.cur;
+        const uint32_t U = d.s.tmask & ~d.s.hand(cur) & ~d.s.rev;
+        for (uint32_t e = lane; e < 104u; e += 32u) E[e] = 0u;
+        __syncwarp();
+        double csl = 0.0;
+        if (nchild) csl = __dmul_rn(sp.c_uct, __dsqrt_rn(ln_series((double)nd.visits)));
+        double best_sc = -1.0;
+        uint32_t best_rank = 0xFFFFFFFFu;
+        int32_t best_slot = -1;
+        uint32_t best_code = 0;
+        int32_t blk = nd.child;
+        uint32_t seen = 0, k = 0;
+        d.last_blk = -1;
+        d.last_size = 0;
+        d.last_cnt = 0;
+        while (seen < nchild) {
+            const uint32_t size = block_size(k, d.node == 0, (uint32_t)tm.root_legal);
+            const uint32_t cnt = min(size, nchild - seen);
+            for (uint32_t e = lane; e < cnt; e += 32u) {
+                const Node ch = nodes[blk + (int32_t)e];
+                const uint32_t code = ch.meta & 0xFFFu;
+                const uint32_t q = code >> 10, sl = (code >> 5) & 31u, x = code & 31u;
+                if (sl < 26u) atomicOr(&E[q * 26u + sl], 1u << x);
+                if (guess_legal(d.s, q, sl, x)) {
+                    const double sc = uct_score(csl, ch.wins, ch.visits);
+                    const uint32_t rk = canon_rank(code, cur, d.s.np);
+                    if (best_slot < 0 || sc > best_sc || (sc == best_sc && rk < best_rank)) {
+                        best_sc = sc;
+                        best_rank = rk;
+                        best_slot = blk + (int32_t)e;
+                        best_code = code;
+                    }
+                }
+            }
+            seen += cnt;
+            d.last_blk = blk;
+            d.last_size = (int32_t)size;
+            d.last_cnt = (int32_t)cnt;
+            ++k;
+            if (seen < nchild) blk = link[blk];
+        }
+        d.nblocks = (int32_t)k;
+        d.nchild = (int32_t)nchild;
+        __syncwarp();
+        // first legal action without a child, canonical order
+        uint32_t act = 0;
+        bool found = false;
+        for (uint32_t off = 1; off < d.s.np && !found; ++off) {
+            uint32_t q = cur + off;
+            q = q >= d.s.np ? q - d.s.np : q;
+            if (!((d.s.alive >> q) & 1u)) continue;
+            const uint32_t nh = __popc(d.s.hand(q) & ~d.s.rev);
+            for (uint32_t h0 = 0; h0 < nh && !found; h0 += 32u) {
+                const uint32_t h = h0 + lane;
+                uint32_t avail = 0u, sp_ = 0u;
+                if (h < nh) {
+                    const uint32_t t = hidden_slot(d.s, q, h);
+                    sp_ = seq_pos(d.s, q, t);
+                    if (sp_ < 26u) avail = U & ~E[q * 26u + sp_];
+                }
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, avail != 0u);
+                if (bal) {
+                    const uint32_t L = __ffs(bal) - 1u;
+                    const uint32_t spL = __shfl_sync(0xFFFFFFFFu, sp_, L);
+                    const uint32_t avL = __shfl_sync(0xFFFFFFFFu, avail, L);
+                    act = (q << 10) | (spL << 5) | ((uint32_t)__ffs(avL) - 1u);
+                    found = true;
+                }
+            }
+        }
+        if (found) {
+            d.found = 1;
+            d.act = act;
+            return;
+        }
+        // UCB1 argmax over lanes: higher score, then lower canonical rank
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double osc = __shfl_xor_sync(0xFFFFFFFFu, best_sc, o);
+            const uint32_t ork = __shfl_xor_sync(0xFFFFFFFFu, best_rank, o);
+            const int32_t osl = __shfl_xor_sync(0xFFFFFFFFu, best_slot, o);
+            const uint32_t ocd = __shfl_xor_sync(0xFFFFFFFFu, best_code, o);
+            const bool take = osl >= 0 && (best_slot < 0 || osc > best_sc || (osc == best_sc && ork < best_rank));
+            if (take) {
+                best_sc = osc;
+                best_rank = ork;
+                best_slot = osl;
+                best_code = ocd;
+            }
+        }
+        const uint32_t who = d.s.cur;
+        tree_apply(d.s, best_code, d.tr);
+        if (lane == 0) {
+            path[d.np] = best_slot;
+            mover[d.np] = (uint8_t)who;
+        }
+        d.np++;
+        d.node = best_slot;
+        ++depth;
+    }
+}
+
+// Create the child found by descend() and step the state through its action.
+// Lane-uniform; lane 0 writes memory.  next_free is the tree's allocator
+// (uniform register copy).  Returns false if the arena is exhausted.
+__device__ __forceinline__ bool expand_child(Descent& d, Node* nodes, int32_t* link, int32_t* created,
+                                             const TreeMeta& tm, int32_t& next_free, int32_t& used, uint32_t it,
+                                             int32_t* path, uint8_t* mover) {
+    const uint32_t lane = threadIdx.x & 31u;
+    int32_t slot;
+    if (d.nchild == 0 || d.last_cnt >= d.last_size) {
+        // a new child block: first block of this node, or the last one is full
+        const uint32_t k = d.nchild == 0 ? 0u : (uint32_t)d.nblocks;
+        const int32_t size = (int32_t)block_size(k, d.node == 0, (uint32_t)tm.root_legal);
+        if (next_free + size > tm.cap) return false;
+        slot = next_free;
+        next_free += size;
+        for (int32_t e = (int32_t)lane; e < size; e += 32) created[slot + e] = -1;  // slots not yet nodes
+        if (lane == 0) {
+            if (d.nchild == 0) nodes[d.node].child = slot;
+            else link[d.last_blk] = slot;
+            link[slot] = -1;
+        }
+    } else {
+        slot = d.last_blk + d.last_cnt;
+    }
+    if (lane == 0) {
+        Node c;
+        c.visits = 0;
+        c.wins = 0;
+        c.child = -1;
+        c.meta = d.act;
+        nodes[slot] = c;
+        created[slot] = (int32_t)it;
+        nodes[d.node].meta += 1u << 12;
+        path[d.np] = slot;
+        mover[d.np] = (uint8_t)d.s.cur;
+    }
+    tree_apply(d.s, d.act, d.tr);
+    d.np++;
+    d.node = slot;
+    ++used;
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Backpropagation (Sec. II-B): every node on the path gains `playouts` visits
+// and the playouts won by the seat that moved into it.
+__device__ __forceinline__ void backprop(Node* nodes, const int32_t* path, const uint8_t* mover, int32_t np,
+                                         const int32_t* wins, int32_t playouts) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (int32_t e = (int32_t)lane; e < np; e += 32) {
+        Node* n = &nodes[path[e]];
+        n->visits += playouts;
+        n->wins += wins[mover[e]];
+    }
+}
+
+}  // namespace dvc

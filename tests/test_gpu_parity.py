@@ -1,0 +1,288 @@
+"""GPU parity: every entry point of libdvc against the CPU oracle, bit for bit.
+
+All inputs are seeded and synthetic.  Integer game logic and the UCT
+decisions are compared exactly (the method has no tolerance to give: states,
+win counts, visit counts and decisions are integers, and the UCT score is
+computed with the same IEEE double operations on both sides).
+"""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2403_10720_gb300.workloads import BATCHED, SINGLE_TREE, UNEVEN
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = {
+    "2p24": dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5),
+    "3p24": dict(nplayers=3, ntiles=24, deal=4, max_predraw=6, max_revealed=3),
+    "4p26j": dict(nplayers=4, ntiles=26, deal=3, max_predraw=8, max_revealed=3),
+}
+
+
+@pytest.fixture(scope="module")
+def dvc():
+    import paper_2403_10720_gb300 as m
+    from paper_2403_10720_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return m
+
+
+def _ctx(dvc, **kw):
+    return dvc.Context(dvc.Config(**kw), 0)
+
+
+def _u32(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.uint32).view(np.int32)).cuda()
+
+
+def test_philox_matches_reference_and_oracle(dvc):
+    ctx = _ctx(dvc)
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key[1] = 0xFFFFFFFF
+    mine = ctx.dvc_philox(_u32(ctr), _u32(key), False).cpu().numpy().view(np.uint32)
+    ref = ctx.dvc_philox(_u32(ctr), _u32(key), True).cpu().numpy().view(np.uint32)
+    assert (mine == ref).all()
+    for i in range(0, 4096, 97):
+        assert list(mine[i]) == oracle.philox4x32_10(ctr[i], key[i])
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+@pytest.mark.parametrize("n", [1, 333])
+def test_init_states_bit_exact(dvc, variant, n):
+    kw = VARIANTS[variant]
+    ctx = _ctx(dvc, **kw)
+    got = ctx.dvc_init_states(99, n).cpu().numpy()
+    want = oracle.init_states(oracle.OracleConfig(**kw), 99, n)
+    assert (got == want).all()
+
+
+def test_init_states_empty(dvc):
+    ctx = _ctx(dvc)
+    out = torch.zeros((1, 32), dtype=torch.uint8, device="cuda")
+    ctx.dvc_init_states(3, 0, out=out)
+    assert int(out.sum()) == 0
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_determinize_bit_exact(dvc, variant):
+    kw = VARIANTS[variant]
+    ocfg = oracle.OracleConfig(**kw)
+    roots = oracle.init_states(ocfg, 7, 300)
+    n = len(roots)
+    rng = np.random.default_rng(1)
+    tree = rng.integers(0, 1 << 20, size=n).astype(np.uint32)
+    it = rng.integers(0, 1 << 20, size=n).astype(np.uint32)
+    ctx = _ctx(dvc, **kw)
+    got = ctx.dvc_determinize(torch.from_numpy(roots).cuda(), -1, 31, _u32(tree), _u32(it)).cpu().numpy()
+    ctx.dvc_check()
+    for i in range(n):
+        want = oracle.determinize(ocfg, roots[i], -1, 31, int(tree[i]), int(it[i]))
+        assert (got[i] == want).all(), i
+
+
+def test_determinize_joker_views(dvc):
+    from test_oracle_det_mcts import VIEWS, _view
+    for name in sorted(VIEWS):
+        v, revealed, s = _view(name)
+        P = len(v["hands"])
+        ocfg = oracle.OracleConfig(nplayers=P, ntiles=v["T"])
+        ctx = _ctx(dvc, nplayers=P, ntiles=v["T"], deal=2)
+        n = 512
+        roots = torch.from_numpy(np.tile(s, (n, 1))).cuda()
+        its = np.arange(n, dtype=np.uint32)
+        got = ctx.dvc_determinize(roots, v["cur"], 5, _u32(np.full(n, 3)), _u32(its)).cpu().numpy()
+        for i in range(0, n, 7):
+            want = oracle.determinize(ocfg, s, v["cur"], 5, 3, i)
+            assert (got[i] == want).all(), (name, i)
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+@pytest.mark.parametrize("P", [1, 37, 64])
+def test_rollout_bit_exact(dvc, variant, P):
+    kw = VARIANTS[variant]
+    ocfg = oracle.OracleConfig(**kw)
+    leaves = oracle.init_states(ocfg, 13, 45)
+    n = len(leaves)
+    tree = np.arange(n, dtype=np.uint32) * 3 + 1
+    leaf = np.arange(n, dtype=np.uint32) * 7 + 2
+    ctx = _ctx(dvc, **kw)
+    words = torch.zeros(1, dtype=torch.int64, device="cuda")
+    wins = ctx.dvc_rollout_batch(torch.from_numpy(leaves).cuda(), P, 77, _u32(tree), _u32(leaf), words=words)
+    wins = wins.cpu().numpy()
+    total = 0
+    for i in range(n):
+        w, wd = oracle.rollout(ocfg, leaves[i], P, 77, int(tree[i]), int(leaf[i]))
+        assert (wins[i] == w).all(), i
+        total += wd
+    assert int(words.item()) == total
+
+
+def test_rollout_finished_leaves(dvc):
+    kw = VARIANTS["2p24"]
+    leaves = oracle.init_states(oracle.OracleConfig(**kw), 1, 3).copy()
+    leaves[0, 28] = 1      # already won by seat 1
+    leaves[2, 28] = 0xFE   # inactive marker: no credit
+    ctx = _ctx(dvc, **kw)
+    wins = ctx.dvc_rollout_batch(torch.from_numpy(leaves).cuda(), 10, 1, _u32([0, 1, 2]), _u32([0, 0, 0]))
+    wins = wins.cpu().numpy()
+    assert wins[0].tolist() == [0, 10, 0, 0]
+    assert wins[1].sum() == 10
+    assert wins[2].tolist() == [0, 0, 0, 0]
+
+
+def _oracle_trees(ocfg, roots, seed, budgets, trees, tree_ids=None):
+    out = {}
+
+    def run(t):
+        tid = t if tree_ids is None else int(tree_ids[t])
+        out[t] = oracle.mcts(ocfg, roots[t], seed, tid, int(budgets[t]))
+
+    ths = [threading.Thread(target=run, args=(t,)) for t in trees]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    return out
+
+
+def _check_forest(forest, stats, want, trees):
+    for t in trees:
+        nodes, best = want[t]
+        exp = forest.dvc_tree_export(t).cpu().numpy()
+        assert (exp[: len(nodes)] == nodes).all(), t
+        assert (exp[len(nodes):] == -1).all(), t
+        assert stats[t][0] == best[0] and stats[t][1] == best[1] and stats[t][2] == best[2], t
+        assert stats[t][3] == best[3] and stats[t][5] == len(nodes), t
+
+
+@pytest.mark.parametrize("variant,P,budgets", [
+    ("2p24", 32, [200, 57, 1, 0, 120, 200]),
+    ("3p24", 16, [150, 90, 3]),
+    ("4p26j", 32, [120, 64, 200, 17]),
+    ("2p24", 256, [40, 33]),
+])
+def test_mcts_fused_bit_exact(dvc, variant, P, budgets):
+    kw = dict(VARIANTS[variant], playouts=P)
+    ocfg = oracle.OracleConfig(**kw)
+    n = len(budgets)
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(21, n)
+    oroots = oracle.init_states(ocfg, 21, n)
+    assert (roots.cpu().numpy() == oroots).all()
+    tree_ids = np.arange(n, dtype=np.uint32) * 5 + 9
+    forest = dvc.Forest(ctx, roots, budgets, 8, tree_ids=tree_ids)
+    forest.dvc_mcts_step(max(budgets))
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    assert (stats[:, 6] == np.asarray(budgets)).all()
+    want = _oracle_trees(ocfg, oroots, 8, budgets, range(n), tree_ids)
+    _check_forest(forest, stats, want, range(n))
+
+
+def test_mcts_steps_compose(dvc):
+    kw = dict(VARIANTS["2p24"], playouts=32)
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(4, 5)
+    a = dvc.Forest(ctx, roots, [150] * 5, 6)
+    a.dvc_mcts_step(150)
+    b = dvc.Forest(ctx, roots, [150] * 5, 6)
+    for _ in range(3):
+        b.dvc_mcts_step(50)
+    b.dvc_mcts_step(50)   # budget spent: no-op
+    for t in range(5):
+        assert torch.equal(a.dvc_tree_export(t), b.dvc_tree_export(t))
+    assert torch.equal(a.dvc_root_stats(), b.dvc_root_stats())
+
+
+@pytest.mark.parametrize("variant,P", [("2p24", 64), ("4p26j", 32)])
+def test_mcts_split_steps_equal_fused(dvc, variant, P):
+    kw = dict(VARIANTS[variant], playouts=P)
+    ctx = _ctx(dvc, **kw)
+    n, budget = 7, 60
+    roots = ctx.dvc_init_states(12, n)
+    budgets = [budget, 30, budget, 1, budget, 45, 0]
+    fused = dvc.Forest(ctx, roots, budgets, 3)
+    fused.dvc_mcts_step(budget)
+    split = dvc.Forest(ctx, roots, budgets, 3)
+    leaves, tids, lids = split.dvc_forest_leaves()
+    wins = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    for _ in range(budget + 2):
+        split.dvc_mcts_select()
+        split.dvc_mcts_expand()
+        rc = dvc.lib().dvc_rollout_batch(ctx.h, leaves, n, P, 3, tids, lids, wins.data_ptr(), None,
+                                         dvc._stream())
+        assert rc == 0
+        split.dvc_mcts_backprop(wins)
+    ctx.dvc_check()
+    for t in range(n):
+        assert torch.equal(fused.dvc_tree_export(t), split.dvc_tree_export(t)), t
+    assert torch.equal(fused.dvc_root_stats(), split.dvc_root_stats())
+
+
+def test_single_tree_workload(dvc):
+    w = SINGLE_TREE
+    kw = w.config_kwargs()
+    ocfg = oracle.OracleConfig(**kw)
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(w.root_seed, 1)
+    forest = dvc.Forest(ctx, roots, w.budgets(), w.seed)
+    forest.dvc_mcts_step(w.budget)
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    oroots = oracle.init_states(ocfg, w.root_seed, 1)
+    want = _oracle_trees(ocfg, oroots, w.seed, w.budgets(), [0])
+    _check_forest(forest, stats, want, [0])
+
+
+def test_batched_workload_full_size_sampled(dvc):
+    """The full 4,096-tree x 4,096-iteration x 256-playout batch as the
+    benchmark launches it; three trees are replayed by the oracle and every
+    tree is checked for the visit-count invariants."""
+    w = BATCHED
+    kw = w.config_kwargs()
+    ocfg = oracle.OracleConfig(**kw)
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(w.root_seed, w.n_trees)
+    forest = dvc.Forest(ctx, roots, w.budgets(), w.seed)
+    forest.dvc_mcts_step(w.budget)
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    assert (stats[:, 3] == w.budget * w.playouts).all()
+    assert (stats[:, 6] == w.budget).all()
+    assert (stats[:, 5] <= w.budget + 1).all() and (stats[:, 7] == 0).all()
+    sample = [0, 1234, w.n_trees - 1]
+    oroots = oracle.init_states(ocfg, w.root_seed, w.n_trees)
+    assert (roots.cpu().numpy() == oroots).all()
+    want = _oracle_trees(ocfg, oroots, w.seed, w.budgets(), sample)
+    _check_forest(forest, stats, want, sample)
+
+
+def test_uneven_workload_sampled(dvc):
+    """The 4-player joker forest at reduced size: 64 trees with the
+    workload's log-uniform budgets capped at 3,000, four replayed."""
+    w = UNEVEN
+    kw = w.config_kwargs()
+    ocfg = oracle.OracleConfig(**kw)
+    ctx = _ctx(dvc, **kw)
+    n = 64
+    budgets = np.minimum(w.budgets(n), 3000)
+    roots = ctx.dvc_init_states(w.root_seed, n)
+    forest = dvc.Forest(ctx, roots, budgets, w.seed)
+    forest.dvc_mcts_step(int(budgets.max()))
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    assert (stats[:, 6] == budgets).all()
+    oroots = oracle.init_states(ocfg, w.root_seed, n)
+    sample = [0, 5, 17, 63]
+    want = _oracle_trees(ocfg, oroots, w.seed, budgets, sample)
+    _check_forest(forest, stats, want, sample)
