@@ -231,6 +231,28 @@ int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream);
  * nodes used are set to -1. */
 int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream);
 
+/*
+ * dvc_determinize without any allocation, for callers that cannot call
+ * cudaMalloc: a process whose device memory is fully reserved by another
+ * framework's caching allocator, or one that may not allocate after start-up.
+ * The paper has no counterpart; this is a deployment variant of
+ * dvc_determinize and returns the same records for the same arguments.
+ * It needs no context: it runs on the calling thread's current device.  Its
+ * scratch is a fixed 8 MiB device array inside the library (64 roots x
+ * 16,384 table cells), held by every GPU that loads the library until exit.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (nothing in
+ * it needs to start at zero); calls that overlap on the GPU race on it, so
+ * issue them on one stream.  n > 64 returns DVC_E_UNSUPPORTED and enqueues
+ * nothing.  d_status (optional, n int32): 0, or DVC_E_UNSUPPORTED for a view
+ * whose table needs more than 16,384 cells (that output is the root).  Calls
+ * no cudaMalloc or cudaFree.
+ */
+int dvc_determinize_noalloc(const dvc_state* d_roots, int n, int observer, uint64_t seed,
+                            const uint32_t* d_tree_ids, const uint32_t* d_iter_ids, dvc_state* d_out,
+                            int32_t* d_status, void* stream);
+
 /* Test hook for the random-number generator: out[4k..4k+3] = Philox-4x32-10
  * of counter d_ctr[4k..], key d_key[2k..], by this library's generator
  * (use_reference = 0) or by cuRAND's device function (use_reference = 1). */

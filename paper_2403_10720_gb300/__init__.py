@@ -96,6 +96,7 @@ def lib():
             "dvc_forest_counters": ([vp, vp, vp], i),
             "dvc_tree_export": ([vp, i, vp, vp], i),
             "dvc_philox": ([vp, i, vp, vp, vp, i, vp], i),
+            "dvc_determinize_noalloc": ([vp, i, i, u64, vp, vp, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
