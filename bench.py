@@ -305,8 +305,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trees", type=int, default=0, help="override the tree count (small profiling cases)")
+    ap.add_argument("--iterations", type=int, default=0, help="override the iterations per tree")
     args = ap.parse_args()
     w = BATCHED
+    if args.trees or args.iterations:
+        import dataclasses
+        n, it = args.trees or w.n_trees, args.iterations or w.budget
+        w = dataclasses.replace(w, n_trees=n, budget=it, name=f"2p24_{n}trees_{it}it_{w.playouts}po")
     if args.impl == "reference":
         run_reference(args, w)
     else:
