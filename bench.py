@@ -180,6 +180,12 @@ def run_ours(args, w):
     roots = ctx.dvc_init_states(w.root_seed + 1000003 * rank, n)
     budgets = w.budgets()
     forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=np.arange(rank * n, (rank + 1) * n, dtype=np.uint32))
+    # launch shape: the three-kernel pipeline in CUDA graphs, two rollout CTAs'
+    # worth of trees per SM, 32 warps per rollout CTA, two overlapping chains
+    sms = props.multi_processor_count
+    trees_per_cta = max(1, min(32, -(-n // (2 * sms))))
+    chains = 2
+    forest.dvc_forest_tune(2, trees_per_cta, 32, chains)
     stats = torch.empty((n, 8), dtype=torch.int32, device=dev)
     words = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -273,13 +279,16 @@ def run_ours(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "trees": n, "iterations": w.budget, "playouts_per_leaf": w.playouts,
                    "players": w.nplayers, "tiles": w.ntiles, "d_max": w.d_max,
+                   "engine": f"pipeline, {trees_per_cta} trees x 32 warps per rollout CTA, {chains} chains, CUDA graph",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "decisions_per_s": n * world * args.steps / total_s,
         "kernel_ms": sum(kern_ms) / len(kern_ms),
         "words_per_playout": words_per_step / playouts_per_step,
         "e2e": {"value": e2e_value, "unit": "playouts/s", "h2d_bytes_per_step": int(host_roots.numel()),
                 "d2h_bytes_per_step": int(host_stats.numel() * 4)},
-        "gpu_launches": 3 * args.steps,
+        # per step: forest reset, pipeline begin, per iteration (select + rollout) x chains,
+        # final backprop, root stats
+        "gpu_launches": args.steps * (4 + 2 * budget * chains),
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops, "traffic": None,
                      "peak_kind": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind})",

@@ -198,6 +198,25 @@ int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream);
 int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
 
 /*
+ * Engine and launch shape of dvc_mcts_step (no effect on results).
+ * engine 1: one fused kernel; each CTA runs trees_per_cta trees in lockstep
+ * with warps_per_cta warps (every warp walks a tree, then all lanes share the
+ * leaves' playouts).  engine 2: per iteration two launches (backprop of the
+ * previous iteration + select, then pooled rollouts) in a CUDA graph of 64
+ * iterations; rollout CTAs pool trees_per_cta trees with warps_per_cta warps,
+ * and the CTAs are split into `chains` (1..4; 0 = keep, default 2)
+ * independent chains on separate streams so that one chain's tree walks run
+ * beside another chain's playouts.  engine 0 keeps the
+ * current engine (the default is 2 for forests of even budgets and at least
+ * two trees per SM, else 1).  trees_per_cta / warps_per_cta 0 = defaults
+ * (ceil(n_trees / SMs) trees; 16 warps fused, 32 pipeline).  Changing
+ * trees_per_cta re-balances which trees share a CTA (longest budget first,
+ * least-loaded CTA) and synchronises the device once.  DVC_E_UNSUPPORTED if
+ * a CTA's state would not fit in shared memory.
+ */
+int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_cta, int chains);
+
+/*
  * The same iteration split into launches, for callers that score leaves
  * themselves: dvc_mcts_select determinizes and descends, dvc_mcts_expand adds
  * the new child and writes each tree's leaf state (dvc_forest_leaves gives

@@ -87,6 +87,7 @@ def lib():
             "dvc_forest_create": ([vp, i, vp, vp, vp, u64, ctypes.POINTER(vp), vp], i),
             "dvc_forest_destroy": ([vp], None),
             "dvc_forest_reset": ([vp, vp, vp], i),
+            "dvc_forest_tune": ([vp, i, i, i, i], i),
             "dvc_mcts_step": ([vp, i, i, vp], i),
             "dvc_mcts_select": ([vp, vp], i),
             "dvc_mcts_expand": ([vp, vp], i),
@@ -219,6 +220,9 @@ class Forest:
             self.close()
         except Exception:
             pass
+
+    def dvc_forest_tune(self, engine=0, trees_per_cta=0, warps_per_cta=0, chains=0):
+        self.ctx._rc(lib().dvc_forest_tune(self.h, engine, trees_per_cta, warps_per_cta, chains), "dvc_forest_tune")
 
     def dvc_forest_reset(self, roots=None, stream=None):
         self.ctx._rc(lib().dvc_forest_reset(self.h, _ptr(roots), _stream(stream)), "dvc_forest_reset")

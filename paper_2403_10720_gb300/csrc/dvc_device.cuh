@@ -88,20 +88,73 @@ struct Rng {
 __device__ __forceinline__ uint32_t pick(uint32_t w, uint32_t n) { return __umulhi(w, n); }
 __device__ __forceinline__ uint64_t pick64(uint64_t r, uint64_t n) { return __umul64hi(r, n); }
 
-// Index of the n-th (0-based) set bit of m; n < popc(m).
+// Position of the r-th set bit (r = 0..7) of each byte value, 4 bits per rank.
+__device__ const uint32_t kSelectInByte[256] = {
+    0x00000000u, 0x00000000u, 0x00000001u, 0x00000010u, 0x00000002u, 0x00000020u, 0x00000021u, 0x00000210u,
+    0x00000003u, 0x00000030u, 0x00000031u, 0x00000310u, 0x00000032u, 0x00000320u, 0x00000321u, 0x00003210u,
+    0x00000004u, 0x00000040u, 0x00000041u, 0x00000410u, 0x00000042u, 0x00000420u, 0x00000421u, 0x00004210u,
+    0x00000043u, 0x00000430u, 0x00000431u, 0x00004310u, 0x00000432u, 0x00004320u, 0x00004321u, 0x00043210u,
+    0x00000005u, 0x00000050u, 0x00000051u, 0x00000510u, 0x00000052u, 0x00000520u, 0x00000521u, 0x00005210u,
+    0x00000053u, 0x00000530u, 0x00000531u, 0x00005310u, 0x00000532u, 0x00005320u, 0x00005321u, 0x00053210u,
+    0x00000054u, 0x00000540u, 0x00000541u, 0x00005410u, 0x00000542u, 0x00005420u, 0x00005421u, 0x00054210u,
+    0x00000543u, 0x00005430u, 0x00005431u, 0x00054310u, 0x00005432u, 0x00054320u, 0x00054321u, 0x00543210u,
+    0x00000006u, 0x00000060u, 0x00000061u, 0x00000610u, 0x00000062u, 0x00000620u, 0x00000621u, 0x00006210u,
+    0x00000063u, 0x00000630u, 0x00000631u, 0x00006310u, 0x00000632u, 0x00006320u, 0x00006321u, 0x00063210u,
+    0x00000064u, 0x00000640u, 0x00000641u, 0x00006410u, 0x00000642u, 0x00006420u, 0x00006421u, 0x00064210u,
+    0x00000643u, 0x00006430u, 0x00006431u, 0x00064310u, 0x00006432u, 0x00064320u, 0x00064321u, 0x00643210u,
+    0x00000065u, 0x00000650u, 0x00000651u, 0x00006510u, 0x00000652u, 0x00006520u, 0x00006521u, 0x00065210u,
+    0x00000653u, 0x00006530u, 0x00006531u, 0x00065310u, 0x00006532u, 0x00065320u, 0x00065321u, 0x00653210u,
+    0x00000654u, 0x00006540u, 0x00006541u, 0x00065410u, 0x00006542u, 0x00065420u, 0x00065421u, 0x00654210u,
+    0x00006543u, 0x00065430u, 0x00065431u, 0x00654310u, 0x00065432u, 0x00654320u, 0x00654321u, 0x06543210u,
+    0x00000007u, 0x00000070u, 0x00000071u, 0x00000710u, 0x00000072u, 0x00000720u, 0x00000721u, 0x00007210u,
+    0x00000073u, 0x00000730u, 0x00000731u, 0x00007310u, 0x00000732u, 0x00007320u, 0x00007321u, 0x00073210u,
+    0x00000074u, 0x00000740u, 0x00000741u, 0x00007410u, 0x00000742u, 0x00007420u, 0x00007421u, 0x00074210u,
+    0x00000743u, 0x00007430u, 0x00007431u, 0x00074310u, 0x00007432u, 0x00074320u, 0x00074321u, 0x00743210u,
+    0x00000075u, 0x00000750u, 0x00000751u, 0x00007510u, 0x00000752u, 0x00007520u, 0x00007521u, 0x00075210u,
+    0x00000753u, 0x00007530u, 0x00007531u, 0x00075310u, 0x00007532u, 0x00075320u, 0x00075321u, 0x00753210u,
+    0x00000754u, 0x00007540u, 0x00007541u, 0x00075410u, 0x00007542u, 0x00075420u, 0x00075421u, 0x00754210u,
+    0x00007543u, 0x00075430u, 0x00075431u, 0x00754310u, 0x00075432u, 0x00754320u, 0x00754321u, 0x07543210u,
+    0x00000076u, 0x00000760u, 0x00000761u, 0x00007610u, 0x00000762u, 0x00007620u, 0x00007621u, 0x00076210u,
+    0x00000763u, 0x00007630u, 0x00007631u, 0x00076310u, 0x00007632u, 0x00076320u, 0x00076321u, 0x00763210u,
+    0x00000764u, 0x00007640u, 0x00007641u, 0x00076410u, 0x00007642u, 0x00076420u, 0x00076421u, 0x00764210u,
+    0x00007643u, 0x00076430u, 0x00076431u, 0x00764310u, 0x00076432u, 0x00764320u, 0x00764321u, 0x07643210u,
+    0x00000765u, 0x00007650u, 0x00007651u, 0x00076510u, 0x00007652u, 0x00076520u, 0x00076521u, 0x00765210u,
+    0x00007653u, 0x00076530u, 0x00076531u, 0x00765310u, 0x00076532u, 0x00765320u, 0x00765321u, 0x07653210u,
+    0x00007654u, 0x00076540u, 0x00076541u, 0x00765410u, 0x00076542u, 0x00765420u, 0x00765421u, 0x07654210u,
+    0x00076543u, 0x00765430u, 0x00765431u, 0x07654310u, 0x00765432u, 0x07654320u, 0x07654321u, 0x76543210u,
+};
+
+// Index of the n-th (0-based) set bit of m; n < popc(m), m below 2^32: pick the
+// byte by running popcounts, then the bit inside it from the byte table.
 __device__ __forceinline__ uint32_t nth_set(uint32_t m, uint32_t n) {
-    uint32_t pos = 0, c;
-    c = __popc(m & 0xFFFFu);
-    if (n >= c) { n -= c; m >>= 16; pos += 16; }
-    c = __popc(m & 0xFFu);
-    if (n >= c) { n -= c; m >>= 8; pos += 8; }
-    c = __popc(m & 0xFu);
-    if (n >= c) { n -= c; m >>= 4; pos += 4; }
-    c = __popc(m & 0x3u);
-    if (n >= c) { n -= c; m >>= 2; pos += 2; }
-    c = m & 1u;
-    if (n >= c) pos += 1;
-    return pos;
+    const uint32_t c0 = __popc(m & 0xFFu);
+    const uint32_t c1 = c0 + __popc(m & 0xFF00u);
+    const uint32_t c2 = c1 + __popc(m & 0xFF0000u);
+    uint32_t b = 0, base = 0;
+    if (n >= c0) { b = 8; base = c0; }
+    if (n >= c1) { b = 16; base = c1; }
+    if (n >= c2) { b = 24; base = c2; }
+    const uint32_t rank = (n - base) & 7u;
+    return b + ((__ldg(&kSelectInByte[(m >> b) & 0xFFu]) >> (4u * rank)) & 0xFu);
+}
+
+// Positions of the set bits of every 12-bit value, 4 bits per rank.  Kernels
+// that run playouts copy it into shared memory (32 KB) and pass it to nth_set12.
+__device__ const unsigned long long kSelect12[4096] = {
+#include "select_tables.inc"
+};
+
+// nth_set for masks below 2^24 with the 12-bit table (in shared memory).
+__device__ __forceinline__ uint32_t nth_set12(uint32_t m, uint32_t n, const unsigned long long* lut12) {
+    const uint32_t c0 = __popc(m & 0xFFFu);
+    const bool hi = n >= c0;
+    const uint32_t chunk = hi ? (m >> 12) & 0xFFFu : m & 0xFFFu;
+    const uint32_t r = (hi ? n - c0 : n) & 15u;
+    return (hi ? 12u : 0u) + (uint32_t)((lut12[chunk] >> (4u * r)) & 0xFull);
+}
+
+__device__ __forceinline__ void fill_select12(unsigned long long* lut12, uint32_t tid, uint32_t nthr) {
+    for (uint32_t e = tid; e < 4096u; e += nthr) lut12[e] = kSelect12[e];
 }
 
 // The k lowest set bits of m (k <= popc(m)).
@@ -241,7 +294,8 @@ __device__ __forceinline__ uint32_t hidden_slot(const G& g, uint32_t p, uint32_t
 // Sorted insertion of tile t into hand p (Sec. II-A).  Numbered: immediately
 // before the first larger numbered tile, so jokers of that gap stay left.
 // Joker: uniform over the len+1 insertion points (one word).
-__device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, Rng& r) {
+template <class R>
+__device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, R& r) {
     const uint32_t hp = g.hand(p);
     if (t < 24u) {
         const uint32_t k = __popc(hp & kNumMask & ((1u << t) - 1u));
@@ -264,7 +318,8 @@ __device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, Rng& r
     g.add(p, 1u << t);
 }
 
-__device__ __forceinline__ void draw(G& g, Rng& r) {
+template <class R>
+__device__ __forceinline__ void draw(G& g, R& r) {
     const uint32_t pool = g.pool();
     if (!pool) {
         g.drawn = kNone;
@@ -287,8 +342,9 @@ enum : int { kTurnOver = 0, kGuessAgain = 1, kGameOver = 2 };
 // Resolve guess `x` at the tile `target` of seat q (Sec. II-A).  In a playout
 // a correct guess continues iff the next word < cont_thr; in the tree it ends
 // the turn (Sec. III-A, simplification 2).
+template <class R>
 __device__ __forceinline__ int resolve(G& g, uint32_t q, uint32_t target, uint32_t x, bool in_tree, uint32_t cont_thr,
-                                       Rng& r) {
+                                       R& r) {
     if (x == target) {
         g.rev |= 1u << target;
         if (!(g.hand(q) & ~g.rev)) g.alive &= ~(1u << q);
@@ -310,15 +366,30 @@ __device__ __forceinline__ int resolve(G& g, uint32_t q, uint32_t target, uint32
     return kTurnOver;
 }
 
-__device__ __forceinline__ void next_turn(G& g, Rng& r) {
+template <class R>
+__device__ __forceinline__ void next_turn(G& g, R& r) {
     g.cur = next_alive(g.alive, g.cur, g.np);
     draw(g, r);
+}
+
+// floor(k / n) for k < 4096 and 1 <= n <= 31 from magic[n] = floor((2^32-1)/n) + 1:
+// k * magic / 2^32 exceeds k/n by less than 2^-20 < 1/n, so the floor is exact.
+__device__ __forceinline__ uint32_t div_small(uint32_t k, uint32_t n, const uint32_t* magic) {
+    if (magic == nullptr) return k / n;
+    return n == 1u ? k : __umulhi(k, magic[n]);
+}
+
+__device__ __forceinline__ void fill_magic(uint32_t* magic, uint32_t tid, uint32_t nthr) {
+    for (uint32_t n = tid; n < 32u; n += nthr) magic[n] = n < 2u ? 0u : 0xFFFFFFFFu / n + 1u;
 }
 
 // A uniform random guess among the legal ones (canonical order: opponents
 // from cur+1, face-down slots left to right, identities ascending; the set is
 // the product of face-down slots and identities outside own hand and face-up).
-__device__ __forceinline__ int random_guess(G& g, Rng& r, uint32_t cont_thr) {
+// The guess (slot s, identity index i) is correct iff i is the rank of the
+// slot's tile among the unknown identities, so only one select is needed.
+template <class R>
+__device__ __forceinline__ int random_guess(G& g, R& r, uint32_t cont_thr, const uint32_t* magic = nullptr) {
     const uint32_t U = g.tmask & ~g.hand(g.cur) & ~g.rev;
     const uint32_t nid = __popc(U);
     uint32_t cnt[3], qs[3], nslots = 0;
@@ -332,7 +403,7 @@ __device__ __forceinline__ int random_guess(G& g, Rng& r, uint32_t cont_thr) {
         nslots += c;
     }
     const uint32_t k = pick(r.next(), nslots * nid);
-    uint32_t s = k / nid;
+    uint32_t s = div_small(k, nid, magic);
     const uint32_t i = k - s * nid;
     uint32_t q = qs[0];
     if (s >= cnt[0]) {
@@ -344,20 +415,115 @@ __device__ __forceinline__ int random_guess(G& g, Rng& r, uint32_t cont_thr) {
         }
     }
     const uint32_t target = hidden_slot(g, q, s);
-    const uint32_t x = nth_set(U, i);
-    return resolve(g, q, target, x, false, cont_thr, r);
+    const uint32_t rank = __popc(U & ((1u << target) - 1u));
+    return resolve(g, q, target, rank == i ? target : 0xFFu, false, cont_thr, r);
 }
 
 // One playout to the end (Sec. II-B); returns the winner.  Every guess turns
 // one tile face up, so a game has at most 26 guesses; the cap only stops a
 // malformed record (result kNone, credited to nobody).
-__device__ __forceinline__ uint32_t playout(G g, Rng& r, uint32_t cont_thr) {
+template <class R>
+__device__ __forceinline__ uint32_t playout(G g, R& r, uint32_t cont_thr, const uint32_t* magic = nullptr) {
     for (int guard = 0; guard < 128; ++guard) {
-        const int res = random_guess(g, r, cont_thr);
+        const int res = random_guess(g, r, cont_thr, magic);
         if (res == kGameOver) return g.winner;
         if (res == kTurnOver) next_turn(g, r);
     }
     return kNone;
+}
+
+// Words for the playout loop of the pooled kernel: a short queue that is
+// topped up once, at the start of each game step, with enough words for the
+// whole step (a guess, a continue coin, a draw and a joker position at most),
+// so the step itself never branches to refill.
+struct WordQueue {
+    uint32_t k0, k1, blk, j, i, tw;
+    uint32_t q0, q1, q2, q3, q4, q5, q6;
+    uint32_t left;
+
+    __device__ __forceinline__ void open(uint64_t seed, uint32_t tree, uint32_t jj, uint32_t ii, uint32_t tag) {
+        k0 = (uint32_t)seed;
+        k1 = tree;
+        blk = 0;
+        j = jj;
+        i = ii;
+        tw = tag + 16u * (uint32_t)(seed >> 32);
+        left = 0;
+    }
+    // make at least n (<= 4) words available
+    __device__ __forceinline__ void ensure(uint32_t n) {
+        if (left >= n) return;
+        uint32_t a = blk, b = j, c = i, d = tw;
+        philox10(a, b, c, d, k0, k1);
+        ++blk;
+        // append a, b, c, d after the `left` words already queued (left <= 3)
+        q0 = left == 0 ? a : q0;
+        q1 = left == 0 ? b : (left == 1 ? a : q1);
+        q2 = left == 0 ? c : (left == 1 ? b : (left == 2 ? a : q2));
+        q3 = left == 0 ? d : (left == 1 ? c : (left == 2 ? b : a));
+        q4 = left == 1 ? d : (left == 2 ? c : b);
+        q5 = left == 2 ? d : c;
+        q6 = d;
+        left += 4;
+    }
+    __device__ __forceinline__ uint32_t next() {
+        const uint32_t r = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        q3 = q4;
+        q4 = q5;
+        q5 = q6;
+        --left;
+        return r;
+    }
+    // words handed out so far
+    __device__ __forceinline__ uint32_t used() const { return 4u * blk - left; }
+};
+
+// One step of a two-player, 24-tile playout (no jokers): the mover guesses;
+// a correct guess reveals the tile and either ends the game, grants another
+// guess (continue coin) or passes the turn; a wrong guess reveals the mover's
+// drawn tile (or lowest face-down tile) and passes the turn; the next mover
+// draws.  Same rules and same word order as random_guess + next_turn.
+__device__ __forceinline__ int step_2p24(uint32_t& h0, uint32_t& h1, uint32_t& rev, uint32_t& cur, uint32_t& drawn,
+                                         uint32_t& winner, WordQueue& r, uint32_t cont_thr, const uint32_t* magic,
+                                         const unsigned long long* lut12) {
+    r.ensure(3);
+    const uint32_t hc = cur ? h1 : h0;
+    const uint32_t hidq = (cur ? h0 : h1) & ~rev;
+    const uint32_t U = kNumMask & ~hc & ~rev;
+    const uint32_t nid = __popc(U);
+    const uint32_t k = __umulhi(r.next(), __popc(hidq) * nid);
+    const uint32_t s = div_small(k, nid, magic);
+    const uint32_t i = k - s * nid;
+    const uint32_t target = nth_set12(hidq, s, lut12);
+    if (__popc(U & ((1u << target) - 1u)) == i) {
+        rev |= 1u << target;
+        if (hidq == (1u << target)) {
+            winner = cur;
+            return kGameOver;
+        }
+        if (cont_thr != 0u && r.next() < cont_thr) return kGuessAgain;
+    } else {
+        const uint32_t t = drawn != kNone ? drawn : (uint32_t)__ffs(hc & ~rev) - 1u;
+        rev |= 1u << t;
+        if (!(hc & ~rev)) {
+            winner = cur ^ 1u;
+            return kGameOver;
+        }
+    }
+    cur ^= 1u;
+    const uint32_t pool = kNumMask & ~(h0 | h1);
+    if (pool) {
+        const uint32_t t = nth_set12(pool, __umulhi(r.next(), __popc(pool)), lut12);
+        if (cur) h1 |= 1u << t;
+        else h0 |= 1u << t;
+        drawn = t;
+    } else {
+        drawn = kNone;
+    }
+    return kTurnOver;
 }
 
 // Is action (q, slot s, identity x) legal for the seat to move?
@@ -400,9 +566,13 @@ __device__ __forceinline__ double ln_series(double x) {
     }
     const double z = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
     const double z2 = __dmul_rn(z, z);
-    double p = __ddiv_rn(1.0, 23.0);
+    // 1/(2k+1) as compile-time constants: the compiler rounds each quotient
+    // correctly, exactly as the runtime IEEE division would
+    constexpr double inv[12] = {1.0 / 1.0,  1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0,  1.0 / 11.0,
+                                1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0, 1.0 / 23.0};
+    double p = inv[11];
 #pragma unroll
-    for (int k = 10; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z2), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    for (int k = 10; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z2), inv[k]);
     const double lnm = __dmul_rn(2.0, __dmul_rn(z, p));
     return __dadd_rn(__dmul_rn((double)e, 0.6931471805599453), lnm);
 }

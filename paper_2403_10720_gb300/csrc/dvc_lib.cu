@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "dvc_tree.cuh"
+#include "dvc_pipe.cuh"
 
 using namespace dvc;
 
@@ -46,11 +46,23 @@ struct dvc_forest {
     unsigned long long* d_words;
     int32_t* export_scratch;
     int32_t export_cap;
+    int32_t* order;          // tree order: CTAs get equal total budget
+    int trees_per_cta;       // trees per CTA (fused kernel and pipeline rollouts)
+    int warps_per_cta;       // 0: default
+    int engine;              // 1: fused lockstep kernel, 2: three-kernel pipeline
+    double2* ucb;
+    double* csl;
+    PipeBufs pipe;
+    cudaStream_t cap_stream;  // capture stream for the pipeline graph
+    cudaStream_t chain_stream[3];
+    cudaEvent_t fork_ev, join_ev[3];
+    cudaGraphExec_t chunk_exec;
+    int chunk_iters;
+    int chains;               // independent chains in the pipeline graph (1..4)
 };
 
 namespace {
 
-constexpr int kPathMax = 20;
 constexpr int kDetChunk = 256;
 
 int fail(dvc_ctx* c, int code, const std::string& msg) {
@@ -176,6 +188,9 @@ __global__ void determinize_kernel(const dvc_state* roots, int n, int observer, 
 __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uint64_t seed,
                                const uint32_t* tree_ids, const uint32_t* leaf_ids, uint32_t cont_thr, int32_t* wins,
                                unsigned long long* words) {
+    __shared__ uint32_t s_magic[32];
+    fill_magic(s_magic, threadIdx.x, blockDim.x);
+    __syncthreads();
     const long long total = (long long)n_leaves * P;
     unsigned long long my_words = 0ull;
     for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
@@ -187,11 +202,20 @@ __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uin
         if (ls.winner != kNone) {
             winner = ls.winner;
         } else {
-            const G g = load_state(ls);
-            Rng r;
+            G g = load_state(ls);
+            WordQueue r;
             r.open(seed, tree_ids[l], (uint32_t)j, leaf_ids[l], kTagRoll);
-            winner = playout(g, r, cont_thr);
-            my_words += r.count;
+            winner = kNone;
+            for (int guard = 0; guard < 128; ++guard) {
+                r.ensure(4);
+                const int res = random_guess(g, r, cont_thr, s_magic);
+                if (res == kGameOver) {
+                    winner = g.winner;
+                    break;
+                }
+                if (res == kTurnOver) next_turn(g, r);
+            }
+            my_words += r.used();
         }
         if (winner < 4u) atomicAdd(&wins[4 * l + (int)winner], 1);
     }
@@ -201,118 +225,7 @@ __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uin
     }
 }
 
-struct ForestDev {
-    const dvc_state* roots;
-    TreeMeta* meta;
-    const DetPlan* plans;
-    const unsigned long long* tables;
-    Node* nodes;
-    int32_t* link;
-    int32_t* created;
-    int32_t* flags;
-    unsigned long long* words;
-};
 
-// Fused search step: one CTA per tree.  Warp 0 determinizes, descends and
-// expands; every thread of the CTA runs playouts of the leaf; warp 0
-// backpropagates.  The table of small views is staged in shared memory.
-__global__ void mcts_fused_kernel(ForestDev F, SearchParams sp, int n_iter, uint32_t smem_cells) {
-    extern __shared__ unsigned long long s_tab[];
-    __shared__ DetPlan s_pl;
-    __shared__ dvc_state s_leaf;
-    __shared__ int32_t s_path[kPathMax];
-    __shared__ uint8_t s_mover[kPathMax];
-    __shared__ int32_t s_np;
-    __shared__ int32_t s_wins[4];
-    __shared__ uint32_t s_E[104];
-    __shared__ int32_t s_stop;
-
-    const int t = blockIdx.x;
-    TreeMeta tm = F.meta[t];
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    if (tid == 0) s_pl = F.plans[t];
-    __syncthreads();
-    const unsigned long long* tab = F.tables + tm.table_off;
-    if (s_pl.cells <= smem_cells) {
-        for (uint32_t c = tid; c < s_pl.cells; c += blockDim.x) s_tab[c] = tab[c];
-        tab = s_tab;
-    }
-    __syncthreads();
-    Node* nodes = F.nodes + tm.node_off;
-    int32_t* link = F.link + tm.node_off;
-    int32_t* created = F.created + tm.node_off;
-    const G root = load_state(F.roots[t]);
-    const uint32_t obs = root.cur;
-    int32_t next_free = tm.next_free;
-    int32_t used = tm.used;
-    const int32_t it0 = tm.done;
-    const int32_t it1 = (s_pl.ok && s_pl.total && !tm.failed) ? min(tm.budget, it0 + n_iter) : it0;
-    unsigned long long words = 0ull;
-    int32_t it = it0;
-    for (; it < it1; ++it) {
-        if (warp == 0) {
-            Rng dr;
-            dr.open(sp.seed, tm.tree_id, 0u, (uint32_t)it, kTagDet);
-            G det;
-            det_sample(s_pl, tab, root, dr, det);
-            Descent d;
-            descend(det, obs, nodes, link, tm, sp, (uint32_t)it, s_path, s_mover, s_E, d);
-            bool ok = true;
-            if (d.found)
-                ok = expand_child(d, nodes, link, created, tm, next_free, used, (uint32_t)it, s_path, s_mover);
-            if (lane == 0) {
-                s_stop = ok ? 0 : 1;
-                s_np = d.np;
-                store_state(d.s, s_leaf);
-                s_wins[0] = s_wins[1] = s_wins[2] = s_wins[3] = 0;
-                if (!ok) latch(F.flags, DVC_E_OOM);
-            }
-        }
-        __syncthreads();
-        if (s_stop) break;
-        if (s_leaf.winner != kNone) {
-            if (tid == 0 && s_leaf.winner < 4) s_wins[s_leaf.winner] = sp.playouts;
-        } else {
-            const G g = load_state(s_leaf);
-            uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-            for (int j = (int)tid; j < sp.playouts; j += (int)blockDim.x) {
-                Rng r;
-                r.open(sp.seed, tm.tree_id, (uint32_t)j, (uint32_t)it, kTagRoll);
-                const uint32_t w = playout(g, r, sp.cont_thr);
-                c0 += w == 0;
-                c1 += w == 1;
-                c2 += w == 2;
-                c3 += w == 3;
-                words += r.count;
-            }
-            c0 = __reduce_add_sync(0xFFFFFFFFu, c0);
-            c1 = __reduce_add_sync(0xFFFFFFFFu, c1);
-            c2 = __reduce_add_sync(0xFFFFFFFFu, c2);
-            c3 = __reduce_add_sync(0xFFFFFFFFu, c3);
-            if (lane == 0) {
-                if (c0) atomicAdd(&s_wins[0], (int)c0);
-                if (c1) atomicAdd(&s_wins[1], (int)c1);
-                if (c2) atomicAdd(&s_wins[2], (int)c2);
-                if (c3) atomicAdd(&s_wins[3], (int)c3);
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {
-            backprop(nodes, s_path, s_mover, s_np, s_wins, sp.playouts);
-            __syncwarp();
-        }
-    }
-    if (tid == 0) {
-        F.meta[t].done = it;
-        F.meta[t].next_free = next_free;
-        F.meta[t].used = used;
-        if (s_stop && it < it1) F.meta[t].failed = 1;
-    }
-    if (F.words) {
-        const unsigned long long s = warp_sum_u64(words);
-        if (lane == 0 && s) atomicAdd(F.words, s);
-    }
-}
 
 // Split steps: one warp per tree for select and expand, results kept in
 // global memory between launches.
@@ -335,8 +248,8 @@ __global__ void mcts_select_kernel(ForestDev F, SearchParams sp, int n, Descent*
     G det;
     det_sample(F.plans[t], F.tables + tm.table_off, root, dr, det);
     Descent dd;
-    descend(det, root.cur, F.nodes + tm.node_off, F.link + tm.node_off, tm, sp, (uint32_t)tm.done,
-            paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, s_E[wl], dd);
+    descend(det, root.cur, F.nodes + tm.node_off, F.link + tm.node_off, F.ucb + tm.node_off, F.csl + tm.node_off, tm,
+            sp, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, s_E[wl], dd);
     if (lane == 0) d = dd;
 }
 
@@ -389,8 +302,8 @@ __global__ void mcts_backprop_kernel(ForestDev F, SearchParams sp, int n, const 
     const Descent& d = work[t];
     if (d.np < 0) return;
     TreeMeta& tm = F.meta[t];
-    backprop(F.nodes + tm.node_off, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, d.np,
-             wins + 4 * t, sp.playouts);
+    backprop(F.nodes + tm.node_off, F.ucb + tm.node_off, F.csl + tm.node_off, paths + (size_t)t * kPathMax,
+             movers + (size_t)t * kPathMax, d.np, wins + 4 * t, sp.playouts, sp.c_uct);
     __syncwarp();
     if ((threadIdx.x & 31u) == 0) tm.done += 1;
 }
@@ -492,7 +405,8 @@ __global__ void export_rows_kernel(ForestDev F, int t, const int32_t* iter_rank,
 // determinization and fill its counting table (one warp per tree), count the
 // root's legal guesses, and reset the tree to a lone root.
 __global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_roots, DetPlan* plans,
-                                   unsigned long long* tables, uint32_t table_cap) {
+                                   unsigned long long* tables, uint32_t table_cap, int nplayers, int ntiles,
+                                   int32_t* pipe_np) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t lane = threadIdx.x & 31u;
     if (t >= n) return;
@@ -509,9 +423,11 @@ __global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_root
     TreeMeta& tm = F.meta[t];
     if (pl.ok) det_fill(pl, tables + tm.table_off, lane, 32u, [] { __syncwarp(); });
     if (lane == 0) {
-        const bool usable = pl.ok && pl.total != 0ull;
+        const dvc_state& rs = roots[t];
+        const bool variant = rs.nplayers == nplayers && rs.ntiles == ntiles;  // the context's game
+        const bool usable = pl.ok && pl.total != 0ull && variant;
         if (!pl.ok) latch(F.flags, DVC_E_UNSUPPORTED);
-        else if (!pl.total) latch(F.flags, DVC_E_INVALID);
+        else if (!pl.total || !variant) latch(F.flags, DVC_E_INVALID);
         const uint32_t U = g.tmask & ~g.hand(g.cur) & ~g.rev;
         uint32_t slots = 0;
         for (uint32_t q = 0; q < g.np; ++q)
@@ -530,6 +446,7 @@ __global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_root
         nodes[0] = r;
         F.link[tm.node_off] = -1;
         F.created[tm.node_off] = -1;
+        pipe_np[t] = -1;  // no pipeline backprop pending
     }
 }
 
@@ -542,6 +459,8 @@ ForestDev dev_of(dvc_forest* f) {
     d.nodes = f->nodes;
     d.link = f->link;
     d.created = f->created;
+    d.ucb = f->ucb;
+    d.csl = f->csl;
     d.flags = f->ctx->d_flags;
     d.words = f->d_words;
     return d;
@@ -713,9 +632,17 @@ int dvc_rollout_batch(dvc_ctx* c, const dvc_state* d_leaves, int n_leaves, int p
 void dvc_forest_destroy(dvc_forest* f) {
     if (!f) return;
     cudaSetDevice(f->ctx->device);
-    void* ptrs[] = {f->roots,  f->meta,   f->plans,     f->tables,    f->nodes,   f->link,
-                    f->created, f->work,  f->paths,     f->movers,    f->leaves,  f->leaf_tree,
-                    f->leaf_iter, f->d_words, f->export_scratch};
+    if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
+    if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
+    for (int k = 0; k < 3; ++k) {
+        if (f->chain_stream[k]) cudaStreamDestroy(f->chain_stream[k]);
+        if (f->join_ev[k]) cudaEventDestroy(f->join_ev[k]);
+    }
+    if (f->fork_ev) cudaEventDestroy(f->fork_ev);
+    void* ptrs[] = {f->roots,     f->meta,      f->plans,     f->tables,         f->nodes,         f->link,
+                    f->created,   f->work,      f->paths,     f->movers,         f->leaves,        f->leaf_tree,
+                    f->leaf_iter, f->d_words,   f->export_scratch, f->order,     f->ucb,           f->csl,
+                    f->pipe.leaf, f->pipe.path, f->pipe.mover, f->pipe.np,       f->pipe.wins,     f->pipe.step_end};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -752,6 +679,54 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         slots += m.cap;
     }
     f->total_slots = slots;
+    // Longest budget first, each tree to the least-loaded CTA that has a free
+    // slot (CTAs hold trees_per_cta trees): balances uneven forests.
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    f->trees_per_cta = std::max(1, std::min(32, (n + std::max(sms, 1) - 1) / std::max(sms, 1)));
+    {
+        long long sum = 0;
+        int mx = 0;
+        for (int t = 0; t < n; ++t) {
+            sum += f->h_budgets[t];
+            mx = std::max(mx, f->h_budgets[t]);
+        }
+        // even budgets: the pipeline (full-occupancy playouts); very uneven: the
+        // fused lockstep kernel (no launches for iterations only a few trees run)
+        f->engine = (n >= 2 * std::max(sms, 1) && (long long)mx * n <= 2 * std::max(sum, 1LL)) ? 2 : 1;
+        // pipeline: two rollout CTAs' worth of trees per SM, split over two chains
+        if (f->engine == 2)
+            f->trees_per_cta = std::max(1, std::min(32, (n + 2 * std::max(sms, 1) - 1) / (2 * std::max(sms, 1))));
+    }
+    std::vector<int32_t> order(n);
+    {
+        const int T = f->trees_per_cta;
+        const int nc = (n + T - 1) / T;
+        std::vector<int> idx(n);
+        for (int i = 0; i < n; ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return f->h_budgets[a] > f->h_budgets[b]; });
+        std::vector<long long> load(nc, 0);
+        std::vector<int> fill(nc, 0);
+        std::vector<int> capc(nc, T);
+        capc[nc - 1] = n - (nc - 1) * T;
+        // min-heap of (load, cta)
+        std::vector<std::pair<long long, int>> heap;
+        for (int k = 0; k < nc; ++k) heap.push_back({0, k});
+        auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (int i : idx) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto [ld, k] = heap.back();
+            heap.pop_back();
+            order[k * T + fill[k]] = i;
+            fill[k]++;
+            load[k] = ld + f->h_budgets[i];
+            if (fill[k] < capc[k]) {
+                heap.push_back({load[k], k});
+                std::push_heap(heap.begin(), heap.end(), cmp);
+            }
+        }
+    }
     auto alloc = [&](void** p, size_t bytes) {
         if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
             cudaGetLastError();
@@ -768,7 +743,11 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         alloc((void**)&f->leaf_iter, sizeof(uint32_t) * n) && alloc((void**)&f->d_words, sizeof(unsigned long long)) &&
         alloc((void**)&f->tables, sizeof(unsigned long long) * (size_t)f->table_cap * n) &&
         alloc((void**)&f->nodes, sizeof(Node) * (size_t)slots) && alloc((void**)&f->link, sizeof(int32_t) * (size_t)slots) &&
-        alloc((void**)&f->created, sizeof(int32_t) * (size_t)slots);
+        alloc((void**)&f->created, sizeof(int32_t) * (size_t)slots) && alloc((void**)&f->order, sizeof(int32_t) * n) &&
+        alloc((void**)&f->ucb, sizeof(double2) * (size_t)slots) && alloc((void**)&f->csl, sizeof(double) * (size_t)slots) &&
+        alloc((void**)&f->pipe.leaf, sizeof(dvc_state) * n) && alloc((void**)&f->pipe.path, sizeof(int32_t) * kPathMax * n) &&
+        alloc((void**)&f->pipe.mover, (size_t)kPathMax * n) && alloc((void**)&f->pipe.np, sizeof(int32_t) * n) &&
+        alloc((void**)&f->pipe.wins, sizeof(int32_t) * 4 * n) && alloc((void**)&f->pipe.step_end, sizeof(int32_t) * n);
     if (!ok) {
         dvc_forest_destroy(f);
         return fail(c, DVC_E_OOM, "dvc_forest_create: device allocation of " + std::to_string(slots) + " node slots");
@@ -777,15 +756,28 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     cudaError_t e = cudaMemcpyAsync(f->meta, hm.data(), sizeof(TreeMeta) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->roots, d_roots, sizeof(dvc_state) * n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         dvc_forest_destroy(f);
         return cuda_fail(c, e, "dvc_forest_create copy");
     }
-    forest_init_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), n, nullptr, f->plans, f->tables, f->table_cap);
+    forest_init_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), n, nullptr, f->plans, f->tables, f->table_cap,
+                                                            c->cfg.nplayers, c->cfg.ntiles, f->pipe.np);
     if (int rc = check_launch(c, "forest_init_kernel")) {
         dvc_forest_destroy(f);
         return rc;
     }
+    bool sok = cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&f->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 3 && sok; ++k)
+        sok = cudaStreamCreateWithFlags(&f->chain_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&f->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!sok) {
+        cudaGetLastError();
+        dvc_forest_destroy(f);
+        return fail(c, DVC_E_CUDA, "dvc_forest_create: streams");
+    }
+    f->chains = 2;
     *out = f;
     return DVC_OK;
 }
@@ -795,10 +787,154 @@ int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream) {
     if (d_roots && !is_device_ptr(d_roots))
         return fail(f->ctx, DVC_E_INVALID, "dvc_forest_reset: d_roots must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
-    forest_init_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_roots, f->plans,
-                                                                                  f->tables, f->table_cap);
+    forest_init_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        dev_of(f), f->n, d_roots, f->plans, f->tables, f->table_cap, f->ctx->cfg.nplayers, f->ctx->cfg.ntiles,
+        f->pipe.np);
     return check_launch(f->ctx, "forest_init_kernel");
 }
+
+}  // extern "C"
+
+namespace {
+
+int launch_fused(dvc_forest* f, int n_iterations, cudaStream_t st) {
+    dvc_ctx* c = f->ctx;
+    const int T = f->trees_per_cta;
+    const int W = std::max(1, std::min(32, f->warps_per_cta ? f->warps_per_cta : std::min(T, 16)));
+    const int grid = (f->n + T - 1) / T;
+    const PoolLayout L(T, W);
+    const int threads = 32 * W;
+    const bool fast2 = c->cfg.nplayers == 2 && c->cfg.ntiles == 24;
+    cudaError_t e;
+#define DVC_LAUNCH_POOL(MT, F2)                                                                                   \
+    do {                                                                                                          \
+        e = cudaFuncSetAttribute(mcts_pool_kernel<MT, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes); \
+        if (e == cudaSuccess)                                                                                     \
+            mcts_pool_kernel<MT, F2><<<grid, threads, L.bytes, st>>>(dev_of(f), params_of(f), n_iterations, f->order, \
+                                                                     f->n, T);                                    \
+    } while (0)
+    if (threads <= 512) {
+        if (fast2) DVC_LAUNCH_POOL(512, true);
+        else DVC_LAUNCH_POOL(512, false);
+    } else if (threads <= 768) {
+        if (fast2) DVC_LAUNCH_POOL(768, true);
+        else DVC_LAUNCH_POOL(768, false);
+    } else {
+        if (fast2) DVC_LAUNCH_POOL(1024, true);
+        else DVC_LAUNCH_POOL(1024, false);
+    }
+#undef DVC_LAUNCH_POOL
+    if (e != cudaSuccess) return cuda_fail(c, e, "mcts_pool_kernel attributes");
+    return check_launch(c, "mcts_pool_kernel");
+}
+
+int pipe_rollout_threads(const dvc_forest* f) { return 32 * (f->warps_per_cta ? f->warps_per_cta : 32); }
+
+// One pipeline iteration of the trees of CTAs [b0, b1): (pending backprop +)
+// select, then rollouts.
+int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
+    dvc_ctx* c = f->ctx;
+    const ForestDev fd = dev_of(f);
+    const SearchParams sp = params_of(f);
+    const int n = f->n, L = f->trees_per_cta;
+    const int i0 = std::min(n, b0 * L), i1 = std::min(n, b1 * L);
+    if (i1 <= i0) return DVC_OK;
+    pipe_select_kernel<<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
+    const uint32_t smem = pipe_rollout_smem(L);
+    const int threads = pipe_rollout_threads(f);
+    if (c->cfg.nplayers == 2 && c->cfg.ntiles == 24)
+        pipe_rollout_kernel<true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
+    else
+        pipe_rollout_kernel<false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
+    return check_launch(c, "pipeline kernels");
+}
+
+constexpr int kChunkIters = 64;
+constexpr int kMaxChains = 4;
+
+// CTA range of chain k when the grid is split into `chains` independent chains.
+void chain_range(const dvc_forest* f, int k, int chains, int& b0, int& b1) {
+    const int grid = (f->n + f->trees_per_cta - 1) / f->trees_per_cta;
+    b0 = (int)((long long)grid * k / chains);
+    b1 = (int)((long long)grid * (k + 1) / chains);
+}
+
+// Capture kChunkIters iterations: the forest's CTAs split into independent
+// chains on their own streams, so one chain's tree walks overlap another's
+// playouts on the same SMs.
+int capture_chunk(dvc_forest* f) {
+    dvc_ctx* c = f->ctx;
+    const int chains = std::max(1, std::min(kMaxChains, f->chains));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pipeline capture");
+    int rc = DVC_OK;
+    cudaStream_t ss[kMaxChains] = {f->cap_stream, f->chain_stream[0], f->chain_stream[1], f->chain_stream[2]};
+    if (chains > 1) {
+        e = cudaEventRecord(f->fork_ev, f->cap_stream);
+        for (int k = 1; k < chains && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], f->fork_ev, 0);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "pipeline fork");
+    }
+    for (int it = 0; it < kChunkIters && rc == DVC_OK; ++it)
+        for (int k = 0; k < chains && rc == DVC_OK; ++k) {
+            int b0, b1;
+            chain_range(f, k, chains, b0, b1);
+            rc = enqueue_pipe_iteration(f, b0, b1, ss[k]);
+        }
+    if (rc == DVC_OK && chains > 1) {
+        for (int k = 1; k < chains && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(f->join_ev[k - 1], ss[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(f->cap_stream, f->join_ev[k - 1], 0);
+        }
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "pipeline join");
+    }
+    e = cudaStreamEndCapture(f->cap_stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "pipeline capture end");
+    e = cudaGraphInstantiate(&f->chunk_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        f->chunk_exec = nullptr;
+        return cuda_fail(c, e, "pipeline graph");
+    }
+    return DVC_OK;
+}
+
+int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
+    dvc_ctx* c = f->ctx;
+    const uint32_t smem = pipe_rollout_smem(f->trees_per_cta);
+    {
+        cudaError_t e = cudaFuncSetAttribute(pipe_rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pipe_rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pipeline attributes");
+    }
+    pipe_begin_kernel<<<(f->n + 127) / 128, 128, 0, st>>>(dev_of(f), f->n, n_iterations, f->pipe.step_end);
+    if (int rc = check_launch(c, "pipe_begin_kernel")) return rc;
+    int left = n_iterations;
+    if (left >= kChunkIters) {
+        if (!f->chunk_exec)
+            if (int rc = capture_chunk(f)) return rc;
+        while (left >= kChunkIters) {
+            const cudaError_t e = cudaGraphLaunch(f->chunk_exec, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "pipeline graph launch");
+            left -= kChunkIters;
+        }
+    }
+    const int grid = (f->n + f->trees_per_cta - 1) / f->trees_per_cta;
+    for (; left > 0; --left)
+        if (int rc = enqueue_pipe_iteration(f, 0, grid, st)) return rc;
+    pipe_backprop_kernel<<<(f->n * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), f->n, f->pipe);
+    return check_launch(c, "pipe_backprop_kernel");
+}
+
+}  // namespace
+
+extern "C" {
 
 int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream) {
     if (!f) return DVC_E_INVALID;
@@ -807,13 +943,61 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream) {
     if (mode != DVC_MODE_ROLLOUT) return fail(c, DVC_E_UNSUPPORTED, "dvc_mcts_step: mode not available");
     if (n_iterations == 0) return DVC_OK;
     if (int rc = set_device(c)) return rc;
-    // two-player tables are small: stage them in shared memory
-    const uint32_t smem_cells = c->cfg.nplayers == 2 ? (c->cfg.ntiles == 24 ? 640u : kDetMaxCells2p) : 0u;
-    int block = c->cfg.playouts >= 256 ? 256 : ((c->cfg.playouts + 31) / 32) * 32;
-    block = std::max(block, 32);
-    mcts_fused_kernel<<<f->n, block, smem_cells * sizeof(unsigned long long), (cudaStream_t)stream>>>(
-        dev_of(f), params_of(f), n_iterations, smem_cells);
-    return check_launch(c, "mcts_fused_kernel");
+    cudaStream_t st = (cudaStream_t)stream;
+    return f->engine == 2 ? launch_pipeline(f, n_iterations, st) : launch_fused(f, n_iterations, st);
+}
+
+int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_cta, int chains) {
+    if (!f) return DVC_E_INVALID;
+    if (engine < 0 || engine > 2 || trees_per_cta < 0 || trees_per_cta > 64 || warps_per_cta < 0 ||
+        warps_per_cta > 32 || chains < 0 || chains > kMaxChains)
+        return fail(f->ctx, DVC_E_INVALID,
+                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..4");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->ctx->device);
+    const int T = trees_per_cta ? trees_per_cta
+                                : std::max(1, std::min(32, (f->n + std::max(sms, 1) - 1) / std::max(sms, 1)));
+    const PoolLayout L(T, warps_per_cta ? warps_per_cta : std::min(T, 16));
+    if (L.bytes > 200 * 1024) return fail(f->ctx, DVC_E_UNSUPPORTED, "dvc_forest_tune: CTA state exceeds shared memory");
+    if (T != f->trees_per_cta) {
+        // re-balance the tree order for the new CTA size (host work, then one copy)
+        std::vector<int32_t> order(f->n);
+        const int nc = (f->n + T - 1) / T;
+        std::vector<int> idx(f->n);
+        for (int i = 0; i < f->n; ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return f->h_budgets[a] > f->h_budgets[b]; });
+        std::vector<std::pair<long long, int>> heap;
+        std::vector<int> fill(nc, 0), capc(nc, T);
+        capc[nc - 1] = f->n - (nc - 1) * T;
+        for (int k = 0; k < nc; ++k) heap.push_back({0, k});
+        auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (int i : idx) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto [ld, k] = heap.back();
+            heap.pop_back();
+            order[k * T + fill[k]++] = i;
+            if (fill[k] < capc[k]) {
+                heap.push_back({ld + f->h_budgets[i], k});
+                std::push_heap(heap.begin(), heap.end(), cmp);
+            }
+        }
+        if (int rc = set_device(f->ctx)) return rc;
+        const cudaError_t e = cudaMemcpy(f->order, order.data(), sizeof(int32_t) * f->n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_tune");
+        f->trees_per_cta = T;
+    }
+    if (engine) f->engine = engine;
+    const int ch = chains ? chains : f->chains;
+    if (f->warps_per_cta != warps_per_cta || T != f->chunk_iters || ch != f->chains) {
+        // the captured pipeline graph holds the old launch shape
+        if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
+        f->chunk_exec = nullptr;
+    }
+    f->warps_per_cta = warps_per_cta;
+    f->chunk_iters = T;
+    f->chains = ch;
+    return DVC_OK;
 }
 
 int dvc_mcts_select(dvc_forest* f, void* stream) {

@@ -69,9 +69,14 @@ struct Descent {
 // of the calling warp enter with the same arguments and leave with the same
 // Descent; lane 0 records the path in path[] / mover[] (shared or global).
 // E is a 4 x 26 word scratch (shared memory) for expanded-identity masks.
+// ucb[slot] = (wins/n, 1/sqrt(n)) and csl[slot] = c * sqrt(ln n) are the
+// node's UCB1 terms, refreshed whenever its counts change (backprop), so a
+// selection scan costs one multiply-add per child.  They are the same IEEE
+// values a scan would compute from the counts.
 __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* nodes, const int32_t* link,
-                                        const TreeMeta& tm, const SearchParams& sp, uint32_t it, int32_t* path,
-                                        uint8_t* mover, uint32_t* E, Descent& d) {
+                                        const double2* ucb, const double* csl_of, const TreeMeta& tm,
+                                        const SearchParams& sp, uint32_t it, int32_t* path, uint8_t* mover,
+                                        uint32_t* E, Descent& d) {
     const uint32_t lane = threadIdx.x & 31u;
     d.s = det;
     d.tr.open(sp.seed, tm.tree_id, 0u, it, kTagTree);
@@ -90,8 +95,7 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         const uint32_t U = d.s.tmask & ~d.s.hand(cur) & ~d.s.rev;
         for (uint32_t e = lane; e < 104u; e += 32u) E[e] = 0u;
         __syncwarp();
-        double csl = 0.0;
-        if (nchild) csl = __dmul_rn(sp.c_uct, __dsqrt_rn(ln_series((double)nd.visits)));
+        const double csl = nchild ? csl_of[d.node] : 0.0;
         double best_sc = -1.0;
         uint32_t best_rank = 0xFFFFFFFFu;
         int32_t best_slot = -1;
@@ -110,7 +114,8 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
                 const uint32_t q = code >> 10, sl = (code >> 5) & 31u, x = code & 31u;
                 if (sl < 26u) atomicOr(&E[q * 26u + sl], 1u << x);
                 if (guess_legal(d.s, q, sl, x)) {
-                    const double sc = uct_score(csl, ch.wins, ch.visits);
+                    const double2 u = ucb[blk + (int32_t)e];
+                    const double sc = __dadd_rn(u.x, __dmul_rn(csl, u.y));
                     const uint32_t rk = canon_rank(code, cur, d.s.np);
                     if (best_slot < 0 || sc > best_sc || (sc == best_sc && rk < best_rank)) {
                         best_sc = sc;
@@ -239,13 +244,20 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // Backpropagation (Sec. II-B): every node on the path gains `playouts` visits
 // and the playouts won by the seat that moved into it.
-__device__ __forceinline__ void backprop(Node* nodes, const int32_t* path, const uint8_t* mover, int32_t np,
-                                         const int32_t* wins, int32_t playouts) {
+__device__ __forceinline__ void backprop(Node* nodes, double2* ucb, double* csl, const int32_t* path,
+                                         const uint8_t* mover, int32_t np, const int32_t* wins, int32_t playouts,
+                                         double c_uct) {
     const uint32_t lane = threadIdx.x & 31u;
     for (int32_t e = (int32_t)lane; e < np; e += 32) {
-        Node* n = &nodes[path[e]];
-        n->visits += playouts;
-        n->wins += wins[mover[e]];
+        const int32_t slot = path[e];
+        Node* n = &nodes[slot];
+        const int32_t v = n->visits + playouts;
+        const int32_t w = n->wins + wins[mover[e]];
+        n->visits = v;
+        n->wins = w;
+        const double dv = (double)v;
+        ucb[slot] = make_double2(__ddiv_rn((double)w, dv), __ddiv_rn(1.0, __dsqrt_rn(dv)));
+        csl[slot] = __dmul_rn(c_uct, __dsqrt_rn(ln_series(dv)));
     }
 }
 

@@ -286,3 +286,29 @@ def test_uneven_workload_sampled(dvc):
     sample = [0, 5, 17, 63]
     want = _oracle_trees(ocfg, oroots, w.seed, budgets, sample)
     _check_forest(forest, stats, want, sample)
+
+
+@pytest.mark.parametrize("shape", [(1, 3, 2, 0), (1, 5, 8, 0), (1, 2, 1, 0), (1, 7, 3, 0), (2, 3, 2, 1), (2, 5, 32, 2),
+                                   (2, 1, 4, 4), (2, 2, 2, 3)])
+def test_mcts_launch_shapes_agree(dvc, shape):
+    """Trees per CTA and warps per CTA change only who does the work."""
+    kw = dict(VARIANTS["4p26j"], playouts=8)
+    ctx = _ctx(dvc, **kw)
+    n = 11
+    budgets = [40, 7, 90, 0, 33, 64, 1, 55, 20, 80, 12]
+    roots = ctx.dvc_init_states(33, n)
+    ref = dvc.Forest(ctx, roots, budgets, 4)
+    ref.dvc_mcts_step(100)
+    alt = dvc.Forest(ctx, roots, budgets, 4)
+    alt.dvc_forest_tune(*shape)
+    alt.dvc_mcts_step(30)
+    alt.dvc_mcts_step(70)
+    alt.dvc_mcts_step(64)    # budgets spent: a whole captured chunk of no-op iterations
+    ctx.dvc_check()
+    for t in range(n):
+        assert torch.equal(ref.dvc_tree_export(t), alt.dvc_tree_export(t)), t
+    assert torch.equal(ref.dvc_root_stats(), alt.dvc_root_stats())
+    ocfg = oracle.OracleConfig(**kw)
+    oroots = oracle.init_states(ocfg, 33, n)
+    want = _oracle_trees(ocfg, oroots, 4, budgets, [2, 9])
+    _check_forest(alt, alt.dvc_root_stats().cpu().numpy(), want, [2, 9])
