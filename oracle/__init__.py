@@ -17,6 +17,9 @@ Pin status per function:
   det_count ......... pinned (brute-force enumeration of consistent deals)
   determinize ....... pinned (chi-square against uniform over those deals)
   mcts .............. pinned (UCB1 forced-win toy sequence, count invariants)
+  value_features .... pinned (hand-made positions with features written out)
+  value_forward ..... pinned (closed form with zero hidden weights)
+  value_loss_grad ... pinned (central finite differences in double)
 """
 import ctypes
 import os
@@ -92,6 +95,16 @@ def lib():
         L.or_mcts.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i32p,
                               ctypes.POINTER(ctypes.c_int), i32p]
         L.or_mcts.restype = ctypes.c_int
+        f32p = ctypes.POINTER(ctypes.c_float)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        L.or_value_nparams.argtypes = []
+        L.or_value_nparams.restype = ctypes.c_int
+        L.or_value_features.argtypes = [u8p, f32p]
+        L.or_value_features.restype = ctypes.c_int
+        L.or_value_forward.argtypes = [f32p, u8p, f64p]
+        L.or_value_forward.restype = ctypes.c_int
+        L.or_value_loss_grad.argtypes = [f32p, u8p, f32p, ctypes.c_int, f64p]
+        L.or_value_loss_grad.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -168,6 +181,45 @@ def playout_trace(cfg: OracleConfig, leaf, seed: int, tree: int, j: int, leaf_id
     c = cfg.c()
     n = lib().or_playout_trace(ctypes.byref(c), _u8(s), seed, tree, j, leaf_id, _u8(out), maxlen)
     return out[:n]
+
+
+VALUE_FEATURES = 640
+VALUE_HIDDEN = 512
+
+
+def value_nparams() -> int:
+    return lib().or_value_nparams()
+
+
+def value_features(state) -> np.ndarray:
+    s = _state(state)
+    out = np.zeros(VALUE_FEATURES, dtype=np.float32)
+    lib().or_value_features(_u8(s), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return out
+
+
+def value_forward(params, state) -> np.ndarray:
+    """Win probability per absolute seat, computed in double."""
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    s = _state(state)
+    out = np.zeros(4, dtype=np.float64)
+    rc = lib().or_value_forward(prm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _u8(s),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc:
+        raise ValueError("or_value_forward")
+    return out
+
+
+def value_loss_grad(params, states, labels):
+    """(mean cross-entropy, gradient per parameter) in double."""
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    st = np.ascontiguousarray(np.asarray(states, dtype=np.uint8).reshape(-1, 32))
+    lab = np.ascontiguousarray(np.asarray(labels, dtype=np.float32).reshape(-1, 4))
+    g = np.zeros(value_nparams(), dtype=np.float64)
+    loss = lib().or_value_loss_grad(prm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _u8(st),
+                                    lab.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(st),
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return loss, g
 
 
 def mcts(cfg: OracleConfig, root, seed: int, tree: int, budget: int):

@@ -943,3 +943,195 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
     free(mem);
     return rc;
 }
+
+/* ------------------------------------------------------------- value net */
+
+/* Leaf evaluator of the workload (no counterpart in the paper's method; the
+ * method's own leaf evaluation is the random playout).  Input features of a
+ * state, from the seat to move (cur), seats relative to cur:
+ *   [0, 182)   per tile t < 26: owner one-hot over 4 relative seats, then
+ *              face-down / face-up (2), then drawn this turn (1) -- 7 each;
+ *              zeros for tiles in the pool or absent from the game;
+ *   [182, 611) per opponent k = 1..3 (relative), per slot s < 11 of its row:
+ *              13 values (12 numbers + joker): a face-up slot marks its own
+ *              value; a face-down slot marks every value v for which some tile
+ *              unknown to the mover (not in its hand, not face up) of value v
+ *              fits between the slot's face-up numbered neighbours, plus the
+ *              joker if an unknown joker exists;
+ *   [611, 640) zero padding.
+ * Network: 640 -> 512 -> 512 -> 512 (GELU, exact erf) -> 4 logits over
+ * relative seats; softmax over the seats in play; output per absolute seat.
+ * Parameter layout (floats): W1[512][640], b1[512], W2[512][512], b2[512],
+ * W3[512][512], b3[512], W4[4][512], b4[4].  Computed in double. */
+#define VF 640
+#define VH 512
+#define VP (VH * VF + VH + VH * VH + VH + VH * VH + VH + 4 * VH + 4)
+
+int or_value_nparams(void) { return VP; }
+
+int or_value_features(const uint8_t* packed, float* out) {
+    ost s;
+    unpack(packed, &s);
+    for (int i = 0; i < VF; i++) out[i] = 0.0f;
+    int c = s.cur, P = s.P;
+    for (int t = 0; t < s.T; t++) {
+        if (s.owner[t] < 0) continue;
+        int rel = ((s.owner[t] - c) % P + P) % P;
+        out[7 * t + rel] = 1.0f;
+        out[7 * t + 4 + (s.rev[t] ? 1 : 0)] = 1.0f;
+        if (t == s.drawn) out[7 * t + 6] = 1.0f;
+    }
+    int unknown[MAXT];
+    for (int t = 0; t < MAXT; t++) unknown[t] = t < s.T && s.owner[t] != c && !s.rev[t];
+    for (int k = 1; k < 4; k++) {
+        if (k >= P) break;
+        int q = (c + k) % P;
+        for (int i = 0; i < s.len[q] && i < 11; i++) {
+            float* f = out + 182 + ((k - 1) * 11 + i) * 13;
+            int t = s.seq[q][i];
+            if (s.rev[t]) {
+                f[t < NUMBERED ? t / 2 : 12] = 1.0f;
+                continue;
+            }
+            int lo = -1, hi = NUMBERED; /* face-up numbered neighbours */
+            for (int j = i - 1; j >= 0; j--) {
+                int u = s.seq[q][j];
+                if (s.rev[u] && u < NUMBERED) { lo = u; break; }
+            }
+            for (int j = i + 1; j < s.len[q]; j++) {
+                int u = s.seq[q][j];
+                if (s.rev[u] && u < NUMBERED) { hi = u; break; }
+            }
+            for (int u = 0; u < NUMBERED; u++)
+                if (unknown[u] && u > lo && u < hi) f[u / 2] = 1.0f;
+            if (unknown[JOKER_BLACK] || unknown[JOKER_WHITE]) f[12] = 1.0f;
+        }
+    }
+    return 0;
+}
+
+static double gelu_d(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+static double gelu_grad_d(double x) {
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * 3.14159265358979323846);
+}
+
+typedef struct {
+    double x[VF], z1[VH], h1[VH], z2[VH], h2[VH], z3[VH], h3[VH], z4[4], p[4];
+    int P, cur;
+} vfwd;
+
+static void dense(const float* W, const float* b, const double* in, int nin, int nout, double* out) {
+    for (int o = 0; o < nout; o++) {
+        double acc = b[o];
+        for (int i = 0; i < nin; i++) acc += (double)W[(size_t)o * nin + i] * in[i];
+        out[o] = acc;
+    }
+}
+
+static void value_forward(const float* prm, const uint8_t* packed, vfwd* f) {
+    float xf[VF];
+    or_value_features(packed, xf);
+    for (int i = 0; i < VF; i++) f->x[i] = xf[i];
+    const float* W1 = prm;
+    const float* b1 = W1 + VH * VF;
+    const float* W2 = b1 + VH;
+    const float* b2 = W2 + VH * VH;
+    const float* W3 = b2 + VH;
+    const float* b3 = W3 + VH * VH;
+    const float* W4 = b3 + VH;
+    const float* b4 = W4 + 4 * VH;
+    dense(W1, b1, f->x, VF, VH, f->z1);
+    for (int i = 0; i < VH; i++) f->h1[i] = gelu_d(f->z1[i]);
+    dense(W2, b2, f->h1, VH, VH, f->z2);
+    for (int i = 0; i < VH; i++) f->h2[i] = gelu_d(f->z2[i]);
+    dense(W3, b3, f->h2, VH, VH, f->z3);
+    for (int i = 0; i < VH; i++) f->h3[i] = gelu_d(f->z3[i]);
+    dense(W4, b4, f->h3, VH, 4, f->z4);
+    f->P = packed[26];
+    f->cur = packed[23];
+    double mx = -1e300, sum = 0.0;
+    for (int r = 0; r < f->P; r++) if (f->z4[r] > mx) mx = f->z4[r];
+    for (int r = 0; r < 4; r++) f->p[r] = r < f->P ? exp(f->z4[r] - mx) : 0.0;
+    for (int r = 0; r < f->P; r++) sum += f->p[r];
+    for (int r = 0; r < f->P; r++) f->p[r] /= sum;
+}
+
+/* Win probability per absolute seat. */
+int or_value_forward(const float* prm, const uint8_t* packed, double* probs) {
+    vfwd* f = (vfwd*)malloc(sizeof(vfwd));
+    if (!f) return -1;
+    value_forward(prm, packed, f);
+    for (int s = 0; s < 4; s++) probs[s] = 0.0;
+    for (int r = 0; r < f->P; r++) probs[(f->cur + r) % f->P] = f->p[r];
+    free(f);
+    return 0;
+}
+
+/* Mean cross-entropy over n states against soft labels (4 per state, by
+ * absolute seat) and its gradient with respect to every parameter. */
+double or_value_loss_grad(const float* prm, const uint8_t* states, const float* labels, int n, double* grad) {
+    for (int i = 0; i < VP; i++) grad[i] = 0.0;
+    const float* W2 = prm + VH * VF + VH;
+    const float* W3 = W2 + VH * VH + VH;
+    const float* W4 = W3 + VH * VH + VH;
+    double* gW1 = grad;
+    double* gb1 = gW1 + VH * VF;
+    double* gW2 = gb1 + VH;
+    double* gb2 = gW2 + VH * VH;
+    double* gW3 = gb2 + VH;
+    double* gb3 = gW3 + VH * VH;
+    double* gW4 = gb3 + VH;
+    double* gb4 = gW4 + 4 * VH;
+    vfwd* f = (vfwd*)malloc(sizeof(vfwd));
+    double* d = (double*)malloc(sizeof(double) * 3 * VH);
+    if (!f || !d) { free(f); free(d); return -1.0; }
+    double* dh = d;
+    double* dz = d + VH;
+    double* dtmp = d + 2 * VH;
+    double loss = 0.0;
+    for (int b = 0; b < n; b++) {
+        value_forward(prm, states + 32 * (size_t)b, f);
+        double dz4[4] = {0, 0, 0, 0};
+        for (int r = 0; r < f->P; r++) {
+            double y = labels[4 * b + (f->cur + r) % f->P];
+            if (y > 0) loss -= y * log(f->p[r]);
+            dz4[r] = (f->p[r] - y) / n;
+        }
+        for (int r = 0; r < 4; r++) {
+            gb4[r] += dz4[r];
+            for (int i = 0; i < VH; i++) gW4[r * VH + i] += dz4[r] * f->h3[i];
+        }
+        for (int i = 0; i < VH; i++) {
+            double acc = 0.0;
+            for (int r = 0; r < 4; r++) acc += dz4[r] * W4[r * VH + i];
+            dz[i] = acc * gelu_grad_d(f->z3[i]);
+        }
+        for (int o = 0; o < VH; o++) {
+            gb3[o] += dz[o];
+            for (int i = 0; i < VH; i++) gW3[(size_t)o * VH + i] += dz[o] * f->h2[i];
+        }
+        for (int i = 0; i < VH; i++) {
+            double acc = 0.0;
+            for (int o = 0; o < VH; o++) acc += dz[o] * W3[(size_t)o * VH + i];
+            dh[i] = acc;
+        }
+        for (int i = 0; i < VH; i++) dtmp[i] = dh[i] * gelu_grad_d(f->z2[i]);
+        for (int o = 0; o < VH; o++) {
+            gb2[o] += dtmp[o];
+            for (int i = 0; i < VH; i++) gW2[(size_t)o * VH + i] += dtmp[o] * f->h1[i];
+        }
+        for (int i = 0; i < VH; i++) {
+            double acc = 0.0;
+            for (int o = 0; o < VH; o++) acc += dtmp[o] * W2[(size_t)o * VH + i];
+            dh[i] = acc;
+        }
+        for (int i = 0; i < VH; i++) dz[i] = dh[i] * gelu_grad_d(f->z1[i]);
+        for (int o = 0; o < VH; o++) {
+            gb1[o] += dz[o];
+            for (int i = 0; i < VF; i++) gW1[(size_t)o * VF + i] += dz[o] * f->x[i];
+        }
+    }
+    free(f);
+    free(d);
+    return loss / n;
+}
