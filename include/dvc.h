@@ -272,6 +272,44 @@ int dvc_determinize_noalloc(const dvc_state* d_roots, int n, int observer, uint6
                             const uint32_t* d_tree_ids, const uint32_t* d_iter_ids, dvc_state* d_out,
                             int32_t* d_status, void* stream);
 
+/*
+ * Value network: a learned leaf evaluator that can replace playouts (the
+ * workload's extension; the paper's own leaf evaluation is the random playout
+ * of Sec. II-B).  Features (640, BF16): per tile the owner seat relative to the
+ * mover, face down/up and drawn this turn; per opponent slot the values it may
+ * hold given its face-up numbered neighbours and the tiles the mover cannot
+ * see.  640 -> 512 -> 512 -> 512 (GELU) -> 4 logits over relative seats,
+ * softmax over the seats in play.  BF16 weights and activations with FP32
+ * accumulation on the tensor cores (tcgen05, accumulators in tensor memory);
+ * FP32 master weights and AdamW moments.  Parameters, as a flat FP32 array:
+ * W1[512][640], b1[512], W2[512][512], b2[512], W3[512][512], b3[512],
+ * W4[4][512], b4[4] (855,556 values).  The network lives in the context.
+ */
+/* Initialise the weights (Glorot uniform from Philox keyed by seed; zero biases). */
+int dvc_value_init(dvc_ctx* ctx, uint64_t seed, void* stream);
+/* Copy the FP32 parameters out (direction 0) or in (direction 1); d_params: 855,556 floats. */
+int dvc_value_params(dvc_ctx* ctx, float* d_params, int direction, void* stream);
+/* Features of n states, FP32 0/1, n x 640 (test and inspection hook). */
+int dvc_value_features(dvc_ctx* ctx, const dvc_state* d_states, int n, float* d_out, void* stream);
+/* Win probability per absolute seat for n leaves: d_winprob n x 4 FP32 (seats beyond the game's player count 0). */
+int dvc_value_eval(dvc_ctx* ctx, const dvc_state* d_leaves, int n, float* d_winprob, void* stream);
+/* One AdamW step (beta 0.9/0.999, eps 1e-8, weight decay 1e-4 on matrices) on the
+ * mean cross-entropy of n states against soft labels d_labels (n x 4 FP32, per
+ * absolute seat, summing to 1).  d_loss (optional): the mean loss before the step. */
+int dvc_value_train_step(dvc_ctx* ctx, const dvc_state* d_states, const float* d_labels, int n, float lr,
+                         float* d_loss, void* stream);
+/* Gradient of the last train step (855,556 FP32, parameter layout above). */
+int dvc_value_grads(dvc_ctx* ctx, float* d_out, void* stream);
+/* Checkpoint: weights, AdamW moments and step, to and from a host file (synchronises). */
+int dvc_value_save(dvc_ctx* ctx, const char* path);
+int dvc_value_load(dvc_ctx* ctx, const char* path);
+/* The tensor-core GEMM used by the network: C = act(A B^T + bias), A M x K and
+ * B N x K row-major BF16, bias N FP32 (optional), C M x N BF16 (optional),
+ * Cf M x N FP32 before the activation (optional); N % 16 == 0, K % 64 == 0;
+ * act 0 none, 1 GELU. */
+int dvc_gemm_bf16(dvc_ctx* ctx, const void* d_A, const void* d_B, const float* d_bias, void* d_C, float* d_Cf, int M,
+                  int N, int K, int act, void* stream);
+
 /* Test hook for the random-number generator: out[4k..4k+3] = Philox-4x32-10
  * of counter d_ctr[4k..], key d_key[2k..], by this library's generator
  * (use_reference = 0) or by cuRAND's device function (use_reference = 1). */

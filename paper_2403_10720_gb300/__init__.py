@@ -98,6 +98,15 @@ def lib():
             "dvc_tree_export": ([vp, i, vp, vp], i),
             "dvc_philox": ([vp, i, vp, vp, vp, i, vp], i),
             "dvc_determinize_noalloc": ([vp, i, i, u64, vp, vp, vp, vp, vp], i),
+            "dvc_value_init": ([vp, u64, vp], i),
+            "dvc_value_params": ([vp, vp, i, vp], i),
+            "dvc_value_features": ([vp, vp, i, vp, vp], i),
+            "dvc_value_eval": ([vp, vp, i, vp, vp], i),
+            "dvc_value_train_step": ([vp, vp, vp, i, ctypes.c_float, vp, vp], i),
+            "dvc_value_grads": ([vp, vp, vp], i),
+            "dvc_value_save": ([vp, ctypes.c_char_p], i),
+            "dvc_value_load": ([vp, ctypes.c_char_p], i),
+            "dvc_gemm_bf16": ([vp, vp, vp, vp, vp, vp, i, i, i, i, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -184,6 +193,57 @@ class Context:
         self._rc(lib().dvc_rollout_batch(self.h, _ptr(leaves), n, playouts, seed, _ptr(tree_ids), _ptr(leaf_ids),
                                          _ptr(wins), _ptr(words), _stream(stream)), "dvc_rollout_batch")
         return wins
+
+    VALUE_NPARAMS = 855556
+
+    def dvc_value_init(self, seed, stream=None):
+        self._rc(lib().dvc_value_init(self.h, seed, _stream(stream)), "dvc_value_init")
+
+    def dvc_value_params(self, params=None, stream=None):
+        """Without `params`: returns the FP32 parameters; with: loads them."""
+        if params is None:
+            out = torch.empty(self.VALUE_NPARAMS, dtype=torch.float32, device=self.dev())
+            self._rc(lib().dvc_value_params(self.h, _ptr(out), 0, _stream(stream)), "dvc_value_params")
+            return out
+        self._rc(lib().dvc_value_params(self.h, _ptr(params), 1, _stream(stream)), "dvc_value_params")
+        return params
+
+    def dvc_value_features(self, states, stream=None):
+        out = torch.empty((states.shape[0], 640), dtype=torch.float32, device=self.dev())
+        self._rc(lib().dvc_value_features(self.h, _ptr(states), states.shape[0], _ptr(out), _stream(stream)),
+                 "dvc_value_features")
+        return out
+
+    def dvc_value_eval(self, leaves, out=None, stream=None):
+        out = torch.empty((leaves.shape[0], 4), dtype=torch.float32, device=self.dev()) if out is None else out
+        self._rc(lib().dvc_value_eval(self.h, _ptr(leaves), leaves.shape[0], _ptr(out), _stream(stream)),
+                 "dvc_value_eval")
+        return out
+
+    def dvc_value_train_step(self, states, labels, lr, loss=None, stream=None):
+        self._rc(lib().dvc_value_train_step(self.h, _ptr(states), _ptr(labels), states.shape[0], lr, _ptr(loss),
+                                            _stream(stream)), "dvc_value_train_step")
+        return loss
+
+    def dvc_value_grads(self, stream=None):
+        out = torch.empty(self.VALUE_NPARAMS, dtype=torch.float32, device=self.dev())
+        self._rc(lib().dvc_value_grads(self.h, _ptr(out), _stream(stream)), "dvc_value_grads")
+        return out
+
+    def dvc_value_save(self, path):
+        self._rc(lib().dvc_value_save(self.h, str(path).encode()), "dvc_value_save")
+
+    def dvc_value_load(self, path):
+        self._rc(lib().dvc_value_load(self.h, str(path).encode()), "dvc_value_load")
+
+    def dvc_gemm_bf16(self, A, B, bias=None, act=0, want_bf16=True, want_f32=True, stream=None):
+        M, K = A.shape
+        N = B.shape[0]
+        C = torch.empty((M, N), dtype=torch.bfloat16, device=self.dev()) if want_bf16 else None
+        Cf = torch.empty((M, N), dtype=torch.float32, device=self.dev()) if want_f32 else None
+        self._rc(lib().dvc_gemm_bf16(self.h, _ptr(A), _ptr(B), _ptr(bias), _ptr(C), _ptr(Cf), M, N, K, act,
+                                     _stream(stream)), "dvc_gemm_bf16")
+        return C, Cf
 
     def dvc_philox(self, ctr, key, use_reference=False, stream=None):
         n = ctr.shape[0]

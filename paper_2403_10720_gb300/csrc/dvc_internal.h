@@ -1,0 +1,59 @@
+// dvc_internal.h -- host-side state shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/dvc.h"
+
+struct dvc_value_net;  // value network state (dvc_value.cu)
+struct dvc_ctx;
+void dvc_value_free(dvc_ctx* c);
+
+struct dvc_ctx {
+    dvc_config cfg;
+    int device;
+    std::string err;
+    int32_t* d_flags;  // [0]: latched error code (0 = none)
+    unsigned long long* d_ws;  // determinization workspace
+    size_t ws_cells;
+    dvc_value_net* vnet;       // created on first use of a dvc_value_* call
+};
+
+
+namespace dvc_host {
+
+inline int fail(dvc_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+inline int cuda_fail(dvc_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, DVC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+inline bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+
+inline int check_launch(dvc_ctx* c, const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return DVC_OK;
+}
+
+inline int set_device(dvc_ctx* c) {
+    const cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return DVC_OK;
+}
+
+
+}  // namespace dvc_host

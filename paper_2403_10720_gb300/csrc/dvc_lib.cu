@@ -9,18 +9,11 @@
 #include <string>
 #include <vector>
 
+#include "dvc_internal.h"
 #include "dvc_pipe.cuh"
 
 using namespace dvc;
-
-struct dvc_ctx {
-    dvc_config cfg;
-    int device;
-    std::string err;
-    int32_t* d_flags;  // [0]: latched error code (0 = none)
-    unsigned long long* d_ws;  // determinization workspace
-    size_t ws_cells;
-};
+using namespace dvc_host;
 
 struct dvc_forest {
     dvc_ctx* ctx;
@@ -64,25 +57,6 @@ struct dvc_forest {
 namespace {
 
 constexpr int kDetChunk = 256;
-
-int fail(dvc_ctx* c, int code, const std::string& msg) {
-    if (c) c->err = msg;
-    return code;
-}
-
-int cuda_fail(dvc_ctx* c, cudaError_t e, const char* where) {
-    return fail(c, DVC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 __device__ __forceinline__ void latch(int32_t* flags, int32_t code) { atomicCAS(&flags[0], 0, code); }
 
@@ -476,18 +450,6 @@ SearchParams params_of(const dvc_forest* f) {
     return sp;
 }
 
-int check_launch(dvc_ctx* c, const char* where) {
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, where);
-    return DVC_OK;
-}
-
-int set_device(dvc_ctx* c) {
-    const cudaError_t e = cudaSetDevice(c->device);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    return DVC_OK;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- C ABI
@@ -530,6 +492,7 @@ int dvc_create(dvc_ctx** out, const dvc_config* cfg, int device) {
 void dvc_destroy(dvc_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    dvc_value_free(c);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->d_ws) cudaFree(c->d_ws);
     delete c;

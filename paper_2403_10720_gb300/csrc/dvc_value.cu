@@ -1,0 +1,634 @@
+// dvc_value.cu -- the value network: a learned leaf evaluator that can stand in
+// for random playouts (the workload's extension of the method; the paper's
+// own leaf evaluation is the playout of Sec. II-B).
+//
+// Features (640): per tile, owner seat relative to the mover, face-down/up
+// and drawn-this-turn; per opponent slot, the values it may hold given the
+// face-up numbered neighbours and the tiles the mover cannot see.  Network
+// 640 -> 512 -> 512 -> 512 (GELU) -> 4 logits over relative seats, softmax
+// over the seats in play.  BF16 weights and activations, FP32 accumulation in
+// tensor memory (tcgen05), FP32 master weights and AdamW moments.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "dvc_device.cuh"
+#include "dvc_gemm.cuh"
+#include "dvc_internal.h"
+
+using namespace dvc;
+using namespace dvc_host;
+
+namespace {
+
+constexpr int VF = 640, VH = 512, VO = 16;
+constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (size_t)VH * VF, OFF_W2 = OFF_B1 + VH, OFF_B2 = OFF_W2 + (size_t)VH * VH,
+                 OFF_W3 = OFF_B2 + VH, OFF_B3 = OFF_W3 + (size_t)VH * VH, OFF_W4 = OFF_B3 + VH,
+                 OFF_B4 = OFF_W4 + 4 * VH, NPARAM = OFF_B4 + 4;
+
+}  // namespace
+
+struct dvc_value_net {
+    float *master, *m, *v, *grad;
+    __nv_bfloat16 *W1, *W2, *W3, *W4;  // W4: 16 x 512, rows 4.. zero
+    __nv_bfloat16 *W2T, *W3T, *W4T;    // W4T: 512 x 64, columns 4.. zero
+    float* b4p;                        // 16
+    int cap;                           // workspace rows (multiple of 128)
+    __nv_bfloat16 *X, *H1, *H2, *H3, *XT, *H1T, *H2T, *H3T, *dZ, *dZT, *dZ4, *dZ4T;
+    float *Z1, *Z2, *Z3, *L, *dH, *dZ4f, *tmp, *part, *loss;
+    long long step;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ kernels
+
+__device__ __forceinline__ uint32_t unknown_mask(const G& g) { return g.tmask & ~g.hand(g.cur) & ~g.rev; }
+
+// One warp per state: X[row] = features (BF16), zero-padded to 640.
+__global__ void features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X, float* Xf) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= npad) return;
+    __nv_bfloat16* x = X ? X + (size_t)row * VF : nullptr;
+    float* xf = Xf ? Xf + (size_t)row * VF : nullptr;
+    for (int i = lane; i < VF; i += 32) {
+        if (x) x[i] = __float2bfloat16_rn(0.0f);
+        if (xf) xf[i] = 0.0f;
+    }
+    __syncwarp();
+    if (row >= n) return;
+    const G g = load_state(states[row]);
+    auto set = [&](int i) {
+        if (x) x[i] = __float2bfloat16_rn(1.0f);
+        if (xf) xf[i] = 1.0f;
+    };
+    const uint32_t held = g.h0 | g.h1 | g.h2 | g.h3;
+    if (lane < 26 && ((g.tmask >> lane) & 1u) && ((held >> lane) & 1u)) {
+        uint32_t owner = 0;
+        for (uint32_t p = 0; p < g.np; ++p)
+            if ((g.hand(p) >> lane) & 1u) owner = p;
+        const uint32_t rel = (owner + g.np - g.cur) % g.np;
+        set(7 * lane + (int)rel);
+        set(7 * lane + 4 + (int)((g.rev >> lane) & 1u));
+        if ((uint32_t)lane == g.drawn) set(7 * lane + 6);
+    }
+    const uint32_t U = unknown_mask(g);
+    for (int pair = lane; pair < 33; pair += 32) {
+        const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
+        if (k >= g.np) continue;
+        const uint32_t q = (g.cur + k) % g.np;
+        const uint32_t len = __popc(g.hand(q));
+        if (s >= len) continue;
+        const int base = 182 + (int)(((k - 1u) * 11u + s) * 13u);
+        const uint32_t t = seq_tile(g, q, s);
+        if ((g.rev >> t) & 1u) {
+            set(base + (t < 24u ? (int)(t >> 1) : 12));
+            continue;
+        }
+        int lo = -1, hi = 24;
+        for (int j = (int)s - 1; j >= 0; --j) {
+            const uint32_t u = seq_tile(g, q, (uint32_t)j);
+            if (((g.rev >> u) & 1u) && u < 24u) {
+                lo = (int)u;
+                break;
+            }
+        }
+        for (uint32_t j = s + 1; j < len; ++j) {
+            const uint32_t u = seq_tile(g, q, j);
+            if (((g.rev >> u) & 1u) && u < 24u) {
+                hi = (int)u;
+                break;
+            }
+        }
+        // unknown numbered tiles strictly between lo and hi
+        const uint32_t above = lo < 0 ? 0x00FFFFFFu : (0x00FFFFFFu & ~((2u << lo) - 1u));
+        const uint32_t below = (1u << hi) - 1u;
+        const uint32_t m = U & above & below;
+        for (int v = 0; v < 12; ++v)
+            if ((m >> (2 * v)) & 3u) set(base + v);
+        if (U & kJokerMask) set(base + 12);
+    }
+}
+
+// Softmax over relative seats 0..P-1, written per absolute seat.
+__global__ void softmax_out_kernel(const float* L, const dvc_state* states, int n, float* out) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const dvc_state& s = states[row];
+    const int P = (s.nplayers >= 2 && s.nplayers <= 4) ? s.nplayers : 2;
+    const int cur = s.cur < P ? s.cur : 0;
+    const float* z = L + (size_t)row * VO;
+    float mx = z[0];
+    for (int r = 1; r < P; ++r) mx = fmaxf(mx, z[r]);
+    float e[4], sum = 0.0f;
+    for (int r = 0; r < P; ++r) {
+        e[r] = expf(z[r] - mx);
+        sum += e[r];
+    }
+    float* o = out + (size_t)row * 4;
+    o[0] = o[1] = o[2] = o[3] = 0.0f;
+    for (int r = 0; r < P; ++r) o[(cur + r) % P] = e[r] / sum;
+}
+
+// Cross-entropy against soft labels (absolute seats) and dL/dlogits / n.
+// Rows >= n get zero gradient.  dZ4 (npad x 64, BF16, K-padded), dZ4T (16 x
+// npad, BF16), dZ4f (npad x 16, FP32); per-row loss into rowloss.
+__global__ void loss_grad_kernel(const float* L, const dvc_state* states, const float* labels, int n, int npad,
+                                 __nv_bfloat16* dZ4, __nv_bfloat16* dZ4T, float* dZ4f, float* rowloss) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= npad) return;
+    float d[VO];
+    for (int r = 0; r < VO; ++r) d[r] = 0.0f;
+    float loss = 0.0f;
+    if (row < n) {
+        const dvc_state& s = states[row];
+        const int P = (s.nplayers >= 2 && s.nplayers <= 4) ? s.nplayers : 2;
+        const int cur = s.cur < P ? s.cur : 0;
+        const float* z = L + (size_t)row * VO;
+        float mx = z[0];
+        for (int r = 1; r < P; ++r) mx = fmaxf(mx, z[r]);
+        float sum = 0.0f;
+        for (int r = 0; r < P; ++r) sum += expf(z[r] - mx);
+        const float lse = mx + logf(sum);
+        for (int r = 0; r < P; ++r) {
+            const float y = labels[(size_t)row * 4 + (cur + r) % P];
+            const float p = expf(z[r] - lse);
+            if (y > 0.0f) loss -= y * (z[r] - lse);
+            d[r] = (p - y) / (float)n;
+        }
+    }
+    rowloss[row] = loss;
+    for (int r = 0; r < 64; ++r) dZ4[(size_t)row * 64 + r] = __float2bfloat16_rn(r < VO ? d[r] : 0.0f);
+    for (int r = 0; r < VO; ++r) {
+        dZ4T[(size_t)r * npad + row] = __float2bfloat16_rn(d[r]);
+        dZ4f[(size_t)row * VO + r] = d[r];
+    }
+}
+
+// out[c][r] = in[r][c] for an R x C BF16 matrix (R, C multiples of 32).
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) tile[i][threadIdx.x] = in[(size_t)(r0 + i) * C + c0 + threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y)
+        out[(size_t)(c0 + i) * R + r0 + threadIdx.x] = tile[threadIdx.x][i];
+}
+
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// dZ = dH * GELU'(Z): FP32 in place in dH, BF16 copy in dZ.
+__global__ void gelu_back_kernel(float* dH, const float* Z, __nv_bfloat16* dZ, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = dH[i] * gelu_grad(Z[i]);
+        dH[i] = v;
+        dZ[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Column sums of an R x C FP32 matrix in a fixed order: partial sums over
+// row blocks of 256, then one thread per column adds the blocks in order.
+__global__ void colsum_partial_kernel(const float* A, int R, int C, float* part) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rb = blockIdx.y;
+    if (c >= C) return;
+    float acc = 0.0f;
+    const int r1 = min(R, (rb + 1) * 256);
+    for (int r = rb * 256; r < r1; ++r) acc += A[(size_t)r * C + c];
+    part[(size_t)rb * C + c] = acc;
+}
+
+__global__ void colsum_final_kernel(const float* part, int nb, int C, float* out, int cols_out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols_out) return;
+    float acc = 0.0f;
+    for (int b = 0; b < nb; ++b) acc += part[(size_t)b * C + c];
+    out[c] = acc;
+}
+
+__global__ void mean_kernel(const float* x, int n, float* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float acc = 0.0f;
+    for (int i = 0; i < n; ++i) acc += x[i];
+    *out = acc / (float)n;
+}
+
+__global__ void copy_rows_kernel(const float* src, float* dst, size_t count) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// AdamW on the FP32 master copy; weight decay on weight matrices only.
+__global__ void adamw_kernel(float* w, float* m, float* v, const float* g, size_t count, float lr, float b1, float b2,
+                             float eps, float wd, float c1, float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const bool is_bias = (i >= OFF_B1 && i < OFF_W2) || (i >= OFF_B2 && i < OFF_W3) ||
+                             (i >= OFF_B3 && i < OFF_W4) || i >= OFF_B4;
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float upd = (mi / c1) / (sqrtf(vi / c2) + eps);
+        if (!is_bias) upd += wd * w[i];
+        w[i] -= lr * upd;
+    }
+}
+
+// BF16 working copies (and transposes) of the master weights.
+__global__ void refresh_kernel(const float* w, __nv_bfloat16* W1, __nv_bfloat16* W2, __nv_bfloat16* W3,
+                               __nv_bfloat16* W4, __nv_bfloat16* W2T, __nv_bfloat16* W3T, __nv_bfloat16* W4T,
+                               float* b4p) {
+    const size_t total = (size_t)VH * VF + 2 * (size_t)VH * VH + (size_t)VO * VH;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < (size_t)VH * VF) {
+            W1[i] = __float2bfloat16_rn(w[OFF_W1 + i]);
+            continue;
+        }
+        size_t j = i - (size_t)VH * VF;
+        if (j < (size_t)VH * VH) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(w[OFF_W2 + j]);
+            W2[j] = b;
+            W2T[(j % VH) * VH + j / VH] = b;
+            continue;
+        }
+        j -= (size_t)VH * VH;
+        if (j < (size_t)VH * VH) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(w[OFF_W3 + j]);
+            W3[j] = b;
+            W3T[(j % VH) * VH + j / VH] = b;
+            continue;
+        }
+        j -= (size_t)VH * VH;  // W4 padded: 16 x 512
+        const size_t r = j / VH, c = j % VH;
+        const __nv_bfloat16 b = __float2bfloat16_rn(r < 4 ? w[OFF_W4 + r * VH + c] : 0.0f);
+        W4[j] = b;
+    }
+    // W4T: 512 x 64 (K-padded), b4 padded
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)VH * 64; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = i / 64, r = i % 64;
+        W4T[i] = __float2bfloat16_rn(r < 4 ? w[OFF_W4 + r * VH + k] : 0.0f);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < VO) b4p[threadIdx.x] = threadIdx.x < 4 ? w[OFF_B4 + threadIdx.x] : 0.0f;
+}
+
+// Glorot-uniform weights from Philox (key = seed, counter = index), zero biases.
+__global__ void init_params_kernel(float* w, uint64_t seed) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < NPARAM; i += (size_t)gridDim.x * blockDim.x) {
+        float fan_in = 0.0f, fan_out = 0.0f;
+        bool bias = true;
+        if (i < OFF_B1) { fan_in = VF; fan_out = VH; bias = false; }
+        else if (i >= OFF_W2 && i < OFF_B2) { fan_in = VH; fan_out = VH; bias = false; }
+        else if (i >= OFF_W3 && i < OFF_B3) { fan_in = VH; fan_out = VH; bias = false; }
+        else if (i >= OFF_W4 && i < OFF_B4) { fan_in = VH; fan_out = 4; bias = false; }
+        if (bias) {
+            w[i] = 0.0f;
+            continue;
+        }
+        uint32_t a = (uint32_t)i, b = (uint32_t)(i >> 32), c = 7u, d = 0u;
+        philox10(a, b, c, d, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const float u = ((float)(a >> 8) + 0.5f) * (1.0f / 16777216.0f);  // (0, 1)
+        const float lim = sqrtf(6.0f / (fan_in + fan_out));
+        w[i] = (2.0f * u - 1.0f) * lim;
+    }
+}
+
+// ------------------------------------------------------------------ host helpers
+
+template <int BN>
+cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
+    const uint32_t smem = gemm_smem_bytes(BN);
+    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.M + kGemmBM - 1) / kGemmBM, a.N / BN);
+    gemm_bf16_tc_kernel<BN><<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, __nv_bfloat16* C, float* Cf, int M,
+                 int N, int K, int act, int32_t* flags, cudaStream_t st) {
+    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags};
+    if (N % 256 == 0) return launch_gemm<256>(a, st);
+    if (N % 128 == 0) return launch_gemm<128>(a, st);
+    if (N % 64 == 0) return launch_gemm<64>(a, st);
+    if (N % 32 == 0) return launch_gemm<32>(a, st);
+    return launch_gemm<16>(a, st);
+}
+
+int net_alloc(dvc_ctx* c) {
+    if (c->vnet) return DVC_OK;
+    dvc_value_net* v = new dvc_value_net();
+    std::memset(v, 0, sizeof(*v));
+    bool ok = cudaMalloc(&v->master, NPARAM * 4) == cudaSuccess && cudaMalloc(&v->m, NPARAM * 4) == cudaSuccess &&
+              cudaMalloc(&v->v, NPARAM * 4) == cudaSuccess && cudaMalloc(&v->grad, NPARAM * 4) == cudaSuccess &&
+              cudaMalloc(&v->W1, (size_t)VH * VF * 2) == cudaSuccess &&
+              cudaMalloc(&v->W2, (size_t)VH * VH * 2) == cudaSuccess &&
+              cudaMalloc(&v->W3, (size_t)VH * VH * 2) == cudaSuccess &&
+              cudaMalloc(&v->W4, (size_t)VO * VH * 2) == cudaSuccess &&
+              cudaMalloc(&v->W2T, (size_t)VH * VH * 2) == cudaSuccess &&
+              cudaMalloc(&v->W3T, (size_t)VH * VH * 2) == cudaSuccess &&
+              cudaMalloc(&v->W4T, (size_t)VH * 64 * 2) == cudaSuccess && cudaMalloc(&v->b4p, VO * 4) == cudaSuccess;
+    if (!ok || cudaMemset(v->m, 0, NPARAM * 4) != cudaSuccess || cudaMemset(v->v, 0, NPARAM * 4) != cudaSuccess ||
+        cudaMemset(v->grad, 0, NPARAM * 4) != cudaSuccess) {
+        cudaGetLastError();
+        c->vnet = v;
+        return fail(c, DVC_E_OOM, "value network: parameter allocation");
+    }
+    c->vnet = v;
+    return DVC_OK;
+}
+
+void free_work(dvc_value_net* v) {
+    void* ptrs[] = {v->X,  v->H1,  v->H2, v->H3,   v->XT,   v->H1T, v->H2T, v->H3T, v->dZ,  v->dZT, v->dZ4,
+                    v->dZ4T, v->Z1, v->Z2, v->Z3, v->L, v->dH, v->dZ4f, v->tmp, v->part, v->loss};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    v->X = v->H1 = v->H2 = v->H3 = v->XT = v->H1T = v->H2T = v->H3T = v->dZ = v->dZT = v->dZ4 = v->dZ4T = nullptr;
+    v->Z1 = v->Z2 = v->Z3 = v->L = v->dH = v->dZ4f = v->tmp = v->part = v->loss = nullptr;
+    v->cap = 0;
+}
+
+int ensure_work(dvc_ctx* c, int npad) {
+    dvc_value_net* v = c->vnet;
+    if (npad <= v->cap) return DVC_OK;
+    free_work(v);
+    const size_t r = (size_t)npad;
+    auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    const bool ok = al((void**)&v->X, r * VF * 2) && al((void**)&v->H1, r * VH * 2) && al((void**)&v->H2, r * VH * 2) &&
+                    al((void**)&v->H3, r * VH * 2) && al((void**)&v->XT, r * VF * 2) && al((void**)&v->H1T, r * VH * 2) &&
+                    al((void**)&v->H2T, r * VH * 2) && al((void**)&v->H3T, r * VH * 2) &&
+                    al((void**)&v->dZ, r * VH * 2) && al((void**)&v->dZT, r * VH * 2) && al((void**)&v->dZ4, r * 64 * 2) &&
+                    al((void**)&v->dZ4T, r * VO * 2) && al((void**)&v->Z1, r * VH * 4) && al((void**)&v->Z2, r * VH * 4) &&
+                    al((void**)&v->Z3, r * VH * 4) && al((void**)&v->L, r * VO * 4) && al((void**)&v->dH, r * VH * 4) &&
+                    al((void**)&v->dZ4f, r * VO * 4) && al((void**)&v->tmp, (size_t)VO * VH * 4) &&
+                    al((void**)&v->part, ((r + 255) / 256) * (size_t)VF * 4) && al((void**)&v->loss, (r + 1) * 4);
+    if (!ok) {
+        cudaGetLastError();
+        free_work(v);
+        return fail(c, DVC_E_OOM, "value network: workspace of " + std::to_string(npad) + " rows");
+    }
+    v->cap = npad;
+    return DVC_OK;
+}
+
+int refresh(dvc_ctx* c, cudaStream_t st) {
+    dvc_value_net* v = c->vnet;
+    refresh_kernel<<<256, 256, 0, st>>>(v->master, v->W1, v->W2, v->W3, v->W4, v->W2T, v->W3T, v->W4T, v->b4p);
+    return check_launch(c, "refresh_kernel");
+}
+
+int need_net(dvc_ctx* c) {
+    if (!c->vnet || !c->vnet->master) return fail(c, DVC_E_INVALID, "value network not initialised (dvc_value_init)");
+    return DVC_OK;
+}
+
+// Forward pass for n rows (npad = n rounded up to 128).  With train = true,
+// keeps pre-activations and transposed activations for the backward pass.
+int forward(dvc_ctx* c, const dvc_state* states, int n, int npad, bool train, cudaStream_t st) {
+    dvc_value_net* v = c->vnet;
+    int32_t* fl = c->d_flags;
+    features_kernel<<<(npad * 32 + 255) / 256, 256, 0, st>>>(states, n, npad, v->X, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = gemm(v->X, v->W1, v->master + OFF_B1, v->H1, train ? v->Z1 : nullptr, npad, VH, VF, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(v->H1, v->W2, v->master + OFF_B2, v->H2, train ? v->Z2 : nullptr, npad, VH, VH, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(v->H2, v->W3, v->master + OFF_B3, v->H3, train ? v->Z3 : nullptr, npad, VH, VH, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(v->H3, v->W4, v->b4p, nullptr, v->L, npad, VO, VH, kActNone, fl, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "value forward");
+    return DVC_OK;
+}
+
+int transpose(dvc_ctx* c, const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C, cudaStream_t st) {
+    transpose_bf16_kernel<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(in, out, R, C);
+    return check_launch(c, "transpose_bf16_kernel");
+}
+
+int colsum(dvc_ctx* c, const float* A, int R, int C, float* out, int cols_out, cudaStream_t st) {
+    dvc_value_net* v = c->vnet;
+    const int nb = (R + 255) / 256;
+    colsum_partial_kernel<<<dim3((C + 127) / 128, nb), 128, 0, st>>>(A, R, C, v->part);
+    colsum_final_kernel<<<(cols_out + 127) / 128, 128, 0, st>>>(v->part, nb, C, out, cols_out);
+    return check_launch(c, "colsum");
+}
+
+int check_states_args(dvc_ctx* c, const void* d_states, int n) {
+    if (n < 0) return fail(c, DVC_E_INVALID, "value network: n < 0");
+    if (n > (1 << 24)) return fail(c, DVC_E_UNSUPPORTED, "value network: more than 2^24 rows");
+    if (n > 0 && !is_device_ptr(d_states)) return fail(c, DVC_E_INVALID, "value network: states must be device memory");
+    return DVC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dvc_value_init(dvc_ctx* c, uint64_t seed, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (int rc = set_device(c)) return rc;
+    if (int rc = net_alloc(c)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    dvc_value_net* v = c->vnet;
+    init_params_kernel<<<512, 256, 0, st>>>(v->master, seed);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->m, 0, NPARAM * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->v, 0, NPARAM * 4, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dvc_value_init");
+    v->step = 0;
+    return refresh(c, st);
+}
+
+int dvc_value_params(dvc_ctx* c, float* d_params, int direction, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (!is_device_ptr(d_params) || (direction != 0 && direction != 1))
+        return fail(c, DVC_E_INVALID, "dvc_value_params: device pointer and direction 0 (out) or 1 (in)");
+    if (int rc = set_device(c)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (direction == 1 && !c->vnet) {
+        if (int rc = net_alloc(c)) return rc;
+    }
+    if (int rc = need_net(c)) return rc;
+    dvc_value_net* v = c->vnet;
+    const cudaError_t e = direction == 0 ? cudaMemcpyAsync(d_params, v->master, NPARAM * 4, cudaMemcpyDeviceToDevice, st)
+                                         : cudaMemcpyAsync(v->master, d_params, NPARAM * 4, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dvc_value_params");
+    return direction == 1 ? refresh(c, st) : DVC_OK;
+}
+
+int dvc_value_features(dvc_ctx* c, const dvc_state* d_states, int n, float* d_out, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (int rc = check_states_args(c, d_states, n)) return rc;
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_out)) return fail(c, DVC_E_INVALID, "dvc_value_features: d_out must be device memory");
+    if (int rc = set_device(c)) return rc;
+    features_kernel<<<(n * 32 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_states, n, n, nullptr, d_out);
+    return check_launch(c, "features_kernel");
+}
+
+int dvc_value_eval(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_winprob, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (int rc = check_states_args(c, d_leaves, n)) return rc;
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_winprob)) return fail(c, DVC_E_INVALID, "dvc_value_eval: d_winprob must be device memory");
+    if (int rc = set_device(c)) return rc;
+    if (int rc = need_net(c)) return rc;
+    const int npad = (n + 127) / 128 * 128;
+    if (int rc = ensure_work(c, npad)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
+    softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, d_leaves, n, d_winprob);
+    return check_launch(c, "softmax_out_kernel");
+}
+
+int dvc_value_train_step(dvc_ctx* c, const dvc_state* d_states, const float* d_labels, int n, float lr, float* d_loss,
+                         void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (int rc = check_states_args(c, d_states, n)) return rc;
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_labels) || (d_loss && !is_device_ptr(d_loss)) || !(lr >= 0.0f))
+        return fail(c, DVC_E_INVALID, "dvc_value_train_step: device labels/loss, lr >= 0");
+    if (int rc = set_device(c)) return rc;
+    if (int rc = need_net(c)) return rc;
+    const int npad = (n + 127) / 128 * 128;
+    if (int rc = ensure_work(c, npad)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    dvc_value_net* v = c->vnet;
+    int32_t* fl = c->d_flags;
+    if (int rc = forward(c, d_states, n, npad, true, st)) return rc;
+    loss_grad_kernel<<<(npad + 127) / 128, 128, 0, st>>>(v->L, d_states, d_labels, n, npad, v->dZ4, v->dZ4T, v->dZ4f,
+                                                          v->loss);
+    if (int rc = check_launch(c, "loss_grad_kernel")) return rc;
+    if (d_loss) mean_kernel<<<1, 32, 0, st>>>(v->loss, n, d_loss);
+    int rc = transpose(c, v->X, v->XT, npad, VF, st);
+    if (!rc) rc = transpose(c, v->H1, v->H1T, npad, VH, st);
+    if (!rc) rc = transpose(c, v->H2, v->H2T, npad, VH, st);
+    if (!rc) rc = transpose(c, v->H3, v->H3T, npad, VH, st);
+    if (rc) return rc;
+    float* g = v->grad;
+    cudaError_t e;
+    // layer 4
+    e = gemm(v->dZ4T, v->H3T, nullptr, nullptr, v->tmp, VO, VH, npad, kActNone, fl, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "value backward 4");
+    copy_rows_kernel<<<16, 256, 0, st>>>(v->tmp, g + OFF_W4, (size_t)4 * VH);
+    if ((rc = colsum(c, v->dZ4f, npad, VO, g + OFF_B4, 4, st))) return rc;
+    e = gemm(v->dZ4, v->W4T, nullptr, nullptr, v->dH, npad, VH, 64, kActNone, fl, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "value backward dH3");
+    // layers 3, 2, 1
+    const float* Zs[3] = {v->Z3, v->Z2, v->Z1};
+    const __nv_bfloat16* Hin_T[3] = {v->H2T, v->H1T, v->XT};
+    const __nv_bfloat16* WT[3] = {v->W3T, v->W2T, nullptr};
+    const size_t offW[3] = {OFF_W3, OFF_W2, OFF_W1}, offB[3] = {OFF_B3, OFF_B2, OFF_B1};
+    const int kin[3] = {VH, VH, VF};
+    for (int l = 0; l < 3; ++l) {
+        const size_t cnt = (size_t)npad * VH;
+        gelu_back_kernel<<<1024, 256, 0, st>>>(v->dH, Zs[l], v->dZ, cnt);
+        if ((rc = check_launch(c, "gelu_back_kernel"))) return rc;
+        if ((rc = colsum(c, v->dH, npad, VH, g + offB[l], VH, st))) return rc;
+        if ((rc = transpose(c, v->dZ, v->dZT, npad, VH, st))) return rc;
+        e = gemm(v->dZT, Hin_T[l], nullptr, nullptr, g + offW[l], VH, kin[l], npad, kActNone, fl, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "value backward dW");
+        if (WT[l]) {
+            e = gemm(v->dZ, WT[l], nullptr, nullptr, v->dH, npad, VH, VH, kActNone, fl, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "value backward dH");
+        }
+    }
+    // AdamW
+    v->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f, wd = 1e-4f;
+    const float c1 = 1.0f - powf(b1, (float)v->step), c2 = 1.0f - powf(b2, (float)v->step);
+    adamw_kernel<<<1024, 256, 0, st>>>(v->master, v->m, v->v, g, NPARAM, lr, b1, b2, eps, wd, c1, c2);
+    if ((rc = check_launch(c, "adamw_kernel"))) return rc;
+    return refresh(c, st);
+}
+
+int dvc_value_grads(dvc_ctx* c, float* d_out, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (!is_device_ptr(d_out)) return fail(c, DVC_E_INVALID, "dvc_value_grads: d_out must be device memory");
+    if (int rc = need_net(c)) return rc;
+    if (int rc = set_device(c)) return rc;
+    const cudaError_t e =
+        cudaMemcpyAsync(d_out, c->vnet->grad, NPARAM * 4, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVC_OK : cuda_fail(c, e, "dvc_value_grads");
+}
+
+// File: "DVCV" magic, u32 version 1, u64 parameter count, i64 Adam step,
+// then master weights, first and second moments (FP32 each).
+int dvc_value_save(dvc_ctx* c, const char* path) {
+    if (!c || !path) return DVC_E_INVALID;
+    if (int rc = need_net(c)) return rc;
+    if (int rc = set_device(c)) return rc;
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(c, DVC_E_CUDA, "dvc_value_save: sync");
+    dvc_value_net* v = c->vnet;
+    std::vector<float> buf(3 * NPARAM);
+    if (cudaMemcpy(buf.data(), v->master, NPARAM * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(buf.data() + NPARAM, v->m, NPARAM * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(buf.data() + 2 * NPARAM, v->v, NPARAM * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, DVC_E_CUDA, "dvc_value_save: copy");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(c, DVC_E_INVALID, std::string("dvc_value_save: cannot open ") + path);
+    const char magic[4] = {'D', 'V', 'C', 'V'};
+    const uint32_t ver = 1;
+    const uint64_t np = NPARAM;
+    const int64_t step = v->step;
+    bool ok = std::fwrite(magic, 1, 4, f) == 4 && std::fwrite(&ver, 4, 1, f) == 1 && std::fwrite(&np, 8, 1, f) == 1 &&
+              std::fwrite(&step, 8, 1, f) == 1 && std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? DVC_OK : fail(c, DVC_E_INVALID, "dvc_value_save: write failed");
+}
+
+int dvc_value_load(dvc_ctx* c, const char* path) {
+    if (!c || !path) return DVC_E_INVALID;
+    if (int rc = set_device(c)) return rc;
+    if (int rc = net_alloc(c)) return rc;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, DVC_E_INVALID, std::string("dvc_value_load: cannot open ") + path);
+    char magic[4];
+    uint32_t ver = 0;
+    uint64_t np = 0;
+    int64_t step = 0;
+    std::vector<float> buf(3 * NPARAM);
+    bool ok = std::fread(magic, 1, 4, f) == 4 && std::memcmp(magic, "DVCV", 4) == 0 && std::fread(&ver, 4, 1, f) == 1 &&
+              ver == 1 && std::fread(&np, 8, 1, f) == 1 && np == NPARAM && std::fread(&step, 8, 1, f) == 1 &&
+              std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return fail(c, DVC_E_INVALID, "dvc_value_load: not a version-1 value-network file");
+    dvc_value_net* v = c->vnet;
+    if (cudaMemcpy(v->master, buf.data(), NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(v->m, buf.data() + NPARAM, NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(v->v, buf.data() + 2 * NPARAM, NPARAM * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(c, DVC_E_CUDA, "dvc_value_load: copy");
+    v->step = step;
+    if (int rc = refresh(c, nullptr)) return rc;
+    return cudaDeviceSynchronize() == cudaSuccess ? DVC_OK : fail(c, DVC_E_CUDA, "dvc_value_load: sync");
+}
+
+int dvc_gemm_bf16(dvc_ctx* c, const void* d_A, const void* d_B, const float* d_bias, void* d_C, float* d_Cf, int M,
+                  int N, int K, int act, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (M < 1 || N < 16 || N % 16 || K < 64 || K % 64 || (act != kActNone && act != kActGelu))
+        return fail(c, DVC_E_INVALID, "dvc_gemm_bf16: M >= 1, N % 16 == 0, K % 64 == 0, act 0 or 1");
+    if (!is_device_ptr(d_A) || !is_device_ptr(d_B) || (d_bias && !is_device_ptr(d_bias)) ||
+        (d_C && !is_device_ptr(d_C)) || (d_Cf && !is_device_ptr(d_Cf)) || (!d_C && !d_Cf))
+        return fail(c, DVC_E_INVALID, "dvc_gemm_bf16: device pointers, at least one output");
+    if (int rc = set_device(c)) return rc;
+    const cudaError_t e = gemm((const __nv_bfloat16*)d_A, (const __nv_bfloat16*)d_B, d_bias, (__nv_bfloat16*)d_C, d_Cf,
+                               M, N, K, act, c->d_flags, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVC_OK : cuda_fail(c, e, "dvc_gemm_bf16");
+}
+
+}  // extern "C"
+
+void dvc_value_free(dvc_ctx* c) {
+    if (!c || !c->vnet) return;
+    dvc_value_net* v = c->vnet;
+    free_work(v);
+    void* ptrs[] = {v->master, v->m, v->v, v->grad, v->W1, v->W2, v->W3, v->W4, v->W2T, v->W3T, v->W4T, v->b4p};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete v;
+    c->vnet = nullptr;
+}

@@ -1,0 +1,136 @@
+"""GPU value network against the oracle: tensor-core GEMM, features, forward,
+gradient, training and checkpoint resume.
+
+Tolerances come from the arithmetic: weights are identical BF16 values on both
+sides (the oracle computes in double); the GPU rounds activations to BF16
+(relative 2^-9) after each of three hidden layers and accumulates in FP32, so
+win probabilities agree to about 1e-2 and gradients to a few percent."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = {
+    "2p24": dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5),
+    "3p24": dict(nplayers=3, ntiles=24, deal=4, max_predraw=6, max_revealed=3),
+    "4p26j": dict(nplayers=4, ntiles=26, deal=3, max_predraw=8, max_revealed=3),
+}
+
+
+@pytest.fixture(scope="module")
+def dvc():
+    import paper_2403_10720_gb300 as m
+    from paper_2403_10720_gb300 import build
+    build.build()
+    return m
+
+
+def _bf16_round(x):
+    return torch.as_tensor(x).to(torch.bfloat16).to(torch.float32)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 512, 640), (300, 512, 512), (77, 16, 512), (256, 640, 128), (1, 32, 64)])
+def test_tensor_core_gemm(dvc, M, N, K):
+    ctx = dvc.Context(dvc.Config(), 0)
+    g = torch.Generator().manual_seed(M * 7 + N)
+    A = torch.randn((M, K), generator=g).to(torch.bfloat16)
+    B = torch.randn((N, K), generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, generator=g)
+    for act in (0, 1):
+        C, Cf = ctx.dvc_gemm_bf16(A.cuda(), B.cuda(), bias.cuda(), act=act)
+        torch.cuda.synchronize()
+        ctx.dvc_check()
+        ref = A.double() @ B.double().T + bias.double()
+        err = (Cf.cpu().double() - ref).abs().max().item()
+        assert err <= 1e-4 * max(1.0, ref.abs().max().item()), err
+        post = torch.nn.functional.gelu(ref) if act == 1 else ref
+        assert torch.allclose(C.cpu().double(), post, rtol=1e-2, atol=1e-2)
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_features_exact(dvc, variant):
+    kw = VARIANTS[variant]
+    states = oracle.init_states(oracle.OracleConfig(**kw), 17, 200)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    got = ctx.dvc_value_features(torch.from_numpy(states).cuda()).cpu().numpy()
+    for i in range(len(states)):
+        assert (got[i] == oracle.value_features(states[i])).all(), i
+
+
+def _net(dvc, kw, seed=5):
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(seed)
+    p = _bf16_round(ctx.dvc_value_params().cpu())   # identical BF16 weights on both sides
+    ctx.dvc_value_params(p.cuda())
+    return ctx, p.numpy()
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_forward_matches_oracle(dvc, variant):
+    kw = VARIANTS[variant]
+    ctx, p = _net(dvc, kw)
+    states = oracle.init_states(oracle.OracleConfig(**kw), 23, 300)
+    got = ctx.dvc_value_eval(torch.from_numpy(states).cuda()).cpu().numpy()
+    ctx.dvc_check()
+    worst = 0.0
+    for i in range(0, len(states), 3):
+        want = oracle.value_forward(p, states[i])
+        worst = max(worst, float(np.abs(got[i] - want).max()))
+        assert abs(got[i].sum() - 1.0) < 1e-5
+        assert (got[i][kw["nplayers"]:] == 0).all()
+    assert worst < 1.5e-2, worst
+
+
+def test_gradient_matches_oracle(dvc):
+    kw = VARIANTS["4p26j"]
+    ctx, p = _net(dvc, kw, seed=9)
+    states = np.concatenate([oracle.init_states(oracle.OracleConfig(**VARIANTS[v]), 31, 40) for v in VARIANTS])
+    rng = np.random.default_rng(2)
+    labels = np.zeros((len(states), 4), dtype=np.float32)
+    for i, s in enumerate(states):
+        labels[i, :s[26]] = rng.dirichlet(np.ones(s[26]))
+    loss = torch.zeros(1, device="cuda")
+    ctx.dvc_value_train_step(torch.from_numpy(states).cuda(), torch.from_numpy(labels).cuda(), 0.0, loss=loss)
+    g = ctx.dvc_value_grads().cpu().numpy().astype(np.float64)
+    ctx.dvc_check()
+    want_loss, want = oracle.value_loss_grad(p, states, labels)
+    assert abs(loss.item() - want_loss) < 1e-2 * want_loss
+    offs = [0, 512 * 640, 512 * 641, 512 * 641 + 512 * 512, 512 * 642 + 512 * 512, 512 * 642 + 2 * 512 * 512,
+            512 * 643 + 2 * 512 * 512, 512 * 647 + 2 * 512 * 512, 855556]
+    for a, b in zip(offs, offs[1:]):
+        rel = np.linalg.norm(g[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-12)
+        assert rel < 5e-2, (a, b, rel)
+
+
+def test_training_reduces_loss_and_resumes_exactly(dvc, tmp_path):
+    kw = VARIANTS["2p24"]
+    ctx, _ = _net(dvc, kw, seed=3)
+    states = torch.from_numpy(oracle.init_states(oracle.OracleConfig(**kw), 41, 512)).cuda()
+    leaf_ids = torch.arange(512, dtype=torch.int32, device="cuda")
+    wins = ctx.dvc_rollout_batch(states, 64, 5, leaf_ids, leaf_ids)
+    labels = (wins.float() / 64.0).contiguous()
+    # the loss cannot go below the labels' own entropy; what training removes
+    # is the excess (the KL divergence from the labels)
+    y = labels.cpu().double()
+    entropy = float(-(y * torch.where(y > 0, y.log(), torch.zeros_like(y))).sum(1).mean())
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for step in range(60):
+        ctx.dvc_value_train_step(states, labels, 3e-3, loss=loss)
+        losses.append(loss.item())
+    assert losses[-1] - entropy < 0.5 * (losses[0] - entropy), (entropy, losses[::10])
+    path = tmp_path / "net.dvcv"
+    ctx.dvc_value_save(path)
+    for _ in range(3):
+        ctx.dvc_value_train_step(states, labels, 1e-3)
+    a = ctx.dvc_value_params().cpu()
+    ctx2 = dvc.Context(dvc.Config(**kw), 0)
+    ctx2.dvc_value_load(path)
+    for _ in range(3):
+        ctx2.dvc_value_train_step(states, labels, 1e-3)
+    b = ctx2.dvc_value_params().cpu()
+    ctx.dvc_check()
+    assert torch.equal(a, b)
