@@ -192,8 +192,11 @@ int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream);
  * from cur+1, slots left to right, identities ascending) while the depth is
  * below d_max, draw in-tree tiles on tag 3, score the leaf (mode ROLLOUT:
  * cfg->playouts playouts on tag 4 keyed by iteration; mode VALUE: the value
- * network, see dvc_value_eval), and add cfg->playouts visits and each node's
- * mover's wins along the path.  One launch; bit-exact with the split steps.
+ * network of the context, see dvc_value_eval, credits each seat
+ * round(p * cfg->playouts) of the cfg->playouts visits; a leaf that ended in
+ * the tree credits its winner in both modes), and add cfg->playouts visits
+ * and each node's mover's wins along the path.  Rollout results are
+ * bit-exact with the split steps for every engine and launch shape.
  */
 int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
 

@@ -8,7 +8,11 @@
 
 struct dvc_value_net;  // value network state (dvc_value.cu)
 struct dvc_ctx;
+struct dvc_state;
 void dvc_value_free(dvc_ctx* c);
+// Win probabilities (n x 4, absolute seats) of n leaves by the context's
+// value network, enqueued on st; no argument checks (library-internal).
+int dvc_value_forward_probs(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_probs, cudaStream_t st);
 
 struct dvc_ctx {
     dvc_config cfg;

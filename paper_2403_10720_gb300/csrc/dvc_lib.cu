@@ -52,6 +52,7 @@ struct dvc_forest {
     cudaGraphExec_t chunk_exec;
     int chunk_iters;
     int chains;               // independent chains in the pipeline graph (1..4)
+    float* probs;             // value mode: win probabilities per tree
 };
 
 namespace {
@@ -605,7 +606,8 @@ void dvc_forest_destroy(dvc_forest* f) {
     void* ptrs[] = {f->roots,     f->meta,      f->plans,     f->tables,         f->nodes,         f->link,
                     f->created,   f->work,      f->paths,     f->movers,         f->leaves,        f->leaf_tree,
                     f->leaf_iter, f->d_words,   f->export_scratch, f->order,     f->ucb,           f->csl,
-                    f->pipe.leaf, f->pipe.path, f->pipe.mover, f->pipe.np,       f->pipe.wins,     f->pipe.step_end};
+                    f->pipe.leaf, f->pipe.path, f->pipe.mover, f->pipe.np,       f->pipe.wins,     f->pipe.step_end,
+                    f->probs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -895,6 +897,32 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     return check_launch(c, "pipe_backprop_kernel");
 }
 
+// Value mode: select over all trees, the value network over every leaf, credit.
+int launch_value_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
+    dvc_ctx* c = f->ctx;
+    if (!f->probs) {
+        if (cudaMalloc(&f->probs, sizeof(float) * 4 * (size_t)f->n) != cudaSuccess) {
+            cudaGetLastError();
+            f->probs = nullptr;
+            return fail(c, DVC_E_OOM, "dvc_mcts_step: value buffer");
+        }
+    }
+    const ForestDev fd = dev_of(f);
+    const SearchParams sp = params_of(f);
+    const int n = f->n;
+    pipe_begin_kernel<<<(n + 127) / 128, 128, 0, st>>>(fd, n, n_iterations, f->pipe.step_end);
+    if (int rc = check_launch(c, "pipe_begin_kernel")) return rc;
+    for (int it = 0; it < n_iterations; ++it) {
+        pipe_select_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(fd, sp, 0, n, f->order, f->pipe);
+        if (int rc = check_launch(c, "pipe_select_kernel")) return rc;
+        if (int rc = dvc_value_forward_probs(c, f->pipe.leaf, n, f->probs, st)) return rc;
+        pipe_value_wins_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, f->pipe, f->probs, sp.playouts);
+        if (int rc = check_launch(c, "pipe_value_wins_kernel")) return rc;
+    }
+    pipe_backprop_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(fd, sp, n, f->pipe);
+    return check_launch(c, "pipe_backprop_kernel");
+}
+
 }  // namespace
 
 extern "C" {
@@ -903,10 +931,12 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream) {
     if (!f) return DVC_E_INVALID;
     dvc_ctx* c = f->ctx;
     if (n_iterations < 0) return fail(c, DVC_E_INVALID, "dvc_mcts_step: n_iterations < 0");
-    if (mode != DVC_MODE_ROLLOUT) return fail(c, DVC_E_UNSUPPORTED, "dvc_mcts_step: mode not available");
+    if (mode != DVC_MODE_ROLLOUT && mode != DVC_MODE_VALUE) return fail(c, DVC_E_INVALID, "dvc_mcts_step: bad mode");
+    if (mode == DVC_MODE_VALUE && !c->vnet) return fail(c, DVC_E_INVALID, "dvc_mcts_step: value network not initialised");
     if (n_iterations == 0) return DVC_OK;
     if (int rc = set_device(c)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (mode == DVC_MODE_VALUE) return launch_value_pipeline(f, n_iterations, st);
     return f->engine == 2 ? launch_pipeline(f, n_iterations, st) : launch_fused(f, n_iterations, st);
 }
 

@@ -211,6 +211,17 @@ __global__ void __launch_bounds__(128) pipe_backprop_kernel(ForestDev F, SearchP
     pipe_apply_pending(F, sp, t, P);
 }
 
+// Value mode: the network's win probabilities stand in for the playouts of
+// every fresh, unfinished leaf -- each seat is credited round(p * P) of the P
+// visits (a leaf that ended inside the tree keeps its exact credit).
+__global__ void pipe_value_wins_kernel(int n, PipeBufs P, const float* probs, int playouts) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    if (P.np[t] < 0 || P.leaf[t].winner != kNone) return;
+    int32_t* w = P.wins + 4 * t;
+    for (int s = 0; s < 4; ++s) w[s] = (int32_t)(probs[4 * t + s] * (float)playouts + 0.5f);
+}
+
 __host__ __device__ inline uint32_t pipe_rollout_smem(int L) {
     return (uint32_t)(4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
 }

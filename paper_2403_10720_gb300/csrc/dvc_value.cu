@@ -622,6 +622,15 @@ int dvc_gemm_bf16(dvc_ctx* c, const void* d_A, const void* d_B, const float* d_b
 
 }  // extern "C"
 
+int dvc_value_forward_probs(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_probs, cudaStream_t st) {
+    if (int rc = need_net(c)) return rc;
+    const int npad = (n + 127) / 128 * 128;
+    if (int rc = ensure_work(c, npad)) return rc;
+    if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
+    softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, d_leaves, n, d_probs);
+    return check_launch(c, "softmax_out_kernel");
+}
+
 void dvc_value_free(dvc_ctx* c) {
     if (!c || !c->vnet) return;
     dvc_value_net* v = c->vnet;

@@ -134,3 +134,54 @@ def test_training_reduces_loss_and_resumes_exactly(dvc, tmp_path):
     b = ctx2.dvc_value_params().cpu()
     ctx.dvc_check()
     assert torch.equal(a, b)
+
+
+def test_value_mode_search(dvc):
+    """MCTS with the network at the leaves: same tree mechanics (visits in
+    playout units, one node per iteration), deterministic, and a finished
+    leaf keeps its exact credit."""
+    kw = dict(VARIANTS["3p24"], playouts=64)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(11)
+    n, budget = 40, 120
+    roots = ctx.dvc_init_states(8, n)
+    runs = []
+    for _ in range(2):
+        f = dvc.Forest(ctx, roots, [budget] * n, 3)
+        f.dvc_mcts_step(budget, dvc.DVC_MODE_VALUE)
+        runs.append((f.dvc_root_stats().cpu(), [f.dvc_tree_export(t).cpu() for t in (0, 17)]))
+    ctx.dvc_check()
+    stats = runs[0][0].numpy()
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert all(torch.equal(a, b) for a, b in zip(runs[0][1], runs[1][1]))
+    assert (stats[:, 3] == budget * 64).all() and (stats[:, 6] == budget).all()
+    exp = runs[0][1][0].numpy()
+    nodes = exp[exp[:, 0] >= 0]
+    assert len(nodes) <= budget + 1
+    for a, par, vis, w in nodes[1:]:
+        assert 0 <= w <= vis and vis % 64 == 0
+
+
+def test_trained_network_gains_over_playouts(dvc):
+    """After training on 131,072 states labelled by 1,024 playouts each, the
+    network's win probabilities on held-out states are closer to the labels
+    than a 16-playout rollout estimate, and cost less GPU time per leaf than
+    the 64 playouts whose accuracy they approach."""
+    from paper_2403_10720_gb300 import value_train as vt
+    kw = dict(VARIANTS["2p24"], playouts=256)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(1)
+    states, labels = vt.make_dataset(ctx, 131072, root_seed=101)
+    hs, hl = vt.make_dataset(ctx, 4096, root_seed=202)
+    vt.train(ctx, states, labels, epochs=12, batch=8192, lr=1e-3)
+    err_net = vt.mean_abs_error(ctx.dvc_value_eval(hs), hl, hs)
+    err16 = vt.mean_abs_error(vt.rollout_estimate(ctx, hs, 16), hl, hs)
+    err64 = vt.mean_abs_error(vt.rollout_estimate(ctx, hs, 64), hl, hs)
+    big = ctx.dvc_init_states(303, 65536)
+    ids = torch.arange(65536, dtype=torch.int32, device="cuda")
+    ms_net = vt.timed(lambda: ctx.dvc_value_eval(big))
+    ms64 = vt.timed(lambda: ctx.dvc_rollout_batch(big, 64, 9, ids, ids))
+    print(f"held-out |dp|: net {err_net:.4f}, 16 playouts {err16:.4f}, 64 playouts {err64:.4f}; "
+          f"65,536 leaves: net {ms_net:.3f} ms, 64 playouts {ms64:.3f} ms")
+    assert err_net < 0.8 * err16
+    assert ms_net < ms64
