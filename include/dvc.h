@@ -313,6 +313,36 @@ int dvc_value_load(dvc_ctx* ctx, const char* path);
 int dvc_gemm_bf16(dvc_ctx* ctx, const void* d_A, const void* d_B, const float* d_bias, void* d_C, float* d_Cf, int M,
                   int N, int K, int act, void* stream);
 
+/*
+ * Serving: a request loop that keeps many searches resident on the device.
+ * Move queries from concurrent games (root state, iteration budget, leaf
+ * mode, id) wait in a FIFO queue and are admitted as search slots free up
+ * (continuous batching): every poll admits queued queries into free slots,
+ * runs `iterations` more iterations of every resident search together, and
+ * returns the queries whose budget is complete.  Slots are sized for
+ * max_budget iterations and their number is fixed at creation by the HBM
+ * budget (value_share_pct of it for value-mode slots if the context has a
+ * value network), so admission is by memory.  A query's search is keyed by
+ * (seed, low 32 bits of its id) and runs exactly as it would alone: results do
+ * not depend on what else is resident.  Host-side calls; poll synchronises
+ * the server's own stream.
+ */
+typedef struct dvc_server dvc_server;
+typedef struct dvc_result {
+    uint64_t query_id;
+    int32_t best_action, best_visits, best_wins, root_visits, iterations, mode;
+    double t_submit, t_done; /* host steady-clock seconds */
+} dvc_result;
+int dvc_server_create(dvc_ctx* ctx, size_t hbm_budget, int max_budget, int value_share_pct, uint64_t seed,
+                      dvc_server** out);
+void dvc_server_destroy(dvc_server* sv);
+/* Queue a query; h_root is a host record of the context's game variant. */
+int dvc_server_submit(dvc_server* sv, const dvc_state* h_root, int budget, int mode, uint64_t query_id);
+/* Admit, search `iterations` more, collect; returns the number of results written (<= max_results). */
+int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int max_results);
+/* h_out[5]: queued, resident, completed, rollout slots, value slots. */
+int dvc_server_stats(dvc_server* sv, int64_t* h_out);
+
 /* Test hook for the random-number generator: out[4k..4k+3] = Philox-4x32-10
  * of counter d_ctr[4k..], key d_key[2k..], by this library's generator
  * (use_reference = 0) or by cuRAND's device function (use_reference = 1). */

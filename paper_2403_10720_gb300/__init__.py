@@ -64,6 +64,20 @@ class Config:
                           self.cont_thr, self.c_uct, self.d_max, self.playouts)
 
 
+class dvc_result(ctypes.Structure):
+    _fields_ = [
+        ("query_id", ctypes.c_uint64),
+        ("best_action", ctypes.c_int32),
+        ("best_visits", ctypes.c_int32),
+        ("best_wins", ctypes.c_int32),
+        ("root_visits", ctypes.c_int32),
+        ("iterations", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("t_submit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -107,6 +121,11 @@ def lib():
             "dvc_value_save": ([vp, ctypes.c_char_p], i),
             "dvc_value_load": ([vp, ctypes.c_char_p], i),
             "dvc_gemm_bf16": ([vp, vp, vp, vp, vp, vp, i, i, i, i, vp], i),
+            "dvc_server_create": ([vp, ctypes.c_size_t, i, i, u64, ctypes.POINTER(vp)], i),
+            "dvc_server_destroy": ([vp], None),
+            "dvc_server_submit": ([vp, vp, i, i, u64], i),
+            "dvc_server_poll": ([vp, i, ctypes.POINTER(dvc_result), i], i),
+            "dvc_server_stats": ([vp, ctypes.POINTER(ctypes.c_int64)], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -321,3 +340,47 @@ class Forest:
         out = torch.empty((rows, 4), dtype=torch.int32, device=self.ctx.dev())
         self.ctx._rc(lib().dvc_tree_export(self.h, tree, _ptr(out), _stream(stream)), "dvc_tree_export")
         return out
+
+
+class Server:
+    """Owns a dvc_server: continuous batching of move queries (see include/dvc.h)."""
+
+    def __init__(self, ctx: Context, hbm_budget: int, max_budget: int, value_share_pct: int = 0, seed: int = 1):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._rc(lib().dvc_server_create(ctx.h, hbm_budget, max_budget, value_share_pct, seed, ctypes.byref(h)),
+                "dvc_server_create")
+        self.h = h
+        self._buf = (dvc_result * 65536)()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dvc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dvc_server_submit(self, root, budget, mode, query_id):
+        import numpy as np
+        r = np.ascontiguousarray(np.asarray(root, dtype=np.uint8).reshape(32))
+        self.ctx._rc(lib().dvc_server_submit(self.h, r.ctypes.data_as(ctypes.c_void_p), budget, mode, query_id),
+                     "dvc_server_submit")
+
+    def dvc_server_poll(self, iterations):
+        n = lib().dvc_server_poll(self.h, iterations, self._buf, len(self._buf))
+        if n < 0:
+            self.ctx._rc(n, "dvc_server_poll")
+        out = []
+        for r in self._buf[:n]:
+            out.append({k: getattr(r, k) for k, _ in dvc_result._fields_})
+        return out
+
+    def dvc_server_stats(self):
+        a = (ctypes.c_int64 * 5)()
+        self.ctx._rc(lib().dvc_server_stats(self.h, a), "dvc_server_stats")
+        return dict(queued=a[0], resident=a[1], completed=a[2], rollout_slots=a[3], value_slots=a[4])
+

@@ -3,7 +3,9 @@
 #include <curand_philox4x32_x.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
+#include <deque>
 #include <cstring>
 #include <new>
 #include <string>
@@ -376,18 +378,12 @@ __global__ void export_rows_kernel(ForestDev F, int t, const int32_t* iter_rank,
     }
 }
 
-// (Re)initialise every tree: optionally take new roots, plan the root view's
-// determinization and fill its counting table (one warp per tree), count the
-// root's legal guesses, and reset the tree to a lone root.
-__global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_roots, DetPlan* plans,
-                                   unsigned long long* tables, uint32_t table_cap, int nplayers, int ntiles,
-                                   int32_t* pipe_np) {
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// (Re)initialise tree t (one warp): plan the root view's determinization, fill
+// its counting table, count the root's legal guesses, reset it to a lone root.
+__device__ void init_tree(ForestDev& F, int t, DetPlan* plans, unsigned long long* tables, uint32_t table_cap,
+                          int nplayers, int ntiles, int32_t* pipe_np) {
     const uint32_t lane = threadIdx.x & 31u;
-    if (t >= n) return;
     dvc_state* roots = const_cast<dvc_state*>(F.roots);
-    if (new_roots && lane == 0) roots[t] = new_roots[t];
-    __syncwarp();
     const G g = load_state(roots[t]);
     DetPlan& pl = plans[t];
     if (lane == 0) {
@@ -423,6 +419,41 @@ __global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_root
         F.created[tm.node_off] = -1;
         pipe_np[t] = -1;  // no pipeline backprop pending
     }
+    __syncwarp();
+}
+
+// Every tree, optionally with new roots.
+__global__ void forest_init_kernel(ForestDev F, int n, const dvc_state* new_roots, DetPlan* plans,
+                                   unsigned long long* tables, uint32_t table_cap, int nplayers, int ntiles,
+                                   int32_t* pipe_np) {
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= n) return;
+    if (new_roots && (threadIdx.x & 31u) == 0) const_cast<dvc_state*>(F.roots)[t] = new_roots[t];
+    __syncwarp();
+    init_tree(F, t, plans, tables, table_cap, nplayers, ntiles, pipe_np);
+}
+
+// Selected trees take a new root, budget and stream id (a new search).
+__global__ void forest_admit_kernel(ForestDev F, int count, const int32_t* slots, const dvc_state* new_roots,
+                                    const int32_t* budgets, const uint32_t* tree_ids, DetPlan* plans,
+                                    unsigned long long* tables, uint32_t table_cap, int nplayers, int ntiles,
+                                    int32_t* pipe_np) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= count) return;
+    const int t = slots[i];
+    if ((threadIdx.x & 31u) == 0) {
+        const_cast<dvc_state*>(F.roots)[t] = new_roots[i];
+        F.meta[t].budget = budgets[i];
+        F.meta[t].tree_id = tree_ids[i];
+    }
+    __syncwarp();
+    init_tree(F, t, plans, tables, table_cap, nplayers, ntiles, pipe_np);
+}
+
+// Budgets of all trees set to `b` (0 = every tree idle).
+__global__ void forest_set_budget_kernel(TreeMeta* meta, int n, int32_t b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) meta[t].budget = b;
 }
 
 ForestDev dev_of(dvc_forest* f) {
@@ -1073,6 +1104,242 @@ int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream) {
     export_scan_kernel<<<1, 1, 0, st>>>(budget, f->export_scratch);
     export_rows_kernel<<<64, 256, 0, st>>>(fd, tree, f->export_scratch, rows, d_out);
     return check_launch(f->ctx, "export kernels");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- serving
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerQuery {
+    dvc_state root;
+    int32_t budget;
+    int32_t mode;
+    uint64_t id;
+    double t_submit;
+};
+
+struct ServerSlot {
+    bool busy = false;
+    ServerQuery q;
+};
+
+}  // namespace
+
+struct dvc_server {
+    dvc_ctx* ctx;
+    int max_budget;
+    dvc_forest* f[2] = {nullptr, nullptr};  // rollout, value
+    std::vector<ServerSlot> slots[2];
+    std::deque<ServerQuery> queue;
+    cudaStream_t st = nullptr;
+    // admission staging (device) and statistics (host, pinned)
+    int32_t* d_slot = nullptr;
+    dvc_state* d_root = nullptr;
+    int32_t* d_budget = nullptr;
+    uint32_t* d_tid = nullptr;
+    int32_t* d_stats = nullptr;
+    int32_t* h_stats = nullptr;
+    long long completed = 0;
+};
+
+namespace {
+
+int server_admit(dvc_server* sv, int m) {
+    dvc_forest* f = sv->f[m];
+    if (!f) return DVC_OK;
+    std::vector<int32_t> slot, budget;
+    std::vector<dvc_state> root;
+    std::vector<uint32_t> tid;
+    std::vector<int> freeidx;
+    for (int s = 0; s < f->n; ++s)
+        if (!sv->slots[m][s].busy) freeidx.push_back(s);
+    size_t next = 0;
+    for (auto it = sv->queue.begin(); it != sv->queue.end() && next < freeidx.size();) {
+        if (it->mode != m) {
+            ++it;
+            continue;
+        }
+        const int s = freeidx[next++];
+        sv->slots[m][s].busy = true;
+        sv->slots[m][s].q = *it;
+        slot.push_back(s);
+        budget.push_back(it->budget);
+        root.push_back(it->root);
+        tid.push_back((uint32_t)it->id);
+        it = sv->queue.erase(it);
+    }
+    const int k = (int)slot.size();
+    if (k == 0) return DVC_OK;
+    dvc_ctx* c = sv->ctx;
+    cudaError_t e = cudaMemcpyAsync(sv->d_slot, slot.data(), 4 * k, cudaMemcpyHostToDevice, sv->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_budget, budget.data(), 4 * k, cudaMemcpyHostToDevice, sv->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_tid, tid.data(), 4 * k, cudaMemcpyHostToDevice, sv->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv->d_root, root.data(), sizeof(dvc_state) * k, cudaMemcpyHostToDevice, sv->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server admit");
+    forest_admit_kernel<<<(k * 32 + 127) / 128, 128, 0, sv->st>>>(dev_of(f), k, sv->d_slot, sv->d_root, sv->d_budget,
+                                                                  sv->d_tid, f->plans, f->tables, f->table_cap,
+                                                                  c->cfg.nplayers, c->cfg.ntiles, f->pipe.np);
+    if (int rc = check_launch(c, "forest_admit_kernel")) return rc;
+    // the staging buffers are reused by the next admission: wait for the copies
+    e = cudaStreamSynchronize(sv->st);
+    return e == cudaSuccess ? DVC_OK : cuda_fail(c, e, "dvc_server admit sync");
+}
+
+}  // namespace
+
+extern "C" {
+
+int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_share_pct, uint64_t seed,
+                      dvc_server** out) {
+    if (!c) return DVC_E_INVALID;
+    if (!out || max_budget < 1 || max_budget > (1 << 24) || value_share_pct < 0 || value_share_pct > 100)
+        return fail(c, DVC_E_INVALID, "dvc_server_create: max_budget 1..2^24, value_share_pct 0..100");
+    *out = nullptr;
+    if (int rc = set_device(c)) return rc;
+    // device bytes per search slot: node arena (48 B per slot: node, UCB terms,
+    // link, creation stamp), counting table, plan, meta and pipeline buffers
+    const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 48;
+    const size_t table = (size_t)(c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells) * 8;
+    const size_t per_slot = arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) + 256;
+    const long long total = (long long)(hbm_budget / per_slot);
+    const long long nv = c->vnet ? total * value_share_pct / 100 : 0;
+    const long long nr = total - nv;
+    if (nr < 1 && nv < 1) return fail(c, DVC_E_OOM, "dvc_server_create: HBM budget below one search slot");
+    if (nr > (1 << 20) || nv > (1 << 20)) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_create: over 2^20 slots");
+    dvc_server* sv = new (std::nothrow) dvc_server();
+    if (!sv) return fail(c, DVC_E_OOM, "dvc_server_create: host allocation");
+    sv->ctx = c;
+    sv->max_budget = max_budget;
+    int rc = DVC_OK;
+    const int nmax = (int)std::max(nr, nv);
+    if (cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&sv->d_slot, 4 * (size_t)nmax) != cudaSuccess || cudaMalloc(&sv->d_budget, 4 * (size_t)nmax) != cudaSuccess ||
+        cudaMalloc(&sv->d_tid, 4 * (size_t)nmax) != cudaSuccess ||
+        cudaMalloc(&sv->d_root, sizeof(dvc_state) * (size_t)nmax) != cudaSuccess ||
+        cudaMalloc(&sv->d_stats, 32 * (size_t)nmax) != cudaSuccess ||
+        cudaMallocHost(&sv->h_stats, 32 * (size_t)nmax) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(c, DVC_E_OOM, "dvc_server_create: staging buffers");
+    }
+    const long long counts[2] = {nr, nv};
+    for (int m = 0; m < 2 && rc == DVC_OK; ++m) {
+        const int n = (int)counts[m];
+        if (n < 1) continue;
+        // any valid roots: the slots start idle (budget 0) and take real roots on admission
+        rc = dvc_init_states(c, seed, n, sv->d_root, sv->st);
+        if (rc == DVC_OK) {
+            std::vector<int32_t> budgets(n, max_budget);
+            rc = dvc_forest_create(c, n, sv->d_root, budgets.data(), nullptr, seed, &sv->f[m], sv->st);
+        }
+        if (rc == DVC_OK) {
+            forest_set_budget_kernel<<<(n + 127) / 128, 128, 0, sv->st>>>(sv->f[m]->meta, n, 0);
+            rc = check_launch(c, "forest_set_budget_kernel");
+        }
+        if (rc == DVC_OK) sv->slots[m].assign(n, ServerSlot());
+    }
+    if (rc == DVC_OK && cudaStreamSynchronize(sv->st) != cudaSuccess) rc = fail(c, DVC_E_CUDA, "dvc_server_create sync");
+    if (rc != DVC_OK) {
+        dvc_server_destroy(sv);
+        return rc;
+    }
+    *out = sv;
+    return DVC_OK;
+}
+
+void dvc_server_destroy(dvc_server* sv) {
+    if (!sv) return;
+    cudaSetDevice(sv->ctx->device);
+    if (sv->st) cudaStreamSynchronize(sv->st);
+    for (int m = 0; m < 2; ++m) dvc_forest_destroy(sv->f[m]);
+    void* ptrs[] = {sv->d_slot, sv->d_budget, sv->d_tid, sv->d_root, sv->d_stats};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (sv->h_stats) cudaFreeHost(sv->h_stats);
+    if (sv->st) cudaStreamDestroy(sv->st);
+    delete sv;
+}
+
+int dvc_server_submit(dvc_server* sv, const dvc_state* h_root, int budget, int mode, uint64_t query_id) {
+    if (!sv) return DVC_E_INVALID;
+    dvc_ctx* c = sv->ctx;
+    if (!h_root || budget < 1 || budget > sv->max_budget || (mode != DVC_MODE_ROLLOUT && mode != DVC_MODE_VALUE))
+        return fail(c, DVC_E_INVALID, "dvc_server_submit: root, budget 1..max_budget, mode");
+    if (!sv->f[mode]) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_submit: no slots for this mode");
+    if (h_root->nplayers != c->cfg.nplayers || h_root->ntiles != c->cfg.ntiles)
+        return fail(c, DVC_E_INVALID, "dvc_server_submit: root of another game variant");
+    ServerQuery q;
+    q.root = *h_root;
+    q.budget = budget;
+    q.mode = mode;
+    q.id = query_id;
+    q.t_submit = now_s();
+    sv->queue.push_back(q);
+    return DVC_OK;
+}
+
+int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int max_results) {
+    if (!sv) return DVC_E_INVALID;
+    dvc_ctx* c = sv->ctx;
+    if (iterations < 0 || max_results < 0 || (max_results > 0 && !h_results))
+        return fail(c, DVC_E_INVALID, "dvc_server_poll: iterations >= 0, results buffer");
+    if (int rc = set_device(c)) return rc;
+    int written = 0;
+    for (int m = 0; m < 2; ++m) {
+        dvc_forest* f = sv->f[m];
+        if (!f) continue;
+        if (int rc = server_admit(sv, m)) return rc;
+        bool any = false;
+        for (const ServerSlot& s : sv->slots[m]) any |= s.busy;
+        if (!any) continue;
+        if (iterations > 0)
+            if (int rc = dvc_mcts_step(f, iterations, m, sv->st)) return rc;
+        if (int rc = dvc_root_stats(f, sv->d_stats, sv->st)) return rc;
+        cudaError_t e = cudaMemcpyAsync(sv->h_stats, sv->d_stats, 32 * (size_t)f->n, cudaMemcpyDeviceToHost, sv->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sv->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll");
+        const double t = now_s();
+        for (int s = 0; s < f->n && written < max_results; ++s) {
+            ServerSlot& sl = sv->slots[m][s];
+            const int32_t* st = sv->h_stats + 8 * s;
+            if (!sl.busy || st[6] < sl.q.budget) continue;
+            dvc_result& r = h_results[written++];
+            r.query_id = sl.q.id;
+            r.best_action = st[0];
+            r.best_visits = st[1];
+            r.best_wins = st[2];
+            r.root_visits = st[3];
+            r.iterations = st[6];
+            r.mode = m;
+            r.t_submit = sl.q.t_submit;
+            r.t_done = t;
+            sl.busy = false;
+            sv->completed++;
+        }
+    }
+    return written;
+}
+
+int dvc_server_stats(dvc_server* sv, int64_t* h_out) {
+    if (!sv || !h_out) return DVC_E_INVALID;
+    long long active = 0, slots = 0;
+    for (int m = 0; m < 2; ++m) {
+        slots += (long long)sv->slots[m].size();
+        for (const ServerSlot& s : sv->slots[m]) active += s.busy;
+    }
+    h_out[0] = (int64_t)sv->queue.size();
+    h_out[1] = active;
+    h_out[2] = sv->completed;
+    h_out[3] = (int64_t)sv->slots[0].size();
+    h_out[4] = (int64_t)sv->slots[1].size();
+    (void)slots;
+    return DVC_OK;
 }
 
 }  // extern "C"
