@@ -1,0 +1,79 @@
+"""Launch-shape autotuner for dvc_mcts_step.
+
+Times every candidate (engine, trees per CTA, warps per CTA, chains) on a
+budget-scaled copy of the forest -- the same roots and seed, budgets scaled
+down so a trial takes a fraction of a second -- with CUDA events, and keeps the
+fastest.  Results are identical for every shape (the library guarantees it),
+so only time is compared.  Choices are cached per workload signature and GPU in
+~/.cache/dvc/autotune.json.
+"""
+import json
+import os
+
+import numpy as np
+import torch
+
+CANDIDATES = [(2, 0, 32, 2), (2, 0, 32, 1), (2, 0, 32, 4), (2, 0, 16, 2), (1, 0, 16, 0), (1, 0, 32, 0)]
+_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "dvc", "autotune.json")
+
+
+def _signature(cfg, n, budgets):
+    b = np.asarray(budgets)
+    name = torch.cuda.get_device_name()
+    return (f"{name}|p{cfg.nplayers}t{cfg.ntiles}po{cfg.playouts}|n{n}|"
+            f"b{int(b.min())}-{int(np.median(b))}-{int(b.max())}")
+
+
+def _load():
+    try:
+        with open(_CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(d):
+    try:
+        os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+        with open(_CACHE, "w") as f:
+            json.dump(d, f, indent=1)
+    except OSError:
+        pass
+
+
+def tune(dvc, ctx, roots, budgets, seed, scale=0.05, candidates=None, use_cache=True, verbose=False):
+    """Returns the fastest (engine, trees_per_cta, warps_per_cta, chains)."""
+    budgets = np.asarray(budgets, dtype=np.int32)
+    key = _signature(ctx.cfg, len(budgets), budgets)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        return tuple(cache[key])
+    small = np.maximum(1, (budgets * scale).astype(np.int32))
+    f = dvc.Forest(ctx, roots, small, seed)
+    best, best_ms, trials = None, float("inf"), []
+    for cand in candidates or CANDIDATES:
+        try:
+            f.dvc_forest_tune(*cand)
+        except Exception:
+            continue
+        times = []
+        for _ in range(2):
+            f.dvc_forest_reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f.dvc_mcts_step(int(small.max()))
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        ms = min(times)
+        trials.append((cand, ms))
+        if ms < best_ms:
+            best, best_ms = cand, ms
+    f.close()
+    if verbose:
+        for c, ms in trials:
+            print(f"autotune {c}: {ms:.2f} ms")
+    if use_cache and best is not None:
+        cache[key] = list(best)
+        _save(cache)
+    return best

@@ -55,6 +55,7 @@ struct dvc_forest {
     int chunk_iters;
     int chains;               // independent chains in the pipeline graph (1..4)
     float* probs;             // value mode: win probabilities per tree
+    int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
 };
 
 namespace {
@@ -680,20 +681,12 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     f->trees_per_cta = std::max(1, std::min(32, (n + std::max(sms, 1) - 1) / std::max(sms, 1)));
-    {
-        long long sum = 0;
-        int mx = 0;
-        for (int t = 0; t < n; ++t) {
-            sum += f->h_budgets[t];
-            mx = std::max(mx, f->h_budgets[t]);
-        }
-        // even budgets: the pipeline (full-occupancy playouts); very uneven: the
-        // fused lockstep kernel (no launches for iterations only a few trees run)
-        f->engine = (n >= 2 * std::max(sms, 1) && (long long)mx * n <= 2 * std::max(sum, 1LL)) ? 2 : 1;
-        // pipeline: two rollout CTAs' worth of trees per SM, split over two chains
-        if (f->engine == 2)
-            f->trees_per_cta = std::max(1, std::min(32, (n + 2 * std::max(sms, 1) - 1) / (2 * std::max(sms, 1))));
-    }
+    // enough trees to fill the GPU: the pipeline (full-occupancy playouts),
+    // two rollout CTAs' worth of trees per SM split over two chains;
+    // small forests: the fused lockstep kernel
+    f->engine = n >= 2 * std::max(sms, 1) ? 2 : 1;
+    if (f->engine == 2)
+        f->trees_per_cta = std::max(1, std::min(64, (n + 2 * std::max(sms, 1) - 1) / (2 * std::max(sms, 1))));
     std::vector<int32_t> order(n);
     {
         const int T = f->trees_per_cta;
@@ -701,6 +694,8 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         std::vector<int> idx(n);
         for (int i = 0; i < n; ++i) idx[i] = i;
         std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return f->h_budgets[a] > f->h_budgets[b]; });
+        bool even = true;
+        for (int t = 1; t < n; ++t) even &= f->h_budgets[t] == f->h_budgets[0];
         std::vector<long long> load(nc, 0);
         std::vector<int> fill(nc, 0);
         std::vector<int> capc(nc, T);
@@ -711,6 +706,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
         std::make_heap(heap.begin(), heap.end(), cmp);
         for (int i : idx) {
+            if (even) break;  // equal budgets: keep trees in index order (slot s -> CTA s / T)
             std::pop_heap(heap.begin(), heap.end(), cmp);
             auto [ld, k] = heap.back();
             heap.pop_back();
@@ -722,6 +718,8 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
                 std::push_heap(heap.begin(), heap.end(), cmp);
             }
         }
+        if (even)
+            for (int i = 0; i < n; ++i) order[i] = i;
     }
     auto alloc = [&](void** p, size_t bytes) {
         if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
@@ -797,7 +795,8 @@ int launch_fused(dvc_forest* f, int n_iterations, cudaStream_t st) {
     dvc_ctx* c = f->ctx;
     const int T = f->trees_per_cta;
     const int W = std::max(1, std::min(32, f->warps_per_cta ? f->warps_per_cta : std::min(T, 16)));
-    const int grid = (f->n + T - 1) / T;
+    const int n_run = f->active_prefix > 0 ? std::min(f->n, f->active_prefix) : f->n;
+    const int grid = (n_run + T - 1) / T;
     const PoolLayout L(T, W);
     const int threads = 32 * W;
     const bool fast2 = c->cfg.nplayers == 2 && c->cfg.ntiles == 24;
@@ -996,7 +995,10 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
         for (int k = 0; k < nc; ++k) heap.push_back({0, k});
         auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
         std::make_heap(heap.begin(), heap.end(), cmp);
+        bool even = true;
+        for (int t = 1; t < f->n; ++t) even &= f->h_budgets[t] == f->h_budgets[0];
         for (int i : idx) {
+            if (even) break;  // equal budgets: index order
             std::pop_heap(heap.begin(), heap.end(), cmp);
             auto [ld, k] = heap.back();
             heap.pop_back();
@@ -1006,6 +1008,8 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
                 std::push_heap(heap.begin(), heap.end(), cmp);
             }
         }
+        if (even)
+            for (int i = 0; i < f->n; ++i) order[i] = i;
         if (int rc = set_device(f->ctx)) return rc;
         const cudaError_t e = cudaMemcpy(f->order, order.data(), sizeof(int32_t) * f->n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_tune");
@@ -1242,6 +1246,9 @@ int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_s
             forest_set_budget_kernel<<<(n + 127) / 128, 128, 0, sv->st>>>(sv->f[m]->meta, n, 0);
             rc = check_launch(c, "forest_set_budget_kernel");
         }
+        // resident searches start and end at any time: the fused engine, one
+        // launch per poll over the CTAs that hold resident slots only
+        if (rc == DVC_OK && m == 0) rc = dvc_forest_tune(sv->f[m], 1, 16, 16, 0);
         if (rc == DVC_OK) sv->slots[m].assign(n, ServerSlot());
     }
     if (rc == DVC_OK && cudaStreamSynchronize(sv->st) != cudaSuccess) rc = fail(c, DVC_E_CUDA, "dvc_server_create sync");
@@ -1295,9 +1302,11 @@ int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int m
         dvc_forest* f = sv->f[m];
         if (!f) continue;
         if (int rc = server_admit(sv, m)) return rc;
-        bool any = false;
-        for (const ServerSlot& s : sv->slots[m]) any |= s.busy;
-        if (!any) continue;
+        int top = -1;
+        for (int s = 0; s < f->n; ++s)
+            if (sv->slots[m][s].busy) top = s;
+        if (top < 0) continue;
+        f->active_prefix = top + 1;
         if (iterations > 0)
             if (int rc = dvc_mcts_step(f, iterations, m, sv->st)) return rc;
         if (int rc = dvc_root_stats(f, sv->d_stats, sv->st)) return rc;
