@@ -33,9 +33,10 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from paper_2403_10720_gb300.workloads import BATCHED  # noqa: E402
+from paper_2403_10720_gb300.workloads import BATCHED, UNEVEN  # noqa: E402
 
 PHILOX_OPS_PER_WORD = 25  # Philox-4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) per 4 words
+VALUE_MACS_PER_LEAF = 640 * 512 + 2 * 512 * 512 + 512 * 4  # dense layers of the value network
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
@@ -44,6 +45,24 @@ def _env_int(k, d):
         return int(os.environ.get(k, d))
     except ValueError:
         return d
+
+
+def shard_tree_ids(rank, n):
+    """Weak scaling: rank r searches its own n trees, stream ids [r*n, (r+1)*n)."""
+    return np.arange(rank * n, (rank + 1) * n, dtype=np.uint32)
+
+
+def root_seed_of(rank, root_seed):
+    """Each rank generates its own roots (no data exchange between ranks)."""
+    return root_seed + 1000003 * rank
+
+
+def max_over_ranks(seconds, dist, device):
+    """The job's time for a phase is the slowest rank's (torch.distributed MAX)."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def _measured_peaks():
@@ -99,6 +118,28 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def value_net_roofline(dvc, ctx, peaks, peak_kind, leaves=65536, reps=5):
+    """Time the value network (tensor cores) on `leaves` synthetic leaves."""
+    import torch
+    ctx.dvc_value_init(7)
+    states = ctx.dvc_init_states(77, leaves)
+    out = torch.empty((leaves, 4), dtype=torch.float32, device=states.device)
+    ctx.dvc_value_eval(states, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ctx.dvc_value_eval(states, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    tflops = 2.0 * VALUE_MACS_PER_LEAF * leaves / (ms * 1e-3) / 1e12
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    return {"leaves": leaves, "ms": ms, "leaves_per_s": leaves / (ms * 1e-3),
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "peak_kind": f"bf16 burst ({peak_kind})"}}
 
 
 def oracle_sample(w, n_trees, threads):
@@ -177,9 +218,9 @@ def run_ours(args, w):
     props = torch.cuda.get_device_properties(dev)
     ctx = dvc.Context(dvc.Config(**w.config_kwargs()), local)
     n = w.n_trees
-    roots = ctx.dvc_init_states(w.root_seed + 1000003 * rank, n)
+    roots = ctx.dvc_init_states(root_seed_of(rank, w.root_seed), n)
     budgets = w.budgets()
-    forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=np.arange(rank * n, (rank + 1) * n, dtype=np.uint32))
+    forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=shard_tree_ids(rank, n))
     # launch shape: the three-kernel pipeline in CUDA graphs, two rollout CTAs'
     # worth of trees per SM, 32 warps per rollout CTA, two overlapping chains
     sms = props.multi_processor_count
@@ -232,9 +273,7 @@ def run_ours(args, w):
     words_per_step = int(words.item()) / args.steps
     total_s = sum(step_ms) / 1e3
     if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+        total_s = max_over_ranks(total_s, dist, dev)
     value = playouts_per_step * world * args.steps / total_s
 
     # end to end through the public API: host roots in, host decisions out
@@ -256,9 +295,7 @@ def run_ours(args, w):
         e2e_ms.append(a.elapsed_time(b))
     e2e_s = sum(e2e_ms) / 1e3
     if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e_value = playouts_per_step * world * len(e2e_ms) / e2e_s
     ctx.dvc_check()
     decisions = host_stats.numpy()
@@ -296,6 +333,8 @@ def run_ours(args, w):
         "clocks": clk,
         "first_decision": int(decisions[0][0]),
     }
+    if rank == 0:
+        line["value_net"] = value_net_roofline(dvc, ctx, peaks, peak_kind)
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         p, dt = oracle_sample(w, cores, cores)
@@ -307,6 +346,81 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_uneven(args, w):
+    """The uneven forest: every tree searches its whole budget; one step = all trees."""
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import autotune, build
+    build.build()
+    ctx = dvc.Context(dvc.Config(**w.config_kwargs()), 0)
+    roots = ctx.dvc_init_states(w.root_seed, w.n_trees)
+    budgets = w.budgets()
+    shape = autotune.tune(dvc, ctx, roots, budgets, w.seed, scale=0.02)
+    forest = dvc.Forest(ctx, roots, budgets, w.seed)
+    forest.dvc_forest_tune(*shape)
+    stats = torch.empty((w.n_trees, 8), dtype=torch.int32, device=roots.device)
+    it = int(budgets.max())
+    for _ in range(args.warmup):
+        forest.dvc_forest_reset()
+        forest.dvc_mcts_step(it)
+    torch.cuda.synchronize()
+    ev = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        forest.dvc_forest_reset()
+        forest.dvc_mcts_step(it)
+        forest.dvc_root_stats(out=stats)
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctx.dvc_check()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(ms) / 1e3
+    playouts = int(budgets.sum()) * w.playouts * args.steps
+    print(json.dumps({
+        "metric": "playouts/s", "value": playouts / total_s, "unit": "playouts/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "trees": w.n_trees, "iterations_total": int(budgets.sum()),
+                   "budget_range": [int(budgets.min()), int(budgets.max())], "playouts_per_leaf": w.playouts,
+                   "players": w.nplayers, "tiles": w.ntiles, "launch_shape": list(shape),
+                   "l2": "working set (node arenas) far above L2"},
+        "decisions_per_s": w.n_trees * args.steps / total_s, "clocks": clk}), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals of move queries into a device-resident server."""
+    import numpy as np
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build, serving
+    build.build()
+    kw = dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5, playouts=32)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    n = args.queries
+    roots = ctx.dvc_init_states(505, n).cpu().numpy()
+    rng = np.random.default_rng(5)
+    budgets = np.floor(np.exp(rng.uniform(np.log(1000), np.log(args.max_budget), size=n))).astype(np.int32)
+    server = dvc.Server(ctx, int(args.hbm_gb * (1 << 30)), args.max_budget, seed=5)
+    out = serving.poisson_run(server, roots, budgets, np.zeros(n, dtype=int), rate=args.rate,
+                              iterations_per_poll=args.poll_iters, seed=6, max_seconds=900)
+    st = server.dvc_server_stats()
+    print(json.dumps({
+        "metric": "decisions/s", "value": out["decisions_per_s"], "unit": "decisions/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "serving_2p24_poisson", "queries": n, "rate_per_s": args.rate,
+                   "budget_range": [1000, args.max_budget], "playouts_per_leaf": 32, "hbm_gb": args.hbm_gb,
+                   "slots": st["rollout_slots"], "iterations_per_poll": args.poll_iters},
+        "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "wall_s": out["wall_s"],
+        "playouts_per_s": float(budgets.sum()) * 32 / out["wall_s"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,7 +430,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trees", type=int, default=0, help="override the tree count (small profiling cases)")
     ap.add_argument("--iterations", type=int, default=0, help="override the iterations per tree")
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve"])
+    ap.add_argument("--queries", type=int, default=2000, help="serve: number of move queries")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (queries/s)")
+    ap.add_argument("--max-budget", type=int, default=100000, help="serve: largest query budget")
+    ap.add_argument("--hbm-gb", type=float, default=64.0, help="serve: HBM budget for resident searches")
+    ap.add_argument("--poll-iters", type=int, default=256, help="serve: iterations per poll")
     args = ap.parse_args()
+    if args.workload == "uneven":
+        run_uneven(args, UNEVEN)
+        return
+    if args.workload == "serve":
+        run_serve(args)
+        return
     w = BATCHED
     if args.trees or args.iterations:
         import dataclasses
