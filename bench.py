@@ -221,12 +221,14 @@ def run_ours(args, w):
     roots = ctx.dvc_init_states(root_seed_of(rank, w.root_seed), n)
     budgets = w.budgets()
     forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=shard_tree_ids(rank, n))
-    # launch shape: the three-kernel pipeline in CUDA graphs, two rollout CTAs'
-    # worth of trees per SM, 32 warps per rollout CTA, two overlapping chains
+    # launch shape: the pipeline in CUDA graphs with the library's default
+    # shape -- min(8, n / (2 SMs)) overlapping chains, 2n / (3 chains SMs)
+    # trees and 16 warps per rollout CTA -- unless overridden
     sms = props.multi_processor_count
-    trees_per_cta = max(1, min(32, -(-n // (2 * sms))))
-    chains = 2
-    forest.dvc_forest_tune(2, trees_per_cta, 32, chains)
+    chains = args.chains or max(1, min(8, n // (2 * sms)))
+    trees_per_cta = args.trees_per_cta or max(1, min(64, 2 * n // (3 * chains * sms)))
+    warps = args.warps or 16
+    forest.dvc_forest_tune(2, trees_per_cta, warps, chains)
     stats = torch.empty((n, 8), dtype=torch.int32, device=dev)
     words = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -316,16 +318,18 @@ def run_ours(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "trees": n, "iterations": w.budget, "playouts_per_leaf": w.playouts,
                    "players": w.nplayers, "tiles": w.ntiles, "d_max": w.d_max,
-                   "engine": f"pipeline, {trees_per_cta} trees x 32 warps per rollout CTA, {chains} chains, CUDA graph",
+                   "engine": f"pipeline, {trees_per_cta} trees x {warps} warps per rollout CTA, {chains} chains, "
+                             "CUDA graph",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "decisions_per_s": n * world * args.steps / total_s,
         "kernel_ms": sum(kern_ms) / len(kern_ms),
         "words_per_playout": words_per_step / playouts_per_step,
         "e2e": {"value": e2e_value, "unit": "playouts/s", "h2d_bytes_per_step": int(host_roots.numel()),
                 "d2h_bytes_per_step": int(host_stats.numel() * 4)},
-        # per step: forest reset, pipeline begin, per iteration (select + rollout) x chains,
+        # kernels per step: forest reset, pipeline begin, per 64-iteration chunk one
+        # determinization launch per chain, per iteration (select + rollout) x chains,
         # final backprop, root stats
-        "gpu_launches": args.steps * (4 + 2 * budget * chains),
+        "gpu_launches": args.steps * (4 + chains * (-(-budget // 64)) + 2 * budget * chains),
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops, "traffic": None,
                      "peak_kind": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind})",
@@ -430,6 +434,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trees", type=int, default=0, help="override the tree count (small profiling cases)")
     ap.add_argument("--iterations", type=int, default=0, help="override the iterations per tree")
+    ap.add_argument("--chains", type=int, default=0, help="pipeline chains (launch shape only; 0 = default)")
+    ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
+    ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
     ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve"])
     ap.add_argument("--queries", type=int, default=2000, help="serve: number of move queries")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (queries/s)")

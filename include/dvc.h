@@ -167,9 +167,11 @@ int dvc_rollout_batch(dvc_ctx* ctx, const dvc_state* d_leaves, int n_leaves, int
  * h_budgets[t] iterations (one node per iteration at most; 0..2^24) and
  * streams keyed (seed, h_tree_ids ? h_tree_ids[t] : t).  d_roots is copied
  * on `stream`; h_budgets and h_tree_ids are host arrays read during the call.
- * Device memory per tree: a node arena of 641 + 4 * budget 24-byte slots and
- * a determinization table of 2,048 cells (2 players) or 32,768 cells (3-4
- * players) of 8 bytes.  The root views are planned on the device without a
+ * Device memory per tree: a node arena of 641 + 4 * budget 48-byte slots
+ * (node 16 B, cached UCB1 terms 24 B, child link 4 B, creation stamp 4 B), a
+ * determinization table of 2,048 cells (2 players) or 32,768 cells (3-4
+ * players) of 8 bytes, and 64 determinized roots (2 KB) sampled ahead by
+ * engine 2.  The root views are planned on the device without a
  * host synchronisation; a view whose table does not fit latches
  * DVC_E_UNSUPPORTED and its tree does no work.  DVC_E_OOM if memory runs out.
  */
@@ -207,14 +209,18 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
  * leaves' playouts).  engine 2: per iteration two launches (backprop of the
  * previous iteration + select, then pooled rollouts) in a CUDA graph of 64
  * iterations; rollout CTAs pool trees_per_cta trees with warps_per_cta warps,
- * and the CTAs are split into `chains` (1..4; 0 = keep, default 2)
- * independent chains on separate streams so that one chain's tree walks run
- * beside another chain's playouts.  engine 0 keeps the
- * current engine (the default is 2 for forests of even budgets and at least
- * two trees per SM, else 1).  trees_per_cta / warps_per_cta 0 = defaults
- * (ceil(n_trees / SMs) trees; 16 warps fused, 32 pipeline).  Changing
+ * and the CTAs are split into `chains` (1..8) independent chains on
+ * separate streams so that one chain's tree walks run beside another chain's
+ * playouts.  The determinizations of the graph's 64 iterations are sampled
+ * up front, one thread per tree and iteration.  engine 0 keeps the current
+ * engine (the default is 2 for forests of at least two trees per SM, else 1).
+ * trees_per_cta, warps_per_cta, chains 0 = the engine's defaults (fused:
+ * ceil(n_trees / SMs) trees, at most 32, and one warp per tree up to 16;
+ * pipeline: min(8, n_trees / (2 SMs)) chains, 2 n_trees / (3 chains SMs)
+ * trees, at most 64, and 16 warps).  Changing
  * trees_per_cta re-balances which trees share a CTA (longest budget first,
- * least-loaded CTA) and synchronises the device once.  DVC_E_UNSUPPORTED if
+ * least-loaded CTA; equal budgets keep index order) and synchronises the
+ * device once.  DVC_E_UNSUPPORTED if
  * a CTA's state would not fit in shared memory.
  */
 int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_cta, int chains);

@@ -13,7 +13,8 @@ import os
 import numpy as np
 import torch
 
-CANDIDATES = [(2, 0, 32, 2), (2, 0, 32, 1), (2, 0, 32, 4), (2, 0, 16, 2), (1, 0, 16, 0), (1, 0, 32, 0)]
+CANDIDATES = [(2, 0, 0, 0), (2, 2, 16, 8), (2, 4, 16, 4), (2, 4, 16, 8), (2, 2, 8, 8), (2, 0, 32, 2), (1, 0, 16, 0),
+              (1, 0, 32, 0)]
 _CACHE = os.path.join(os.path.expanduser("~"), ".cache", "dvc", "autotune.json")
 
 

@@ -481,13 +481,56 @@ struct WordQueue {
     __device__ __forceinline__ uint32_t used() const { return 4u * blk - left; }
 };
 
+// The same stream as WordQueue, queued in shared memory: a ring of 16 words
+// per thread, word s of thread t at ring[s * stride + t] (a warp's lanes hit
+// consecutive banks).  Refills are warp-wide: when any lane is short of words,
+// every lane with room for a block appends its next Philox block, so one
+// evaluation of the Philox rounds serves most lanes of the warp instead of
+// the few that ran dry.  Word order per stream is unchanged.
+struct RingQueue {
+    uint32_t* ring;  // &ring[threadIdx.x]
+    uint32_t stride;
+    uint32_t k0, k1, j, i, tw;
+    uint32_t head, tail;  // words handed out / appended (tail = 4 x blocks)
+
+    __device__ __forceinline__ void open(uint64_t seed, uint32_t tree, uint32_t jj, uint32_t ii, uint32_t tag) {
+        k0 = (uint32_t)seed;
+        k1 = tree;
+        j = jj;
+        i = ii;
+        tw = tag + 16u * (uint32_t)(seed >> 32);
+        head = tail = 0u;
+    }
+    // make at least n (<= 4) words available; called by converged lanes
+    __device__ __forceinline__ void ensure(uint32_t n) {
+        const uint32_t left = tail - head;
+        if (__any_sync(__activemask(), left < n) && left <= 12u) {
+            uint32_t a = tail >> 2, b = j, c = i, d = tw;
+            philox10(a, b, c, d, k0, k1);
+            const uint32_t s = tail & 15u;  // tail is a multiple of 4: slots s..s+3 do not wrap
+            ring[s * stride] = a;
+            ring[(s + 1u) * stride] = b;
+            ring[(s + 2u) * stride] = c;
+            ring[(s + 3u) * stride] = d;
+            tail += 4u;
+        }
+    }
+    __device__ __forceinline__ uint32_t next() {
+        const uint32_t r = ring[(head & 15u) * stride];
+        ++head;
+        return r;
+    }
+    __device__ __forceinline__ uint32_t used() const { return head; }
+};
+
 // One step of a two-player, 24-tile playout (no jokers): the mover guesses;
 // a correct guess reveals the tile and either ends the game, grants another
 // guess (continue coin) or passes the turn; a wrong guess reveals the mover's
 // drawn tile (or lowest face-down tile) and passes the turn; the next mover
 // draws.  Same rules and same word order as random_guess + next_turn.
+template <class Q>
 __device__ __forceinline__ int step_2p24(uint32_t& h0, uint32_t& h1, uint32_t& rev, uint32_t& cur, uint32_t& drawn,
-                                         uint32_t& winner, WordQueue& r, uint32_t cont_thr, const uint32_t* magic,
+                                         uint32_t& winner, Q& r, uint32_t cont_thr, const uint32_t* magic,
                                          const unsigned long long* lut12) {
     r.ensure(3);
     const uint32_t hc = cur ? h1 : h0;

@@ -17,6 +17,27 @@
 using namespace dvc;
 using namespace dvc_host;
 
+namespace {
+constexpr int kMaxChains = 8;  // independent chains of the pipeline graph
+
+// Default launch shape of an engine for n trees on `sms` SMs.  Pipeline: many
+// small rollout CTAs (16 warps, about 1.5 CTAs per SM per chain) in up to 8
+// chains, so that the tree walks of some chains run beside the playouts of
+// the others.  Fused: every SM holds a CTA, one warp per tree up to 16.
+void default_shape(int n, int sms, int engine, int& T, int& W, int& chains) {
+    const int S = std::max(sms, 1);
+    if (engine == 2) {
+        chains = std::max(1, std::min(kMaxChains, n / (2 * S)));
+        T = std::max(1, std::min(64, 2 * n / (3 * chains * S)));
+        W = 16;
+    } else {
+        T = std::max(1, std::min(32, (n + S - 1) / S));
+        W = std::min(T, 16);
+        chains = 1;
+    }
+}
+}  // namespace
+
 struct dvc_forest {
     dvc_ctx* ctx;
     int n;
@@ -49,11 +70,10 @@ struct dvc_forest {
     double* csl;
     PipeBufs pipe;
     cudaStream_t cap_stream;  // capture stream for the pipeline graph
-    cudaStream_t chain_stream[3];
-    cudaEvent_t fork_ev, join_ev[3];
-    cudaGraphExec_t chunk_exec;
-    int chunk_iters;
-    int chains;               // independent chains in the pipeline graph (1..4)
+    cudaStream_t chain_stream[7];  // chains 2.. of the pipeline graph (chain 1 runs on cap_stream)
+    cudaEvent_t fork_ev, join_ev[7];
+    cudaGraphExec_t chunk_exec;  // pipeline graph of kChunkIters iterations (captured on first use)
+    int chains;               // independent chains in the pipeline graph (1..8)
     float* probs;             // value mode: win probabilities per tree
     int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
 };
@@ -630,7 +650,7 @@ void dvc_forest_destroy(dvc_forest* f) {
     cudaSetDevice(f->ctx->device);
     if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 7; ++k) {
         if (f->chain_stream[k]) cudaStreamDestroy(f->chain_stream[k]);
         if (f->join_ev[k]) cudaEventDestroy(f->join_ev[k]);
     }
@@ -639,7 +659,7 @@ void dvc_forest_destroy(dvc_forest* f) {
                     f->created,   f->work,      f->paths,     f->movers,         f->leaves,        f->leaf_tree,
                     f->leaf_iter, f->d_words,   f->export_scratch, f->order,     f->ucb,           f->csl,
                     f->pipe.leaf, f->pipe.path, f->pipe.mover, f->pipe.np,       f->pipe.wins,     f->pipe.step_end,
-                    f->probs};
+                    f->pipe.det,  f->pipe.det_base, f->probs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -680,13 +700,10 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     // slot (CTAs hold trees_per_cta trees): balances uneven forests.
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    f->trees_per_cta = std::max(1, std::min(32, (n + std::max(sms, 1) - 1) / std::max(sms, 1)));
-    // enough trees to fill the GPU: the pipeline (full-occupancy playouts),
-    // two rollout CTAs' worth of trees per SM split over two chains;
-    // small forests: the fused lockstep kernel
+    // enough trees to fill the GPU: the pipeline; small forests: the fused
+    // lockstep kernel
     f->engine = n >= 2 * std::max(sms, 1) ? 2 : 1;
-    if (f->engine == 2)
-        f->trees_per_cta = std::max(1, std::min(64, (n + 2 * std::max(sms, 1) - 1) / (2 * std::max(sms, 1))));
+    default_shape(n, sms, f->engine, f->trees_per_cta, f->warps_per_cta, f->chains);
     std::vector<int32_t> order(n);
     {
         const int T = f->trees_per_cta;
@@ -741,7 +758,9 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         alloc((void**)&f->ucb, sizeof(double2) * (size_t)slots) && alloc((void**)&f->csl, sizeof(double) * (size_t)slots) &&
         alloc((void**)&f->pipe.leaf, sizeof(dvc_state) * n) && alloc((void**)&f->pipe.path, sizeof(int32_t) * kPathMax * n) &&
         alloc((void**)&f->pipe.mover, (size_t)kPathMax * n) && alloc((void**)&f->pipe.np, sizeof(int32_t) * n) &&
-        alloc((void**)&f->pipe.wins, sizeof(int32_t) * 4 * n) && alloc((void**)&f->pipe.step_end, sizeof(int32_t) * n);
+        alloc((void**)&f->pipe.wins, sizeof(int32_t) * 4 * n) && alloc((void**)&f->pipe.step_end, sizeof(int32_t) * n) &&
+        alloc((void**)&f->pipe.det, sizeof(dvc_state) * kDetAhead * (size_t)n) &&
+        alloc((void**)&f->pipe.det_base, sizeof(int32_t) * n);
     if (!ok) {
         dvc_forest_destroy(f);
         return fail(c, DVC_E_OOM, "dvc_forest_create: device allocation of " + std::to_string(slots) + " node slots");
@@ -751,6 +770,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->roots, d_roots, sizeof(dvc_state) * n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->pipe.det_base, 0xC0, sizeof(int32_t) * n, st);  // none ahead
     if (e != cudaSuccess) {
         dvc_forest_destroy(f);
         return cuda_fail(c, e, "dvc_forest_create copy");
@@ -763,7 +783,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     }
     bool sok = cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&f->fork_ev, cudaEventDisableTiming) == cudaSuccess;
-    for (int k = 0; k < 3 && sok; ++k)
+    for (int k = 0; k < 7 && sok; ++k)
         sok = cudaStreamCreateWithFlags(&f->chain_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&f->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
     if (!sok) {
@@ -771,7 +791,6 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         dvc_forest_destroy(f);
         return fail(c, DVC_E_CUDA, "dvc_forest_create: streams");
     }
-    f->chains = 2;
     *out = f;
     return DVC_OK;
 }
@@ -835,17 +854,36 @@ int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
     const int i0 = std::min(n, b0 * L), i1 = std::min(n, b1 * L);
     if (i1 <= i0) return DVC_OK;
     pipe_select_kernel<<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
-    const uint32_t smem = pipe_rollout_smem(L);
     const int threads = pipe_rollout_threads(f);
     if (c->cfg.nplayers == 2 && c->cfg.ntiles == 24)
-        pipe_rollout_kernel<true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
+        pipe_rollout_kernel<true><<<b1 - b0, threads, pipe_rollout_smem(L, threads, true), st>>>(
+            sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
     else
-        pipe_rollout_kernel<false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
+        pipe_rollout_kernel<false><<<b1 - b0, threads, pipe_rollout_smem(L, threads, false), st>>>(
+            sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
     return check_launch(c, "pipeline kernels");
 }
 
+// Sample the next `count` determinizations of the trees of CTAs [b0, b1) ahead.
+int enqueue_pipe_det(dvc_forest* f, int b0, int b1, int count, cudaStream_t st) {
+    const int n = f->n, L = f->trees_per_cta;
+    const int i0 = std::min(n, b0 * L), i1 = std::min(n, b1 * L);
+    if (i1 <= i0 || count <= 0) return DVC_OK;
+    const long long threads = (long long)(i1 - i0) * count;
+    pipe_det_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(dev_of(f), params_of(f), i0, i1, f->order,
+                                                                       f->pipe, count);
+    return check_launch(f->ctx, "pipe_det_kernel");
+}
+
+// Outside a pipeline step no tree has determinizations sampled ahead.
+int clear_pipe_det(dvc_forest* f, cudaStream_t st) {
+    // 0xC0C0C0C0 is below -2^29: no iteration lies within kDetAhead of it
+    const cudaError_t e = cudaMemsetAsync(f->pipe.det_base, 0xC0, sizeof(int32_t) * f->n, st);
+    return e == cudaSuccess ? DVC_OK : cuda_fail(f->ctx, e, "pipeline determinization buffer");
+}
+
 constexpr int kChunkIters = 64;
-constexpr int kMaxChains = 4;
+static_assert(kChunkIters <= kDetAhead, "a chunk's determinizations are sampled at its start");
 
 // CTA range of chain k when the grid is split into `chains` independent chains.
 void chain_range(const dvc_forest* f, int k, int chains, int& b0, int& b1) {
@@ -864,11 +902,17 @@ int capture_chunk(dvc_forest* f) {
     cudaError_t e = cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "pipeline capture");
     int rc = DVC_OK;
-    cudaStream_t ss[kMaxChains] = {f->cap_stream, f->chain_stream[0], f->chain_stream[1], f->chain_stream[2]};
+    cudaStream_t ss[kMaxChains] = {f->cap_stream};
+    for (int k = 1; k < kMaxChains; ++k) ss[k] = f->chain_stream[k - 1];
     if (chains > 1) {
         e = cudaEventRecord(f->fork_ev, f->cap_stream);
         for (int k = 1; k < chains && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], f->fork_ev, 0);
         if (e != cudaSuccess) rc = cuda_fail(c, e, "pipeline fork");
+    }
+    for (int k = 0; k < chains && rc == DVC_OK; ++k) {
+        int b0, b1;
+        chain_range(f, k, chains, b0, b1);
+        rc = enqueue_pipe_det(f, b0, b1, kChunkIters, ss[k]);
     }
     for (int it = 0; it < kChunkIters && rc == DVC_OK; ++it)
         for (int k = 0; k < chains && rc == DVC_OK; ++k) {
@@ -900,14 +944,20 @@ int capture_chunk(dvc_forest* f) {
 
 int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     dvc_ctx* c = f->ctx;
-    const uint32_t smem = pipe_rollout_smem(f->trees_per_cta);
     {
+        const int threads = pipe_rollout_threads(f);
         cudaError_t e = cudaFuncSetAttribute(pipe_rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+                                             (int)pipe_rollout_smem(f->trees_per_cta, threads, true));
+        // two 1024-thread CTAs per SM need the largest shared-memory carveout
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pipe_rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaFuncSetAttribute(pipe_rollout_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pipe_rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pipe_rollout_smem(f->trees_per_cta, threads, false));
         if (e != cudaSuccess) return cuda_fail(c, e, "pipeline attributes");
     }
+    if (int rc = clear_pipe_det(f, st)) return rc;
     pipe_begin_kernel<<<(f->n + 127) / 128, 128, 0, st>>>(dev_of(f), f->n, n_iterations, f->pipe.step_end);
     if (int rc = check_launch(c, "pipe_begin_kernel")) return rc;
     int left = n_iterations;
@@ -921,6 +971,7 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
         }
     }
     const int grid = (f->n + f->trees_per_cta - 1) / f->trees_per_cta;
+    if (int rc = enqueue_pipe_det(f, 0, grid, left, st)) return rc;
     for (; left > 0; --left)
         if (int rc = enqueue_pipe_iteration(f, 0, grid, st)) return rc;
     pipe_backprop_kernel<<<(f->n * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), f->n, f->pipe);
@@ -940,6 +991,7 @@ int launch_value_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     const ForestDev fd = dev_of(f);
     const SearchParams sp = params_of(f);
     const int n = f->n;
+    if (int rc = clear_pipe_det(f, st)) return rc;
     pipe_begin_kernel<<<(n + 127) / 128, 128, 0, st>>>(fd, n, n_iterations, f->pipe.step_end);
     if (int rc = check_launch(c, "pipe_begin_kernel")) return rc;
     for (int it = 0; it < n_iterations; ++it) {
@@ -975,12 +1027,16 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     if (engine < 0 || engine > 2 || trees_per_cta < 0 || trees_per_cta > 64 || warps_per_cta < 0 ||
         warps_per_cta > 32 || chains < 0 || chains > kMaxChains)
         return fail(f->ctx, DVC_E_INVALID,
-                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..4");
+                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..8");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->ctx->device);
-    const int T = trees_per_cta ? trees_per_cta
-                                : std::max(1, std::min(32, (f->n + std::max(sms, 1) - 1) / std::max(sms, 1)));
-    const PoolLayout L(T, warps_per_cta ? warps_per_cta : std::min(T, 16));
+    const int eng = engine ? engine : f->engine;
+    int dT, dW, dC;
+    default_shape(f->n, sms, eng, dT, dW, dC);
+    const int T = trees_per_cta ? trees_per_cta : dT;
+    const int W = warps_per_cta ? warps_per_cta : (trees_per_cta && eng == 1 ? std::min(T, 16) : dW);
+    const int oldT = f->trees_per_cta, oldW = f->warps_per_cta, oldC = f->chains;
+    const PoolLayout L(T, W);
     if (L.bytes > 200 * 1024) return fail(f->ctx, DVC_E_UNSUPPORTED, "dvc_forest_tune: CTA state exceeds shared memory");
     if (T != f->trees_per_cta) {
         // re-balance the tree order for the new CTA size (host work, then one copy)
@@ -1015,15 +1071,14 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
         if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_tune");
         f->trees_per_cta = T;
     }
-    if (engine) f->engine = engine;
-    const int ch = chains ? chains : f->chains;
-    if (f->warps_per_cta != warps_per_cta || T != f->chunk_iters || ch != f->chains) {
+    f->engine = eng;
+    const int ch = chains ? chains : dC;
+    if (W != oldW || T != oldT || ch != oldC) {
         // the captured pipeline graph holds the old launch shape
         if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
         f->chunk_exec = nullptr;
     }
-    f->warps_per_cta = warps_per_cta;
-    f->chunk_iters = T;
+    f->warps_per_cta = W;
     f->chains = ch;
     return DVC_OK;
 }
@@ -1209,9 +1264,11 @@ int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_s
     if (int rc = set_device(c)) return rc;
     // device bytes per search slot: node arena (48 B per slot: node, UCB terms,
     // link, creation stamp), counting table, plan, meta and pipeline buffers
+    // (determinizations sampled ahead included)
     const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 48;
     const size_t table = (size_t)(c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells) * 8;
-    const size_t per_slot = arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) + 256;
+    const size_t per_slot = arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) +
+                            sizeof(dvc_state) * kDetAhead + 256;
     const long long total = (long long)(hbm_budget / per_slot);
     const long long nv = c->vnet ? total * value_share_pct / 100 : 0;
     const long long nr = total - nv;

@@ -15,6 +15,8 @@
 
 namespace dvc {
 
+constexpr int kDetAhead = 64;  // determinizations sampled ahead per tree
+
 struct PipeBufs {
     dvc_state* leaf;    // per tree
     int32_t* path;      // per tree, kPathMax slots
@@ -22,6 +24,8 @@ struct PipeBufs {
     int32_t* np;        // per tree: path length, -1 if the tree does not run this iteration
     int32_t* wins;      // per tree, 4 seats
     int32_t* step_end;  // per tree: iteration at which this step stops
+    dvc_state* det;     // per tree, kDetAhead determinized roots: iterations det_base .. det_base + kDetAhead - 1
+    int32_t* det_base;  // per tree; far below zero (bytes 0xC0) when nothing is sampled ahead
 };
 
 __global__ void pipe_begin_kernel(ForestDev F, int n, int n_iter, int32_t* step_end) {
@@ -49,6 +53,31 @@ __device__ __forceinline__ void pipe_apply_pending(ForestDev& F, const SearchPar
     __syncwarp();
 }
 
+// A determinization depends only on the root view, the seed, the tree id and
+// the iteration (stream tag 2), not on the tree's statistics, so the next
+// `count` of them are sampled up front, one thread per (tree, iteration),
+// instead of on the tree walk's critical path.  Trees order[i0 .. i1-1].
+__global__ void __launch_bounds__(128)
+    pipe_det_kernel(ForestDev F, SearchParams sp, int i0, int i1, const int32_t* order, PipeBufs P, int count) {
+    const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int i = i0 + g / count, k = g % count;
+    if (i >= i1) return;
+    const int t = order[i];
+    const TreeMeta& tm = F.meta[t];
+    // the tree's next select first applies its pending backprop (done + 1)
+    const int32_t base = tm.done + (P.np[t] >= 0 ? 1 : 0);
+    if (k == 0) P.det_base[t] = base;
+    if (base + k >= P.step_end[t]) return;
+    const G root = load_state(F.roots[t]);
+    Rng dr;
+    dr.open(sp.seed, tm.tree_id, 0u, (uint32_t)(base + k), kTagDet);
+    G det;
+    det_sample(F.plans[t], F.tables + tm.table_off, root, dr, det);
+    dvc_state s;
+    store_state(det, s);
+    P.det[(size_t)t * kDetAhead + k] = s;
+}
+
 // Finish the previous iteration of tree t (backprop) and run its next
 // selection and expansion.
 // Trees order[i0 .. i1-1], one warp each.
@@ -70,10 +99,15 @@ __global__ void __launch_bounds__(128)
     Node* nodes = F.nodes + tm.node_off;
     int32_t* link = F.link + tm.node_off;
     const G root = load_state(F.roots[t]);
-    Rng dr;
-    dr.open(sp.seed, tm.tree_id, 0u, it, kTagDet);
     G det;
-    det_sample(F.plans[t], F.tables + tm.table_off, root, dr, det);
+    const uint32_t ahead = it - (uint32_t)P.det_base[t];
+    if (ahead < (uint32_t)kDetAhead) {
+        det = load_state(P.det[(size_t)t * kDetAhead + ahead]);
+    } else {
+        Rng dr;
+        dr.open(sp.seed, tm.tree_id, 0u, it, kTagDet);
+        det_sample(F.plans[t], F.tables + tm.table_off, root, dr, det);
+    }
     Descent d;
     int32_t* path = P.path + (size_t)t * kPathMax;
     uint8_t* mover = P.mover + (size_t)t * kPathMax;
@@ -103,16 +137,22 @@ __global__ void __launch_bounds__(128)
 }
 
 // Trees order[b*L .. b*L+L-1] belong to CTA b; this launch runs CTAs b0 + blockIdx.x.
+// The CTA's L x P playouts form one pool: a lane whose game ends takes the
+// next playout index (warp-aggregated: one shared-memory atomic per warp and
+// step), so lanes wait for the longest game only at the end of the pool.
+// Two-player 24-tile games queue their words in a shared-memory ring
+// (RingQueue) so that two 1024-thread CTAs fit on an SM.
 template <bool FAST2>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     pipe_rollout_kernel(SearchParams sp, int n, int L, int b0, const int32_t* order, const TreeMeta* meta, PipeBufs P,
                         unsigned long long* words_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_magic[32];
     __shared__ unsigned long long s_lut12[FAST2 ? 4096 : 1];
     __shared__ int32_t s_n, s_next;
-    int32_t* s_tree = (int32_t*)smem;       // listed leaves: tree index
-    int32_t* s_wins = s_tree + L;           // 4 per listed leaf
+    uint32_t* s_ring = (uint32_t*)smem;                            // FAST2: 16 words per thread
+    int32_t* s_tree = (int32_t*)(smem + (FAST2 ? 64u * blockDim.x : 0u));  // listed leaves: tree index
+    int32_t* s_wins = s_tree + L;                                  // 4 per listed leaf
     uint32_t* s_tid = (uint32_t*)(s_wins + 4 * L);
     uint32_t* s_it = s_tid + L;
     dvc_state* s_leaf = (dvc_state*)(((uintptr_t)(s_it + L) + 15) & ~(uintptr_t)15);
@@ -142,15 +182,24 @@ __global__ void __launch_bounds__(1024, 1)
         s_wins[4 * k] = s_wins[4 * k + 1] = s_wins[4 * k + 2] = s_wins[4 * k + 3] = 0;
     }
     __syncthreads();
-    const int Pp = sp.playouts;
-    const int total = nl * Pp;
+    const uint32_t Pp = (uint32_t)sp.playouts;
+    const uint32_t total = (uint32_t)nl * Pp;
+    // playout p belongs to leaf p / Pp: multiply-high by ceil(2^32 / Pp) gives
+    // the quotient or one more (p < 2^32), fixed by one comparison
+    const uint32_t mP = Pp > 1u ? 0xFFFFFFFFu / Pp + 1u : 0u;
     unsigned long long words = 0ull;
-    int k = 0, steps = 0;
-    WordQueue r;
+    uint32_t k = 0, steps = 0;
+    using Queue = typename std::conditional<FAST2, RingQueue, WordQueue>::type;
+    Queue r;
+    if constexpr (FAST2) {
+        r.ring = s_ring + tid;
+        r.stride = blockDim.x;
+    }
     G g;
     uint32_t h0 = 0, h1 = 0, rev = 0, cur = 0, drawn = kNone, winner = kNone;
-    auto start = [&](int p) {
-        k = p / Pp;
+    auto start = [&](uint32_t p) {
+        k = Pp > 1u ? __umulhi(p, mP) : p;
+        if (k * Pp > p) --k;
         const dvc_state& ls = s_leaf[k];
         if constexpr (FAST2) {
             h0 = ls.hand[0];
@@ -162,13 +211,25 @@ __global__ void __launch_bounds__(1024, 1)
         } else {
             g = load_state(ls);
         }
-        r.open(sp.seed, s_tid[k], (uint32_t)(p - k * Pp), s_it[k], kTagRoll);
+        r.open(sp.seed, s_tid[k], p - k * Pp, s_it[k], kTagRoll);
         steps = 0;
     };
-    int p = atomicAdd(&s_next, 1);
+    // the lanes in `want` take consecutive playout indices (all lanes call)
+    auto take = [&](bool want) -> uint32_t {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+        uint32_t base = 0;
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) base = (uint32_t)atomicAdd(&s_next, __popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        }
+        return base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+    };
+    uint32_t p = take(true);
     bool busy = p < total;
     if (busy) start(p);
     while (__any_sync(0xFFFFFFFFu, busy)) {
+        bool ended = false;
         if (busy) {
             int res;
             if constexpr (FAST2) {
@@ -180,13 +241,18 @@ __global__ void __launch_bounds__(1024, 1)
                 winner = g.winner;
             }
             ++steps;
-            if (res == kGameOver || steps >= 128) {
+            if (res == kGameOver || steps >= 128u) {
                 const uint32_t w = res == kGameOver ? winner : kNone;
-                if (w < 4u) atomicAdd(&s_wins[4 * k + (int)w], 1);
+                if (w < 4u) atomicAdd(&s_wins[4 * k + w], 1);
                 words += r.used();
-                p = atomicAdd(&s_next, 1);
-                busy = p < total;
-                if (busy) start(p);
+                ended = true;
+            }
+        }
+        if (__any_sync(0xFFFFFFFFu, ended)) {
+            const uint32_t q = take(ended);
+            if (ended) {
+                busy = q < total;
+                if (busy) start(q);
             }
         }
     }
@@ -222,8 +288,10 @@ __global__ void pipe_value_wins_kernel(int n, PipeBufs P, const float* probs, in
     for (int s = 0; s < 4; ++s) w[s] = (int32_t)(probs[4 * t + s] * (float)playouts + 0.5f);
 }
 
-__host__ __device__ inline uint32_t pipe_rollout_smem(int L) {
-    return (uint32_t)(4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
+// Dynamic shared memory of pipe_rollout_kernel: the word rings (two-player
+// 24-tile games) and the listed leaves.
+__host__ __device__ inline uint32_t pipe_rollout_smem(int L, int threads, bool fast2) {
+    return (uint32_t)((fast2 ? 64 * threads : 0) + 4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
 }
 
 }  // namespace dvc

@@ -288,11 +288,16 @@ def test_uneven_workload_sampled(dvc):
     _check_forest(forest, stats, want, sample)
 
 
-@pytest.mark.parametrize("shape", [(1, 3, 2, 0), (1, 5, 8, 0), (1, 2, 1, 0), (1, 7, 3, 0), (2, 3, 2, 1), (2, 5, 32, 2),
-                                   (2, 1, 4, 4), (2, 2, 2, 3)])
-def test_mcts_launch_shapes_agree(dvc, shape):
-    """Trees per CTA and warps per CTA change only who does the work."""
-    kw = dict(VARIANTS["4p26j"], playouts=8)
+@pytest.mark.parametrize("variant,shape", [
+    ("4p26j", (1, 3, 2, 0)), ("4p26j", (1, 5, 8, 0)), ("4p26j", (1, 2, 1, 0)), ("4p26j", (1, 7, 3, 0)),
+    ("4p26j", (2, 3, 2, 1)), ("4p26j", (2, 5, 32, 2)), ("4p26j", (2, 1, 4, 4)), ("4p26j", (2, 2, 2, 3)),
+    # two players, 24 tiles: the playout fast path with its shared-memory word rings
+    ("2p24", (2, 3, 16, 4)), ("2p24", (2, 7, 16, 2)), ("2p24", (2, 2, 8, 3)), ("2p24", (2, 11, 32, 1)),
+    ("2p24", (1, 4, 16, 0)),
+])
+def test_mcts_launch_shapes_agree(dvc, variant, shape):
+    """Trees per CTA, warps per CTA and chains change only who does the work."""
+    kw = dict(VARIANTS[variant], playouts=8 if variant == "4p26j" else 48)
     ctx = _ctx(dvc, **kw)
     n = 11
     budgets = [40, 7, 90, 0, 33, 64, 1, 55, 20, 80, 12]
