@@ -397,6 +397,75 @@ def run_uneven(args, w):
         "decisions_per_s": w.n_trees * args.steps / total_s, "clocks": clk}), flush=True)
 
 
+def run_selfplay(args):
+    """The value network against playouts: train it on states labelled by
+    1,024-playout estimates, measure its win-probability error and move
+    agreement, then play games between the value agent and the playout agent
+    at equal iteration budgets (one line of JSON)."""
+    import numpy as np
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build, selfplay
+    from paper_2403_10720_gb300 import value_train as vt
+    build.build()
+    w = BATCHED
+    kw = dict(w.config_kwargs(), playouts=32)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(1)
+    t0 = time.perf_counter()
+    states, labels = vt.make_dataset(ctx, args.train_states, root_seed=1001)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    curve = vt.train(ctx, states, labels, epochs=args.epochs, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del states, labels
+    hs, hl = vt.make_dataset(ctx, 16384, root_seed=2002)
+    err = {"net": vt.mean_abs_error(ctx.dvc_value_eval(hs), hl, hs)}
+    for k in (16, 64, 256):
+        err[f"playouts_{k}"] = vt.mean_abs_error(vt.rollout_estimate(ctx, hs, k), hl, hs)
+    roots = ctx.dvc_init_states(w.root_seed, 4096)
+    agree = selfplay.move_agreement(ctx, dvc, roots, args.move_budget, 16 * args.move_budget, seed=7)
+    # GPU time per decision of each agent on the same 4,096 positions
+    per_dec = {}
+    for name, mode in (("value", dvc.DVC_MODE_VALUE), ("rollout", dvc.DVC_MODE_ROLLOUT)):
+        f = dvc.Forest(ctx, roots, [args.move_budget] * 4096, 5)
+        f.dvc_mcts_step(args.move_budget, mode=mode)
+        f.dvc_forest_reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f.dvc_mcts_step(args.move_budget, mode=mode)
+        b.record()
+        torch.cuda.synchronize()
+        per_dec[name] = a.elapsed_time(b) / 4096
+        f.close()
+    # games: fresh deals of the same variant
+    gctx = dvc.Context(dvc.Config(**dict(kw, max_predraw=0)), 0)
+    params = ctx.dvc_value_params()
+    gctx.dvc_value_init(1)
+    gctx.dvc_value_params(params)
+    server = dvc.Server(gctx, int(args.hbm_gb * (1 << 30)), args.move_budget, value_share_pct=50, seed=9)
+    games = selfplay.play_games(gctx, server, args.games, args.move_budget, root_seed=3003, seed=11,
+                                poll_iters=args.move_budget)
+    server.close()
+    print(json.dumps({
+        "metric": "value-agent win rate", "value": games["value_win_rate"], "unit": "fraction of games",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "bf16 net / u32 playouts", "data": "synthetic",
+        "config": {"workload": "2p24_value_vs_playouts_selfplay", "train_states": args.train_states,
+                   "label_playouts": 1024, "epochs": args.epochs, "games": args.games,
+                   "iterations_per_move": args.move_budget, "playouts_per_leaf": 32, "players": 2, "tiles": 24},
+        "ci95": games["ci95"], "fair_share": games["fair_share"], "games_finished": games["games_finished"],
+        "turns": games["turns"], "selfplay_decisions_per_s": games["decisions_per_s"],
+        "selfplay_wall_s": games["wall_s"],
+        "winprob_abs_err_heldout": err, "move_agreement": agree,
+        "gpu_ms_per_decision": per_dec,
+        "train": {"label_s": t_label, "train_s": t_train, "loss_first_epoch": curve[0], "loss_last_epoch": curve[-1]},
+    }), flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals of move queries into a device-resident server."""
     import numpy as np
@@ -437,7 +506,11 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="pipeline chains (launch shape only; 0 = default)")
     ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve", "selfplay"])
+    ap.add_argument("--train-states", type=int, default=10_000_000, help="selfplay: training states")
+    ap.add_argument("--epochs", type=int, default=4, help="selfplay: training epochs")
+    ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
+    ap.add_argument("--move-budget", type=int, default=256, help="selfplay: UCT iterations per move")
     ap.add_argument("--queries", type=int, default=2000, help="serve: number of move queries")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (queries/s)")
     ap.add_argument("--max-budget", type=int, default=100000, help="serve: largest query budget")
@@ -449,6 +522,11 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "selfplay":
+        if args.hbm_gb == 64.0:
+            args.hbm_gb = 4.0
+        run_selfplay(args)
         return
     w = BATCHED
     if args.trees or args.iterations:

@@ -38,7 +38,8 @@
  * Random numbers: Philox-4x32-10 (Salmon et al., SC'11).  A stream is keyed
  * (low 32 bits of seed, tree id) with counter (block, playout j, iteration or
  * leaf i, tag + 16 * high 32 bits of seed), tag 1 = root-state generation,
- * 2 = determinization, 3 = draws inside the tree, 4 = playouts.  Words of a
+ * 2 = determinization, 3 = draws inside the tree, 4 = playouts, 5 = draws of
+ * self-play games (dvc_play_move).  Words of a
  * block are consumed in order.  Every result is therefore a pure function of
  * (seed, tree id, iteration, playout index) and does not depend on the thread
  * mapping, the launch shape or the order in which playouts finish.
@@ -118,7 +119,8 @@ void dvc_destroy(dvc_ctx* ctx);
 const char* dvc_last_error(const dvc_ctx* ctx);
 
 /* Synchronise the context's device and report (then clear) any error a
- * kernel latched: DVC_E_UNSUPPORTED, DVC_E_OOM or DVC_E_TIMEOUT. */
+ * kernel latched: DVC_E_UNSUPPORTED, DVC_E_OOM, DVC_E_TIMEOUT, or
+ * DVC_E_INVALID for an illegal guess passed to dvc_play_move. */
 int dvc_check(dvc_ctx* ctx);
 
 /*
@@ -160,6 +162,20 @@ int dvc_determinize(dvc_ctx* ctx, const dvc_state* d_roots, int n, int observer,
 int dvc_rollout_batch(dvc_ctx* ctx, const dvc_state* d_leaves, int n_leaves, int playouts_per_leaf, uint64_t seed,
                       const uint32_t* d_tree_ids, const uint32_t* d_leaf_ids, int32_t* d_wins, uint64_t* d_words,
                       void* stream);
+
+/*
+ * One move of each of n games played out by search agents (self-play; the
+ * game model the tree searches, Sec. III-A simplification 2): the seat to
+ * move in d_states[i] makes the guess d_actions[i] (action code seat << 10 |
+ * slot << 5 | identity, as dvc_root_stats reports it) on the true state; the
+ * turn ends after the guess, correct or not; then the next seat still in
+ * draws on stream (seed, d_game_ids[i] or i if NULL, turn, tag 5).  d_states
+ * is updated in place; d_actions[i] < 0 or a finished game leaves the record
+ * unchanged.  An illegal guess leaves the record unchanged and latches
+ * DVC_E_INVALID (see dvc_check).  All pointers are device memory.
+ */
+int dvc_play_move(dvc_ctx* ctx, dvc_state* d_states, int n, const int32_t* d_actions, uint64_t seed,
+                  const uint32_t* d_game_ids, uint32_t turn, void* stream);
 
 /*
  * A forest of independent UCT trees (Sec. II-B; Sec. III-B runs many at

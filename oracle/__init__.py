@@ -17,6 +17,9 @@ Pin status per function:
   det_count ......... pinned (brute-force enumeration of consistent deals)
   determinize ....... pinned (chi-square against uniform over those deals)
   mcts .............. pinned (UCB1 forced-win toy sequence, count invariants)
+  legal_actions ..... pinned (88 root guesses, canonical order written out)
+  play_move ......... pinned (hand-made positions: correct and wrong guesses,
+                      elimination, empty pool, the draw that follows)
   value_features .... pinned (hand-made positions with features written out)
   value_forward ..... pinned (closed form with zero hidden weights)
   value_loss_grad ... pinned (central finite differences in double)
@@ -92,6 +95,10 @@ def lib():
         L.or_playout_trace.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_uint32, u8p, ctypes.c_int]
         L.or_playout_trace.restype = ctypes.c_int
+        L.or_play_move.argtypes = [u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u8p]
+        L.or_play_move.restype = ctypes.c_int
+        L.or_legal_actions.argtypes = [u8p, i32p]
+        L.or_legal_actions.restype = ctypes.c_int
         L.or_mcts.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i32p,
                               ctypes.POINTER(ctypes.c_int), i32p]
         L.or_mcts.restype = ctypes.c_int
@@ -146,6 +153,22 @@ def init_states(cfg: OracleConfig, seed: int, n: int) -> np.ndarray:
 def legal_count(state) -> int:
     s = _state(state)
     return lib().or_legal_count(_u8(s))
+
+
+def legal_actions(state) -> np.ndarray:
+    """Legal guesses in canonical order as action codes (seat << 10 | slot << 5 | identity)."""
+    s = _state(state)
+    out = np.zeros(3 * 26 * 26, dtype=np.int32)
+    n = lib().or_legal_actions(_u8(s), _i32(out))
+    return out[:n].copy()
+
+
+def play_move(state, code: int, seed: int, game: int, turn: int):
+    """Returns (rc, next state): rc 0 played, 1 game already over, -1 illegal guess."""
+    s = _state(state)
+    out = np.zeros(32, dtype=np.uint8)
+    rc = lib().or_play_move(_u8(s), int(code), seed, game, turn, _u8(out))
+    return rc, out
 
 
 def det_count(state, observer: int = -1) -> int:

@@ -51,7 +51,7 @@
 #define MAXP 4
 #define MAXLEGAL (3 * MAXT * MAXT)
 
-enum { TAG_INIT = 1, TAG_DET = 2, TAG_TREE = 3, TAG_ROLL = 4 };
+enum { TAG_INIT = 1, TAG_DET = 2, TAG_TREE = 3, TAG_ROLL = 4, TAG_PLAY = 5 };
 
 typedef struct {
     int32_t nplayers, ntiles, deal, max_predraw, max_revealed;
@@ -772,6 +772,43 @@ int or_legal_count(const uint8_t* state) {
     ost s;
     unpack(state, &s);
     return legal_list(&s, legal_q, legal_s, legal_x);
+}
+
+/* One move of a game played out by search agents (the workload's self-play
+ * games between two leaf evaluators), under the game model the tree searches
+ * (Sec. III-A, simplification 2): the seat to move makes the guess `code`
+ * (seat << 10 | slot << 5 | identity) on the true state, the turn ends after
+ * it whether or not it was correct, and the next seat still in draws on the
+ * stream (seed, game, turn, tag 5).  Returns 0; 1 if the game was already
+ * over; -1 if the guess is not legal (the state is copied unchanged). */
+int or_play_move(const uint8_t* in, int code, uint64_t seed, uint32_t game, uint32_t turn, uint8_t* out) {
+    ost s;
+    unpack(in, &s);
+    if (s.winner >= 0) {
+        pack(&s, out);
+        return 1;
+    }
+    const int q = code >> 10, slot = (code >> 5) & 31, x = code & 31;
+    if (code < 0 || !guess_is_legal(&s, q, slot, x)) {
+        pack(&s, out);
+        return -1;
+    }
+    stream rng;
+    stream_open(&rng, seed, game, 0, turn, TAG_PLAY);
+    if (resolve(&s, q, slot, x, 1, 0, NULL) != GAME_OVER) next_turn(&s, &rng);
+    pack(&s, out);
+    return 0;
+}
+
+/* The legal guesses of a state in canonical order (opponents from the mover
+ * + 1, slots left to right, identities ascending) as action codes; returns
+ * their number (at most 3 * 26 * 26). */
+int or_legal_actions(const uint8_t* state, int32_t* codes) {
+    ost s;
+    unpack(state, &s);
+    const int n = legal_list(&s, legal_q, legal_s, legal_x);
+    for (int a = 0; a < n; a++) codes[a] = (legal_q[a] << 10) | (legal_s[a] << 5) | legal_x[a];
+    return n;
 }
 
 /* --------------------------------------------------------------------- UCT */

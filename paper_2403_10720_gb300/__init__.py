@@ -98,6 +98,7 @@ def lib():
             "dvc_init_states": ([vp, u64, i, vp, vp], i),
             "dvc_determinize": ([vp, vp, i, i, u64, vp, vp, vp, vp], i),
             "dvc_rollout_batch": ([vp, vp, i, i, u64, vp, vp, vp, vp, vp], i),
+            "dvc_play_move": ([vp, vp, i, vp, u64, vp, u32, vp], i),
             "dvc_forest_create": ([vp, i, vp, vp, vp, u64, ctypes.POINTER(vp), vp], i),
             "dvc_forest_destroy": ([vp], None),
             "dvc_forest_reset": ([vp, vp, vp], i),
@@ -212,6 +213,13 @@ class Context:
         self._rc(lib().dvc_rollout_batch(self.h, _ptr(leaves), n, playouts, seed, _ptr(tree_ids), _ptr(leaf_ids),
                                          _ptr(wins), _ptr(words), _stream(stream)), "dvc_rollout_batch")
         return wins
+
+    def dvc_play_move(self, states, actions, seed, turn, game_ids=None, stream=None):
+        """One self-play move per game, in place on `states` (n x 32 uint8);
+        actions: n int32 action codes, -1 = no move."""
+        self._rc(lib().dvc_play_move(self.h, _ptr(states), states.shape[0], _ptr(actions), seed, _ptr(game_ids),
+                                     turn, _stream(stream)), "dvc_play_move")
+        return states
 
     VALUE_NPARAMS = 855556
 

@@ -18,7 +18,7 @@ namespace dvc {
 constexpr uint32_t kNumMask = 0x00FFFFFFu;  // numbered tiles 0..23
 constexpr uint32_t kJokerMask = 0x03000000u;
 constexpr uint32_t kNone = 0xFFu;
-constexpr uint32_t kTagInit = 1, kTagDet = 2, kTagTree = 3, kTagRoll = 4;
+constexpr uint32_t kTagInit = 1, kTagDet = 2, kTagTree = 3, kTagRoll = 4, kTagPlay = 5;
 
 // ------------------------------------------------------------------ Philox
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

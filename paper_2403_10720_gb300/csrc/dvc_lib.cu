@@ -183,6 +183,26 @@ __global__ void determinize_kernel(const dvc_state* roots, int n, int observer, 
 
 // Leaf-parallel playouts: thread -> (leaf, playout).  Win counts are summed
 // with integer atomics, so the result is independent of scheduling.
+// One self-play move per game: the guess actions[i] on the true state, then
+// the next seat's draw on stream (seed, game id, turn, tag 5).
+__global__ void play_move_kernel(dvc_state* states, int n, const int32_t* actions, uint64_t seed,
+                                 const uint32_t* game_ids, uint32_t turn, int32_t* flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t code = actions[i];
+    G g = load_state(states[i]);
+    if (code < 0 || g.winner != kNone) return;  // no move, or the game is over
+    const uint32_t c = (uint32_t)code, q = c >> 10, s = (c >> 5) & 31u, x = c & 31u;
+    if (q > 3u || !guess_legal(g, q, s, x)) {
+        atomicCAS(&flags[0], 0, DVC_E_INVALID);
+        return;
+    }
+    Rng tr;
+    tr.open(seed, game_ids ? game_ids[i] : (uint32_t)i, 0u, turn, kTagPlay);
+    tree_apply(g, c, tr);
+    store_state(g, states[i]);
+}
+
 __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uint64_t seed,
                                const uint32_t* tree_ids, const uint32_t* leaf_ids, uint32_t cont_thr, int32_t* wins,
                                unsigned long long* words) {
@@ -643,6 +663,19 @@ int dvc_rollout_batch(dvc_ctx* c, const dvc_state* d_leaves, int n_leaves, int p
                                                        d_leaf_ids, c->cfg.cont_thr, d_wins,
                                                        (unsigned long long*)d_words);
     return check_launch(c, "rollout_kernel");
+}
+
+int dvc_play_move(dvc_ctx* c, dvc_state* d_states, int n, const int32_t* d_actions, uint64_t seed,
+                  const uint32_t* d_game_ids, uint32_t turn, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (n < 0) return fail(c, DVC_E_INVALID, "dvc_play_move: n < 0");
+    if (n == 0) return DVC_OK;
+    if (!is_device_ptr(d_states) || !is_device_ptr(d_actions) || (d_game_ids && !is_device_ptr(d_game_ids)))
+        return fail(c, DVC_E_INVALID, "dvc_play_move: pointers must be device memory");
+    if (int rc = set_device(c)) return rc;
+    play_move_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_states, n, d_actions, seed, d_game_ids, turn,
+                                                                         c->d_flags);
+    return check_launch(c, "play_move_kernel");
 }
 
 void dvc_forest_destroy(dvc_forest* f) {
