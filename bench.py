@@ -38,6 +38,12 @@ from paper_2403_10720_gb300.workloads import BATCHED, UNEVEN  # noqa: E402
 PHILOX_OPS_PER_WORD = 25  # Philox-4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) per 4 words
 VALUE_MACS_PER_LEAF = 640 * 512 + 2 * 512 * 512 + 512 * 4  # dense layers of the value network
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# DRAM bytes per launch of the pipeline's kernels at the default shape of the
+# 4,096-tree workload (8 chains of 512 trees; 2 trees x 16 warps per rollout
+# CTA), from ncu full captures (cold cache) summarised under profiles/
+# (pipe_select_kernel / pipe_rollout_kernel / pipe_det_kernel _2p24_4096trees_64it.md).
+PROFILED_SHAPE = (8, 2, 16)
+DRAM_PER_LAUNCH = {"select": 450_816, "rollout": 98_048, "det": 517_376}
 
 
 def _env_int(k, d):
@@ -302,6 +308,10 @@ def run_ours(args, w):
     ctx.dvc_check()
     decisions = host_stats.numpy()
 
+    traffic = None
+    if (chains, trees_per_cta, warps) == PROFILED_SHAPE and n == 4096:
+        traffic = (budget * chains * (DRAM_PER_LAUNCH["select"] + DRAM_PER_LAUNCH["rollout"])
+                   + -(-budget // 64) * chains * DRAM_PER_LAUNCH["det"])
     peaks, peak_kind = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_gops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e9
@@ -331,9 +341,13 @@ def run_ours(args, w):
         # final backprop, root stats
         "gpu_launches": args.steps * (4 + chains * (-(-budget // 64)) + 2 * budget * chains),
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved_gops / peak_gops, "traffic": None,
+                     "frac": achieved_gops / peak_gops, "traffic": traffic,
                      "peak_kind": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind})",
-                     "work": "Philox-4x32-10 integer ops of the random words the playouts consume"},
+                     "work": "Philox-4x32-10 integer ops of the random words the playouts consume",
+                     "launch": "one dvc_mcts_step: the CUDA-graph pipeline (determinize-ahead, select, rollout "
+                               "kernels of all chains)",
+                     "traffic_source": "ncu dram__bytes per kernel launch (cold cache) x launches per step; null "
+                                       "when the launch shape differs from the profiled one"},
         "clocks": clk,
         "first_decision": int(decisions[0][0]),
     }
