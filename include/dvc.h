@@ -186,9 +186,10 @@ int dvc_play_move(dvc_ctx* ctx, dvc_state* d_states, int n, const int32_t* d_act
  * Device memory per tree: a node arena of 641 + 4 * budget 48-byte slots
  * (node 16 B, cached UCB1 terms 24 B, child link 4 B, creation stamp 4 B), a
  * determinization table of 2,048 cells (2 players) or 32,768 cells (3-4
- * players) of 8 bytes, and 64 determinized roots (2 KB) sampled ahead by
- * engine 2.  The root views are planned on the device without a
- * host synchronisation; a view whose table does not fit latches
+ * players) of 8 bytes, and 64 determinized roots with the first block of
+ * their in-tree random streams (3 KB) sampled ahead by engine 2.  The root
+ * views are planned on the device without a host synchronisation; a view
+ * whose table does not fit latches
  * DVC_E_UNSUPPORTED and its tree does no work.  DVC_E_OOM if memory runs out.
  */
 int dvc_forest_create(dvc_ctx* ctx, int n_trees, const dvc_state* d_roots, const int32_t* h_budgets,

@@ -68,6 +68,21 @@ struct Rng {
         left = 4;
         ++blk;
     }
+    // Take block 0 as computed elsewhere (e.g. ahead of time); right after open().
+    __device__ __forceinline__ void preload(uint4 b0) {
+        w0 = b0.x;
+        w1 = b0.y;
+        w2 = b0.z;
+        w3 = b0.w;
+        left = 4;
+        blk = 1;
+    }
+    // Block 0 of a stream, as refill() computes it.
+    __device__ __forceinline__ uint4 block0() const {
+        uint32_t a = 0u, b = j, c = i, d = tw;
+        philox10(a, b, c, d, k0, k1);
+        return make_uint4(a, b, c, d);
+    }
     __device__ __forceinline__ uint32_t next() {
         if (left == 0) refill();
         const uint32_t r = w0;

@@ -2,14 +2,18 @@
 // sm_103a, for the value network's dense layers:
 //     C[m, n] = act(sum_k A[m, k] * B[n, k] + bias[n])      (A, B K-major BF16)
 // One CTA computes a 128 x BN tile with FP32 accumulators in tensor memory.
-// Operand tiles of 64 K-elements are staged in shared memory in the 128-byte
-// swizzled K-major layout (8-row atoms of 1024 bytes, 16-byte chunks XOR-ed
-// with the row index) by cp.async, double-buffered; one thread issues the
-// tcgen05.mma instructions (K = 16 each) and commits them to an mbarrier;
-// four warps read the accumulators back with tcgen05.ld for the epilogue.
+// Operand tiles of 64 K-elements arrive by TMA (cp.async.bulk.tensor) in the
+// 128-byte swizzled K-major layout into a ring of S stages guarded by
+// full/empty mbarriers: one producer thread keeps up to S tiles in flight,
+// one MMA thread issues tcgen05.mma (K = 16 each) as tiles land and commits
+// each stage back to the producer; then four warps read the accumulators with
+// tcgen05.ld for the epilogue.  Tiles are numbered with N fastest so the CTAs
+// that share an A tile run together and read it once from HBM.
 // Every wait on an mbarrier is bounded: on time-out the kernel records an
-// error, waits (bounded) for its own MMAs, frees its tensor memory and exits.
+// error, waits (bounded) for its own copies and MMAs, frees its tensor memory
+// and exits.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
 #include <stdint.h>
 
 namespace dvc {
@@ -106,26 +110,18 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, uint32_t bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(bytes) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Byte offset of 16-byte chunk j (0..7) of row r in a 128-byte-swizzled tile.
-__device__ __forceinline__ uint32_t sw128(uint32_t r, uint32_t j) {
-    return (r >> 3) * 1024u + (r & 7u) * 128u + ((j ^ (r & 7u)) << 4);
-}
-
-// Stage rows [0, rows) x 64 K-elements starting at column k0 of a row-major
-// K-major matrix (ld elements per row) into a swizzled tile; rows at or
-// beyond `valid` are zero-filled.
-__device__ __forceinline__ void stage_tile(uint32_t sbase, const __nv_bfloat16* g, int ld, int k0, int rows,
-                                           int valid, int tid, int nthr) {
-    for (int c = tid; c < rows * 8; c += nthr) {
-        const int r = c >> 3, j = c & 7;
-        const bool ok = r < valid;
-        const __nv_bfloat16* src = g + (size_t)(ok ? r : 0) * ld + k0 + j * 8;
-        cp_async16(sbase + sw128((uint32_t)r, (uint32_t)j), src, ok ? 16u : 0u);
-    }
+// 2-D TMA load of box (x = K offset, y = row offset) into shared memory,
+// completing `bytes` of the barrier's transaction count.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
@@ -141,82 +137,102 @@ struct GemmArgs {
     int32_t* flags;
 };
 
-// BN in {16, 32, 64, 128, 256}.  128 threads, dynamic smem = 2 stages x
-// (16 KB + BN x 128 B) + 1024 alignment slack.
+// Stage geometry for a BN-column tile: A 128 x 64 and B BN x 64 BF16 per
+// stage, as many stages as fit in 200 KB (at most 6).
 template <int BN>
-__global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(GemmArgs a) {
+struct GemmCfg {
+    static constexpr uint32_t kA = (uint32_t)kGemmBM * kGemmBK * 2;  // 16 KB
+    static constexpr uint32_t kB = (uint32_t)BN * kGemmBK * 2;
+    static constexpr uint32_t kStage = kA + kB;
+    static constexpr int kStages = (int)((200u * 1024u) / kStage) > 6 ? 6 : (int)((200u * 1024u) / kStage);
+    static constexpr uint32_t kSmem = (uint32_t)kStages * kStage + 1024u;  // + alignment slack
+    static constexpr uint32_t kCols = BN < 32 ? 32u : (uint32_t)BN;       // tensor-memory columns
+};
+
+// BN in {16, 32, 64, 128, 256}; 128 threads; one tile per CTA, tile index
+// blockIdx.x with the N tile fastest.  tA: A as a (K, M) tensor, box (64,
+// 128); tB: B as (K, N), box (64, BN); both 128-byte swizzled.
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, GemmArgs a) {
+    using Cfg = GemmCfg<BN>;
+    constexpr int S = Cfg::kStages;
     extern __shared__ __align__(1024) unsigned char gsm[];
-    __shared__ uint64_t s_bar[2];
-    __shared__ uint64_t s_done;
+    __shared__ uint64_t s_full[S], s_empty[S], s_done;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_fail;
-    constexpr uint32_t kATile = kGemmBM * kGemmBK * 2;  // 16 KB
-    constexpr uint32_t kBTile = BN * kGemmBK * 2;
-    constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+    __shared__ int s_fail, s_issued, s_consumed;
+    volatile int* fail = &s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * kGemmBM, n0 = blockIdx.y * BN;
+    const int ntn = a.N / BN;
+    const int n0 = (int)(blockIdx.x % (unsigned)ntn) * BN, m0 = (int)(blockIdx.x / (unsigned)ntn) * kGemmBM;
     const uint32_t base = (smem_u32(gsm) + 1023u) & ~1023u;
-    const uint32_t sA[2] = {base, base + kATile + kBTile};
-    const uint32_t sB[2] = {base + kATile, base + 2 * kATile + kBTile};
     if (tid == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&s_full[s], 1);
+            mbar_init(&s_empty[s], 1);
+        }
         mbar_init(&s_done, 1);
         s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tc_alloc(&s_tmem, kCols);
+    if (warp == 0) tc_alloc(&s_tmem, Cfg::kCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t idesc = idesc_bf16_f32(kGemmBM, BN);
     const int nk = a.K / kGemmBK;
-    const int mvalid = min(kGemmBM, a.M - m0);
-    uint32_t issued[2] = {0, 0};  // MMA batches committed per stage (phase tracking)
-    // prologue: stage 0
-    stage_tile(sA[0], a.A + (size_t)m0 * a.K, a.K, 0, kGemmBM, mvalid, tid, 128);
-    stage_tile(sB[0], a.B + (size_t)n0 * a.K, a.K, 0, BN, BN, tid, 128);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    for (int kc = 0; kc < nk; ++kc) {
-        const int st = kc & 1;
-        // prefetch the next chunk into the other stage once its previous MMAs are done
-        if (kc + 1 < nk) {
-            const int nx = st ^ 1;
-            if (issued[nx]) {
-                if (!mbar_wait(&s_bar[nx], (issued[nx] - 1) & 1)) {
-                    if (tid == 0) s_fail = 1;
-                }
+    if (warp == 0 && lane == 0) {
+        // producer: keep up to S stages of operands in flight
+        int kc = 0;
+        for (; kc < nk; ++kc) {
+            const int s = kc % S, r = kc / S;
+            if (kc >= S && !mbar_wait(&s_empty[s], (uint32_t)(r - 1) & 1u)) {
+                *fail = 1;
+                break;
             }
-            stage_tile(sA[nx], a.A + (size_t)m0 * a.K, a.K, (kc + 1) * kGemmBK, kGemmBM, mvalid, tid, 128);
-            stage_tile(sB[nx], a.B + (size_t)n0 * a.K, a.K, (kc + 1) * kGemmBK, BN, BN, tid, 128);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (*fail) break;
+            const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
+            mbar_expect_tx(&s_full[s], Cfg::kStage);
+            tma_load_2d(sa, &tA, kc * kGemmBK, m0, &s_full[s]);
+            tma_load_2d(sa + Cfg::kA, &tB, kc * kGemmBK, n0, &s_full[s]);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (s_fail) break;
-        if (tid == 0) {
+        s_issued = kc;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: one stage = four K = 16 MMAs, then free the stage
+        const uint32_t idesc = idesc_bf16_f32(kGemmBM, BN);
+        int kc = 0;
+        for (; kc < nk; ++kc) {
+            const int s = kc % S, r = kc / S;
+            if (!mbar_wait(&s_full[s], (uint32_t)r & 1u)) {
+                *fail = 1;
+                break;
+            }
             tc_fence_after();
+            const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
 #pragma unroll
             for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(sA[st] + kk * 32);
-                const uint64_t bd = smem_desc_sw128(sB[st] + kk * 32);
+                const uint64_t ad = smem_desc_sw128(sa + (uint32_t)kk * 32u);
+                const uint64_t bd = smem_desc_sw128(sa + Cfg::kA + (uint32_t)kk * 32u);
                 tc_mma(tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
             }
-            tc_commit(&s_bar[st]);
+            tc_commit(&s_empty[s]);
         }
-        issued[st]++;
+        s_consumed = kc;
+        tc_commit(&s_done);  // arrives when every MMA issued above has completed
     }
-    // all MMAs done -> accumulators readable
-    if (tid == 0) tc_commit(&s_done);
     __syncthreads();
-    const bool ok = mbar_wait(&s_done, 0) && !s_fail;
+    // one verdict for the whole CTA: the epilogue's tcgen05.ld needs whole warps
+    const bool ok = __syncthreads_and(mbar_wait(&s_done, 0) && !*fail) != 0;
     tc_fence_after();
     if (!ok) {
-        if (tid == 0 && a.flags) atomicCAS(a.flags, 0, -4);  // DVC_E_TIMEOUT
+        if (tid == 0) {
+            // let the copies still in flight land before the CTA exits
+            for (int kc = s_consumed; kc < s_issued; ++kc) mbar_wait(&s_full[kc % S], (uint32_t)(kc / S) & 1u);
+            mbar_wait(&s_done, 0);
+            if (a.flags) atomicCAS(a.flags, 0, -4);  // DVC_E_TIMEOUT
+        }
     } else {
         const int row = m0 + warp * 32 + lane;
         const bool live = row < a.M;
@@ -250,10 +266,8 @@ __global__ void __launch_bounds__(128) gemm_bf16_tc_kernel(GemmArgs a) {
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tc_dealloc(tmem, kCols);
+        tc_dealloc(tmem, Cfg::kCols);
     }
 }
-
-__host__ __device__ inline uint32_t gemm_smem_bytes(int BN) { return 2u * (16384u + (uint32_t)BN * 128u) + 1024u; }
 
 }  // namespace dvc

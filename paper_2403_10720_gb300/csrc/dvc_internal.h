@@ -14,6 +14,24 @@ void dvc_value_free(dvc_ctx* c);
 // value network, enqueued on st; no argument checks (library-internal).
 int dvc_value_forward_probs(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_probs, cudaStream_t st);
 
+// Value-network activations owned by one caller (a forest's value-mode
+// pipeline), so that a captured graph never points into the context's own
+// workspace, which other calls may reallocate.  rows: a multiple of 128.
+struct dvc_value_rows {
+    void *X, *H1, *H2, *H3;  // BF16: rows x 640, rows x 512 (three)
+    float* L;                // rows x 16 logits
+    int rows;
+};
+int dvc_value_rows_alloc(dvc_ctx* c, dvc_value_rows* r, int rows);
+void dvc_value_rows_free(dvc_value_rows* r);
+// Set the network kernels' launch attributes; call before capturing a graph.
+int dvc_value_prepare(dvc_ctx* c);
+// Win probabilities of n leaves into d_probs, with the activations in rows
+// [row0, row0 + n rounded up to 128) of r.  Enqueues kernels only: no
+// allocation, no synchronisation, so it may be captured into a graph.
+int dvc_value_forward_rows(dvc_ctx* c, const dvc_state* d_leaves, int n, dvc_value_rows* r, int row0, float* d_probs,
+                           cudaStream_t st);
+
 struct dvc_ctx {
     dvc_config cfg;
     int device;

@@ -73,6 +73,8 @@ struct dvc_forest {
     cudaStream_t chain_stream[7];  // chains 2.. of the pipeline graph (chain 1 runs on cap_stream)
     cudaEvent_t fork_ev, join_ev[7];
     cudaGraphExec_t chunk_exec;  // pipeline graph of kChunkIters iterations (captured on first use)
+    cudaGraphExec_t value_exec;  // the same for value mode
+    dvc_value_rows vrows;        // value mode: network activations, one slice per chain
     int chains;               // independent chains in the pipeline graph (1..8)
     float* probs;             // value mode: win probabilities per tree
     int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
@@ -682,6 +684,8 @@ void dvc_forest_destroy(dvc_forest* f) {
     if (!f) return;
     cudaSetDevice(f->ctx->device);
     if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
+    if (f->value_exec) cudaGraphExecDestroy(f->value_exec);
+    dvc_value_rows_free(&f->vrows);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (int k = 0; k < 7; ++k) {
         if (f->chain_stream[k]) cudaStreamDestroy(f->chain_stream[k]);
@@ -692,7 +696,7 @@ void dvc_forest_destroy(dvc_forest* f) {
                     f->created,   f->work,      f->paths,     f->movers,         f->leaves,        f->leaf_tree,
                     f->leaf_iter, f->d_words,   f->export_scratch, f->order,     f->ucb,           f->csl,
                     f->pipe.leaf, f->pipe.path, f->pipe.mover, f->pipe.np,       f->pipe.wins,     f->pipe.step_end,
-                    f->pipe.det,  f->pipe.det_base, f->probs};
+                    f->pipe.det,  f->pipe.tree0, f->pipe.det_base, f->probs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -793,6 +797,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         alloc((void**)&f->pipe.mover, (size_t)kPathMax * n) && alloc((void**)&f->pipe.np, sizeof(int32_t) * n) &&
         alloc((void**)&f->pipe.wins, sizeof(int32_t) * 4 * n) && alloc((void**)&f->pipe.step_end, sizeof(int32_t) * n) &&
         alloc((void**)&f->pipe.det, sizeof(dvc_state) * kDetAhead * (size_t)n) &&
+        alloc((void**)&f->pipe.tree0, sizeof(uint4) * kDetAhead * (size_t)n) &&
         alloc((void**)&f->pipe.det_base, sizeof(int32_t) * n);
     if (!ok) {
         dvc_forest_destroy(f);
@@ -925,12 +930,13 @@ void chain_range(const dvc_forest* f, int k, int chains, int& b0, int& b1) {
     b1 = (int)((long long)grid * (k + 1) / chains);
 }
 
-// Capture kChunkIters iterations: the forest's CTAs split into independent
-// chains on their own streams, so one chain's tree walks overlap another's
-// playouts on the same SMs.
-int capture_chunk(dvc_forest* f) {
+// Capture kChunkIters iterations into *exec: `chains` independent chains on
+// their own streams (forked from and joined to the capture stream), so one
+// chain's tree walks overlap another chain's leaf scoring on the same SMs.
+// begin(k, stream) runs once per chain, then step(k, stream) per iteration.
+template <class Begin, class Step>
+int capture_chains(dvc_forest* f, int chains, cudaGraphExec_t* exec, Begin begin, Step step) {
     dvc_ctx* c = f->ctx;
-    const int chains = std::max(1, std::min(kMaxChains, f->chains));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "pipeline capture");
@@ -942,17 +948,9 @@ int capture_chunk(dvc_forest* f) {
         for (int k = 1; k < chains && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ss[k], f->fork_ev, 0);
         if (e != cudaSuccess) rc = cuda_fail(c, e, "pipeline fork");
     }
-    for (int k = 0; k < chains && rc == DVC_OK; ++k) {
-        int b0, b1;
-        chain_range(f, k, chains, b0, b1);
-        rc = enqueue_pipe_det(f, b0, b1, kChunkIters, ss[k]);
-    }
+    for (int k = 0; k < chains && rc == DVC_OK; ++k) rc = begin(k, ss[k]);
     for (int it = 0; it < kChunkIters && rc == DVC_OK; ++it)
-        for (int k = 0; k < chains && rc == DVC_OK; ++k) {
-            int b0, b1;
-            chain_range(f, k, chains, b0, b1);
-            rc = enqueue_pipe_iteration(f, b0, b1, ss[k]);
-        }
+        for (int k = 0; k < chains && rc == DVC_OK; ++k) rc = step(k, ss[k]);
     if (rc == DVC_OK && chains > 1) {
         for (int k = 1; k < chains && e == cudaSuccess; ++k) {
             e = cudaEventRecord(f->join_ev[k - 1], ss[k]);
@@ -966,13 +964,30 @@ int capture_chunk(dvc_forest* f) {
         return rc;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "pipeline capture end");
-    e = cudaGraphInstantiate(&f->chunk_exec, g, 0);
+    e = cudaGraphInstantiate(exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        f->chunk_exec = nullptr;
+        *exec = nullptr;
         return cuda_fail(c, e, "pipeline graph");
     }
     return DVC_OK;
+}
+
+// Rollout mode: the forest's rollout CTAs split into chains.
+int capture_chunk(dvc_forest* f) {
+    const int chains = std::max(1, std::min(kMaxChains, f->chains));
+    return capture_chains(
+        f, chains, &f->chunk_exec,
+        [&](int k, cudaStream_t s) {
+            int b0, b1;
+            chain_range(f, k, chains, b0, b1);
+            return enqueue_pipe_det(f, b0, b1, kChunkIters, s);
+        },
+        [&](int k, cudaStream_t s) {
+            int b0, b1;
+            chain_range(f, k, chains, b0, b1);
+            return enqueue_pipe_iteration(f, b0, b1, s);
+        });
 }
 
 int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
@@ -1011,7 +1026,48 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     return check_launch(c, "pipe_backprop_kernel");
 }
 
-// Value mode: select over all trees, the value network over every leaf, credit.
+// Value mode.  Trees t0 .. t1-1 of chain k (index order; each chain's leaves
+// are contiguous so the network reads them in place) and the first row of the
+// chain's activation slice.
+void value_chain(const dvc_forest* f, int k, int chains, int& t0, int& t1, int& row0) {
+    row0 = 0;
+    for (int j = 0; j <= k; ++j) {
+        t0 = (int)((long long)f->n * j / chains);
+        t1 = (int)((long long)f->n * (j + 1) / chains);
+        if (j < k) row0 += (t1 - t0 + 127) / 128 * 128;
+    }
+}
+
+int value_chains(const dvc_forest* f) { return std::max(1, std::min({kMaxChains, f->chains, f->n / 128})); }
+
+// One value-mode iteration of chain k: (pending backprop +) select, the
+// network over the chain's leaves, credit.
+int enqueue_value_iteration(dvc_forest* f, int k, int chains, cudaStream_t st) {
+    dvc_ctx* c = f->ctx;
+    int t0, t1, row0;
+    value_chain(f, k, chains, t0, t1, row0);
+    if (t1 <= t0) return DVC_OK;
+    pipe_select_kernel<<<((t1 - t0) * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), t0, t1, nullptr,
+                                                                      f->pipe);
+    if (int rc = check_launch(c, "pipe_select_kernel")) return rc;
+    if (int rc = dvc_value_forward_rows(c, f->pipe.leaf + t0, t1 - t0, &f->vrows, row0, f->probs + 4 * (size_t)t0, st))
+        return rc;
+    pipe_value_wins_kernel<<<(t1 - t0 + 127) / 128, 128, 0, st>>>(t0, t1, f->pipe, f->probs, f->ctx->cfg.playouts);
+    return check_launch(c, "pipe_value_wins_kernel");
+}
+
+int enqueue_value_det(dvc_forest* f, int k, int chains, int count, cudaStream_t st) {
+    int t0, t1, row0;
+    value_chain(f, k, chains, t0, t1, row0);
+    if (t1 <= t0 || count <= 0) return DVC_OK;
+    const long long threads = (long long)(t1 - t0) * count;
+    pipe_det_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(dev_of(f), params_of(f), t0, t1, nullptr,
+                                                                       f->pipe, count);
+    return check_launch(f->ctx, "pipe_det_kernel");
+}
+
+// Value mode: the same chained, graph-captured pipeline as rollout mode, the
+// rollout launch replaced by the network over each chain's leaves.
 int launch_value_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     dvc_ctx* c = f->ctx;
     if (!f->probs) {
@@ -1021,20 +1077,40 @@ int launch_value_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
             return fail(c, DVC_E_OOM, "dvc_mcts_step: value buffer");
         }
     }
-    const ForestDev fd = dev_of(f);
-    const SearchParams sp = params_of(f);
-    const int n = f->n;
-    if (int rc = clear_pipe_det(f, st)) return rc;
-    pipe_begin_kernel<<<(n + 127) / 128, 128, 0, st>>>(fd, n, n_iterations, f->pipe.step_end);
-    if (int rc = check_launch(c, "pipe_begin_kernel")) return rc;
-    for (int it = 0; it < n_iterations; ++it) {
-        pipe_select_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(fd, sp, 0, n, f->order, f->pipe);
-        if (int rc = check_launch(c, "pipe_select_kernel")) return rc;
-        if (int rc = dvc_value_forward_probs(c, f->pipe.leaf, n, f->probs, st)) return rc;
-        pipe_value_wins_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, f->pipe, f->probs, sp.playouts);
-        if (int rc = check_launch(c, "pipe_value_wins_kernel")) return rc;
+    const int chains = value_chains(f);
+    int t0, t1, rows;
+    value_chain(f, chains - 1, chains, t0, t1, rows);
+    rows += (t1 - t0 + 127) / 128 * 128;
+    if (f->vrows.rows < rows) {
+        if (f->value_exec) cudaGraphExecDestroy(f->value_exec);
+        f->value_exec = nullptr;
+        if (int rc = dvc_value_rows_alloc(c, &f->vrows, rows)) return rc;
     }
-    pipe_backprop_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(fd, sp, n, f->pipe);
+    if (int rc = dvc_value_prepare(c)) return rc;
+    if (int rc = clear_pipe_det(f, st)) return rc;
+    pipe_begin_kernel<<<(f->n + 127) / 128, 128, 0, st>>>(dev_of(f), f->n, n_iterations, f->pipe.step_end);
+    if (int rc = check_launch(c, "pipe_begin_kernel")) return rc;
+    int left = n_iterations;
+    if (left >= kChunkIters) {
+        if (!f->value_exec) {
+            const int rc = capture_chains(
+                f, chains, &f->value_exec,
+                [&](int k, cudaStream_t s) { return enqueue_value_det(f, k, chains, kChunkIters, s); },
+                [&](int k, cudaStream_t s) { return enqueue_value_iteration(f, k, chains, s); });
+            if (rc) return rc;
+        }
+        while (left >= kChunkIters) {
+            const cudaError_t e = cudaGraphLaunch(f->value_exec, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "value pipeline graph launch");
+            left -= kChunkIters;
+        }
+    }
+    for (int k = 0; k < chains; ++k)
+        if (int rc = enqueue_value_det(f, k, chains, left, st)) return rc;
+    for (; left > 0; --left)
+        for (int k = 0; k < chains; ++k)
+            if (int rc = enqueue_value_iteration(f, k, chains, st)) return rc;
+    pipe_backprop_kernel<<<(f->n * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), f->n, f->pipe);
     return check_launch(c, "pipe_backprop_kernel");
 }
 
@@ -1107,9 +1183,10 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     f->engine = eng;
     const int ch = chains ? chains : dC;
     if (W != oldW || T != oldT || ch != oldC) {
-        // the captured pipeline graph holds the old launch shape
+        // the captured pipeline graphs hold the old launch shape
         if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
-        f->chunk_exec = nullptr;
+        if (f->value_exec) cudaGraphExecDestroy(f->value_exec);
+        f->chunk_exec = f->value_exec = nullptr;
     }
     f->warps_per_cta = W;
     f->chains = ch;
@@ -1301,7 +1378,7 @@ int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_s
     const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 48;
     const size_t table = (size_t)(c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells) * 8;
     const size_t per_slot = arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) +
-                            sizeof(dvc_state) * kDetAhead + 256;
+                            (sizeof(dvc_state) + sizeof(uint4)) * kDetAhead + 256;
     const long long total = (long long)(hbm_budget / per_slot);
     const long long nv = c->vnet ? total * value_share_pct / 100 : 0;
     const long long nr = total - nv;

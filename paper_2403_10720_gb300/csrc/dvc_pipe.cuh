@@ -25,6 +25,7 @@ struct PipeBufs {
     int32_t* wins;      // per tree, 4 seats
     int32_t* step_end;  // per tree: iteration at which this step stops
     dvc_state* det;     // per tree, kDetAhead determinized roots: iterations det_base .. det_base + kDetAhead - 1
+    uint4* tree0;       // per tree, kDetAhead first blocks of the iterations' tree streams (tag 3)
     int32_t* det_base;  // per tree; far below zero (bytes 0xC0) when nothing is sampled ahead
 };
 
@@ -56,13 +57,14 @@ __device__ __forceinline__ void pipe_apply_pending(ForestDev& F, const SearchPar
 // A determinization depends only on the root view, the seed, the tree id and
 // the iteration (stream tag 2), not on the tree's statistics, so the next
 // `count` of them are sampled up front, one thread per (tree, iteration),
-// instead of on the tree walk's critical path.  Trees order[i0 .. i1-1].
+// instead of on the tree walk's critical path.  Trees order[i0 .. i1-1]
+// (trees i0 .. i1-1 if order is null).
 __global__ void __launch_bounds__(128)
     pipe_det_kernel(ForestDev F, SearchParams sp, int i0, int i1, const int32_t* order, PipeBufs P, int count) {
     const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const int i = i0 + g / count, k = g % count;
     if (i >= i1) return;
-    const int t = order[i];
+    const int t = order ? order[i] : i;
     const TreeMeta& tm = F.meta[t];
     // the tree's next select first applies its pending backprop (done + 1)
     const int32_t base = tm.done + (P.np[t] >= 0 ? 1 : 0);
@@ -76,17 +78,20 @@ __global__ void __launch_bounds__(128)
     dvc_state s;
     store_state(det, s);
     P.det[(size_t)t * kDetAhead + k] = s;
+    Rng tr;  // the iteration's in-tree draws start from this block
+    tr.open(sp.seed, tm.tree_id, 0u, (uint32_t)(base + k), kTagTree);
+    P.tree0[(size_t)t * kDetAhead + k] = tr.block0();
 }
 
 // Finish the previous iteration of tree t (backprop) and run its next
 // selection and expansion.
-// Trees order[i0 .. i1-1], one warp each.
+// Trees order[i0 .. i1-1] (trees i0 .. i1-1 if order is null), one warp each.
 __global__ void __launch_bounds__(128)
     pipe_select_kernel(ForestDev F, SearchParams sp, int i0, int i1, const int32_t* order, PipeBufs P) {
     __shared__ uint32_t s_E[4][104];
     const int i = i0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (i >= i1) return;
-    const int t = order[i];
+    const int t = order ? order[i] : i;
     const uint32_t lane = threadIdx.x & 31u, wl = (threadIdx.x >> 5) & 3u;
     pipe_apply_pending(F, sp, t, P);
     TreeMeta& tmr = F.meta[t];
@@ -101,8 +106,10 @@ __global__ void __launch_bounds__(128)
     const G root = load_state(F.roots[t]);
     G det;
     const uint32_t ahead = it - (uint32_t)P.det_base[t];
+    const uint4* tree0 = nullptr;
     if (ahead < (uint32_t)kDetAhead) {
         det = load_state(P.det[(size_t)t * kDetAhead + ahead]);
+        tree0 = P.tree0 + (size_t)t * kDetAhead + ahead;
     } else {
         Rng dr;
         dr.open(sp.seed, tm.tree_id, 0u, it, kTagDet);
@@ -112,7 +119,7 @@ __global__ void __launch_bounds__(128)
     int32_t* path = P.path + (size_t)t * kPathMax;
     uint8_t* mover = P.mover + (size_t)t * kPathMax;
     descend(det, root.cur, nodes, link, F.ucb + tm.node_off, F.csl + tm.node_off, tm, sp, it, path, mover, s_E[wl],
-            d);
+            d, tree0);
     bool ok = true;
     int32_t next_free = tm.next_free, used = tm.used;
     if (d.found) ok = expand_child(d, nodes, link, F.created + tm.node_off, tm, next_free, used, it, path, mover);
@@ -278,11 +285,12 @@ __global__ void __launch_bounds__(128) pipe_backprop_kernel(ForestDev F, SearchP
 }
 
 // Value mode: the network's win probabilities stand in for the playouts of
-// every fresh, unfinished leaf -- each seat is credited round(p * P) of the P
-// visits (a leaf that ended inside the tree keeps its exact credit).
-__global__ void pipe_value_wins_kernel(int n, PipeBufs P, const float* probs, int playouts) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+// every fresh, unfinished leaf of trees t0 .. t1-1 -- each seat is credited
+// round(p * P) of the P visits (a leaf that ended inside the tree keeps its
+// exact credit).
+__global__ void pipe_value_wins_kernel(int t0, int t1, PipeBufs P, const float* probs, int playouts) {
+    const int t = t0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (t >= t1) return;
     if (P.np[t] < 0 || P.leaf[t].winner != kNone) return;
     int32_t* w = P.wins + 4 * t;
     for (int s = 0; s < 4; ++s) w[s] = (int32_t)(probs[4 * t + s] * (float)playouts + 0.5f);

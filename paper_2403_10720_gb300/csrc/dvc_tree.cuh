@@ -73,13 +73,16 @@ struct Descent {
 // node's UCB1 terms, refreshed whenever its counts change (backprop), so a
 // selection scan costs one multiply-add per child.  They are the same IEEE
 // values a scan would compute from the counts.
+// tree0 (optional): the first block of the iteration's tree stream, computed
+// ahead of time (the same four words the stream would generate).
 __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* nodes, const int32_t* link,
                                         const double2* ucb, const double* csl_of, const TreeMeta& tm,
                                         const SearchParams& sp, uint32_t it, int32_t* path, uint8_t* mover,
-                                        uint32_t* E, Descent& d) {
+                                        uint32_t* E, Descent& d, const uint4* tree0 = nullptr) {
     const uint32_t lane = threadIdx.x & 31u;
     d.s = det;
     d.tr.open(sp.seed, tm.tree_id, 0u, it, kTagTree);
+    if (tree0) d.tr.preload(*tree0);
     d.node = 0;
     d.found = 0;
     d.np = 1;
@@ -89,13 +92,17 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
     }
     uint32_t depth = 0;
     while (d.s.winner == kNone && depth < (uint32_t)sp.d_max) {
+        // loads that do not depend on one another are issued together: the
+        // node and its exploration term; below, each child with its UCB1
+        // terms, and the next block's start before this block is scanned
         const Node nd = nodes[d.node];
+        const double csl_node = csl_of[d.node];  // any slot's entry exists; used only if it has children
         const uint32_t nchild = (nd.meta >> 12) & 0xFFFu;
         const uint32_t cur = d.s.cur;
         const uint32_t U = d.s.tmask & ~d.s.hand(cur) & ~d.s.rev;
         for (uint32_t e = lane; e < 104u; e += 32u) E[e] = 0u;
         __syncwarp();
-        const double csl = nchild ? csl_of[d.node] : 0.0;
+        const double csl = nchild ? csl_node : 0.0;
         double best_sc = -1.0;
         uint32_t best_rank = 0xFFFFFFFFu;
         int32_t best_slot = -1;
@@ -108,13 +115,14 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         while (seen < nchild) {
             const uint32_t size = block_size(k, d.node == 0, (uint32_t)tm.root_legal);
             const uint32_t cnt = min(size, nchild - seen);
+            const int32_t next_blk = seen + cnt < nchild ? link[blk] : -1;
             for (uint32_t e = lane; e < cnt; e += 32u) {
                 const Node ch = nodes[blk + (int32_t)e];
+                const double2 u = ucb[blk + (int32_t)e];  // set by the child's first backprop
                 const uint32_t code = ch.meta & 0xFFFu;
                 const uint32_t q = code >> 10, sl = (code >> 5) & 31u, x = code & 31u;
                 if (sl < 26u) atomicOr(&E[q * 26u + sl], 1u << x);
                 if (guess_legal(d.s, q, sl, x)) {
-                    const double2 u = ucb[blk + (int32_t)e];
                     const double sc = __dadd_rn(u.x, __dmul_rn(csl, u.y));
                     const uint32_t rk = canon_rank(code, cur, d.s.np);
                     if (best_slot < 0 || sc > best_sc || (sc == best_sc && rk < best_rank)) {
@@ -130,7 +138,7 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
             d.last_size = (int32_t)size;
             d.last_cnt = (int32_t)cnt;
             ++k;
-            if (seen < nchild) blk = link[blk];
+            if (seen < nchild) blk = next_blk;
         }
         d.nblocks = (int32_t)k;
         d.nchild = (int32_t)nchild;

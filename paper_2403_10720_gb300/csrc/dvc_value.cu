@@ -10,6 +10,7 @@
 // tensor memory (tcgen05), FP32 master weights and AdamW moments.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdio>
 #include <cstring>
@@ -302,12 +303,54 @@ __global__ void init_params_kernel(float* w, uint64_t seed) {
 // ------------------------------------------------------------------ host helpers
 
 template <int BN>
+cudaError_t gemm_attributes() {
+    return cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)GemmCfg<BN>::kSmem);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so the
+// library needs no link against the driver library.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
+
+// A row-major rows x K BF16 matrix as the 2-D tensor (K, rows) read in boxes
+// of 64 x box_rows with the 128-byte swizzle; rows past the end read as zero.
+bool encode_kmajor(CUtensorMap* m, const __nv_bfloat16* p, int rows, int K, int box_rows) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2u};
+    const cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
 cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
-    const uint32_t smem = gemm_smem_bytes(BN);
-    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // inside a stream capture the attributes were set beforehand (dvc_value_prepare)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) e = gemm_attributes<BN>();
     if (e != cudaSuccess) return e;
-    dim3 grid((a.M + kGemmBM - 1) / kGemmBM, a.N / BN);
-    gemm_bf16_tc_kernel<BN><<<grid, 128, smem, st>>>(a);
+    CUtensorMap tA, tB;
+    if (!encode_kmajor(&tA, a.A, a.M, a.K, kGemmBM) || !encode_kmajor(&tB, a.B, a.N, a.K, BN))
+        return cudaErrorInvalidValue;
+    const long long tiles = (long long)((a.M + kGemmBM - 1) / kGemmBM) * (a.N / BN);
+    gemm_bf16_tc_kernel<BN><<<(unsigned)tiles, 128, GemmCfg<BN>::kSmem, st>>>(tA, tB, a);
     return cudaGetLastError();
 }
 
@@ -390,17 +433,26 @@ int need_net(dvc_ctx* c) {
 
 // Forward pass for n rows (npad = n rounded up to 128).  With train = true,
 // keeps pre-activations and transposed activations for the backward pass.
-int forward(dvc_ctx* c, const dvc_state* states, int n, int npad, bool train, cudaStream_t st) {
+// Features and the four layers of npad rows (n live) into the given
+// activation buffers; Z1..Z3 (pre-activation FP32, training) may be null.
+int forward_into(dvc_ctx* c, const dvc_state* states, int n, int npad, __nv_bfloat16* X, __nv_bfloat16* H1,
+                 __nv_bfloat16* H2, __nv_bfloat16* H3, float* L, float* Z1, float* Z2, float* Z3, cudaStream_t st) {
     dvc_value_net* v = c->vnet;
     int32_t* fl = c->d_flags;
-    features_kernel<<<(npad * 32 + 255) / 256, 256, 0, st>>>(states, n, npad, v->X, nullptr);
+    features_kernel<<<(npad * 32 + 255) / 256, 256, 0, st>>>(states, n, npad, X, nullptr);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = gemm(v->X, v->W1, v->master + OFF_B1, v->H1, train ? v->Z1 : nullptr, npad, VH, VF, kActGelu, fl, st);
-    if (e == cudaSuccess) e = gemm(v->H1, v->W2, v->master + OFF_B2, v->H2, train ? v->Z2 : nullptr, npad, VH, VH, kActGelu, fl, st);
-    if (e == cudaSuccess) e = gemm(v->H2, v->W3, v->master + OFF_B3, v->H3, train ? v->Z3 : nullptr, npad, VH, VH, kActGelu, fl, st);
-    if (e == cudaSuccess) e = gemm(v->H3, v->W4, v->b4p, nullptr, v->L, npad, VO, VH, kActNone, fl, st);
+    if (e == cudaSuccess) e = gemm(X, v->W1, v->master + OFF_B1, H1, Z1, npad, VH, VF, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(H1, v->W2, v->master + OFF_B2, H2, Z2, npad, VH, VH, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(H2, v->W3, v->master + OFF_B3, H3, Z3, npad, VH, VH, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(H3, v->W4, v->b4p, nullptr, L, npad, VO, VH, kActNone, fl, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "value forward");
     return DVC_OK;
+}
+
+int forward(dvc_ctx* c, const dvc_state* states, int n, int npad, bool train, cudaStream_t st) {
+    dvc_value_net* v = c->vnet;
+    return forward_into(c, states, n, npad, v->X, v->H1, v->H2, v->H3, v->L, train ? v->Z1 : nullptr,
+                        train ? v->Z2 : nullptr, train ? v->Z3 : nullptr, st);
 }
 
 int transpose(dvc_ctx* c, const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C, cudaStream_t st) {
@@ -628,6 +680,53 @@ int dvc_value_forward_probs(dvc_ctx* c, const dvc_state* d_leaves, int n, float*
     if (int rc = ensure_work(c, npad)) return rc;
     if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
     softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, d_leaves, n, d_probs);
+    return check_launch(c, "softmax_out_kernel");
+}
+
+int dvc_value_rows_alloc(dvc_ctx* c, dvc_value_rows* r, int rows) {
+    dvc_value_rows_free(r);
+    const size_t n = (size_t)rows;
+    const bool ok = cudaMalloc(&r->X, n * VF * 2) == cudaSuccess && cudaMalloc(&r->H1, n * VH * 2) == cudaSuccess &&
+                    cudaMalloc(&r->H2, n * VH * 2) == cudaSuccess && cudaMalloc(&r->H3, n * VH * 2) == cudaSuccess &&
+                    cudaMalloc(&r->L, n * VO * 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        dvc_value_rows_free(r);
+        return fail(c, DVC_E_OOM, "value network: activation rows");
+    }
+    r->rows = rows;
+    return DVC_OK;
+}
+
+void dvc_value_rows_free(dvc_value_rows* r) {
+    void* ptrs[] = {r->X, r->H1, r->H2, r->H3, r->L};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    *r = dvc_value_rows{};
+}
+
+int dvc_value_prepare(dvc_ctx* c) {
+    if (int rc = need_net(c)) return rc;
+    cudaError_t e = gemm_attributes<256>();
+    if (e == cudaSuccess) e = gemm_attributes<128>();
+    if (e == cudaSuccess) e = gemm_attributes<64>();
+    if (e == cudaSuccess) e = gemm_attributes<32>();
+    if (e == cudaSuccess) e = gemm_attributes<16>();
+    return e == cudaSuccess ? DVC_OK : cuda_fail(c, e, "value network attributes");
+}
+
+int dvc_value_forward_rows(dvc_ctx* c, const dvc_state* d_leaves, int n, dvc_value_rows* r, int row0, float* d_probs,
+                           cudaStream_t st) {
+    if (n <= 0) return DVC_OK;
+    const int npad = (n + 127) / 128 * 128;
+    if (row0 < 0 || row0 + npad > r->rows) return fail(c, DVC_E_INVALID, "value network: activation rows");
+    const size_t o = (size_t)row0;
+    float* L = r->L + o * VO;
+    if (int rc = forward_into(c, d_leaves, n, npad, (__nv_bfloat16*)r->X + o * VF, (__nv_bfloat16*)r->H1 + o * VH,
+                              (__nv_bfloat16*)r->H2 + o * VH, (__nv_bfloat16*)r->H3 + o * VH, L, nullptr, nullptr,
+                              nullptr, st))
+        return rc;
+    softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(L, d_leaves, n, d_probs);
     return check_launch(c, "softmax_out_kernel");
 }
 

@@ -162,6 +162,29 @@ def test_value_mode_search(dvc):
         assert 0 <= w <= vis and vis % 64 == 0
 
 
+def test_value_mode_chains_agree(dvc):
+    """The chained, graph-captured value pipeline gives the same trees for
+    1, 3 and 8 chains, across a captured 64-iteration chunk and a tail."""
+    kw = dict(VARIANTS["2p24"], playouts=16)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(13)
+    n, budget = 1100, 100
+    roots = ctx.dvc_init_states(27, n)
+    out = []
+    for chains in (1, 3, 8):
+        f = dvc.Forest(ctx, roots, [budget] * n, 5)
+        f.dvc_forest_tune(0, 0, 0, chains)
+        f.dvc_mcts_step(70, dvc.DVC_MODE_VALUE)
+        f.dvc_mcts_step(30, dvc.DVC_MODE_VALUE)
+        out.append((f.dvc_root_stats().cpu(), [f.dvc_tree_export(t).cpu() for t in (0, 549, 1099)]))
+        f.close()
+    ctx.dvc_check()
+    for stats, trees in out[1:]:
+        assert torch.equal(stats, out[0][0])
+        assert all(torch.equal(a, b) for a, b in zip(trees, out[0][1]))
+    assert (out[0][0][:, 6] == budget).all()
+
+
 def test_trained_network_gains_over_playouts(dvc):
     """After training on 131,072 states labelled by 1,024 playouts each, the
     network's win probabilities on held-out states are closer to the labels
