@@ -226,7 +226,7 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
  * leaves' playouts).  engine 2: per iteration two launches (backprop of the
  * previous iteration + select, then pooled rollouts) in a CUDA graph of 64
  * iterations; rollout CTAs pool trees_per_cta trees with warps_per_cta warps,
- * and the CTAs are split into `chains` (1..8) independent chains on
+ * and the CTAs are split into `chains` (1..16) independent chains on
  * separate streams so that one chain's tree walks run beside another chain's
  * playouts.  The determinizations of the graph's 64 iterations are sampled
  * up front, one thread per tree and iteration.  engine 0 keeps the current

@@ -1,17 +1,17 @@
 // dvc_gemm.cuh -- BF16 GEMM on the 5th-generation tensor cores (tcgen05) of
 // sm_103a, for the value network's dense layers:
 //     C[m, n] = act(sum_k A[m, k] * B[n, k] + bias[n])      (A, B K-major BF16)
-// One CTA computes a 128 x BN tile with FP32 accumulators in tensor memory.
-// Operand tiles of 64 K-elements arrive by TMA (cp.async.bulk.tensor) in the
-// 128-byte swizzled K-major layout into a ring of S stages guarded by
-// full/empty mbarriers: one producer thread keeps up to S tiles in flight,
-// one MMA thread issues tcgen05.mma (K = 16 each) as tiles land and commits
-// each stage back to the producer; then four warps read the accumulators with
-// tcgen05.ld for the epilogue.  Tiles are numbered with N fastest so the CTAs
-// that share an A tile run together and read it once from HBM.
-// Every wait on an mbarrier is bounded: on time-out the kernel records an
-// error, waits (bounded) for its own copies and MMAs, frees its tensor memory
-// and exits.
+// A persistent, warp-specialised kernel: one CTA per SM walks its 128 x BN
+// output tiles (N tile fastest, so CTAs working at the same time share A
+// tiles in L2).  Warp 0 streams 64-wide K slices of A and B by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) into a ring of S stages guarded by
+// full/empty mbarriers; warp 1 issues tcgen05.mma (K = 16 each, FP32
+// accumulators in tensor memory) as slices land and frees each stage by
+// tcgen05.commit; the accumulators are double-buffered in tensor memory, so
+// warps 4-11 drain tile i (tcgen05.ld, bias, activation, 16-byte stores)
+// while the tensor cores compute tile i + 1.  Every wait on an mbarrier is
+// bounded: on time-out the kernel records an error, waits (bounded) for its
+// own copies and MMAs, frees its tensor memory and exits.
 #pragma once
 #include <cuda.h>  // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
 #include <stdint.h>
@@ -110,6 +110,10 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -138,38 +142,47 @@ struct GemmArgs {
 };
 
 // Stage geometry for a BN-column tile: A 128 x 64 and B BN x 64 BF16 per
-// stage, as many stages as fit in 200 KB (at most 6).
+// stage, as many stages as fit in 192 KB (at most 6); two accumulator
+// buffers of max(BN, 32) tensor-memory columns.
 template <int BN>
 struct GemmCfg {
     static constexpr uint32_t kA = (uint32_t)kGemmBM * kGemmBK * 2;  // 16 KB
     static constexpr uint32_t kB = (uint32_t)BN * kGemmBK * 2;
     static constexpr uint32_t kStage = kA + kB;
-    static constexpr int kStages = (int)((200u * 1024u) / kStage) > 6 ? 6 : (int)((200u * 1024u) / kStage);
+    static constexpr int kStages = (int)((192u * 1024u) / kStage) > 6 ? 6 : (int)((192u * 1024u) / kStage);
     static constexpr uint32_t kSmem = (uint32_t)kStages * kStage + 1024u;  // + alignment slack
-    static constexpr uint32_t kCols = BN < 32 ? 32u : (uint32_t)BN;       // tensor-memory columns
+    static constexpr uint32_t kAccCols = BN < 32 ? 32u : (uint32_t)BN;
+    static constexpr uint32_t kCols = 2u * kAccCols;  // a power of two, >= 64
 };
 
-// BN in {16, 32, 64, 128, 256}; 128 threads; one tile per CTA, tile index
-// blockIdx.x with the N tile fastest.  tA: A as a (K, M) tensor, box (64,
-// 128); tB: B as (K, N), box (64, BN); both 128-byte swizzled.
+constexpr int kGemmThreads = 384;  // warp 0 TMA, warp 1 MMA, warps 2-3 idle, warps 4-11 epilogue
+
+// BN in {16, 32, 64, 128, 256}.  tA: A as a (K, M) tensor, box (64, 128);
+// tB: B as (K, N), box (64, BN); both 128-byte swizzled.  Grid: at most one
+// CTA per SM; CTA c takes tiles c, c + gridDim.x, ...
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, GemmArgs a) {
     using Cfg = GemmCfg<BN>;
     constexpr int S = Cfg::kStages;
     extern __shared__ __align__(1024) unsigned char gsm[];
-    __shared__ uint64_t s_full[S], s_empty[S], s_done;
+    __shared__ uint64_t s_full[S], s_empty[S], s_accf[2], s_acce[2], s_done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail, s_issued, s_consumed;
     volatile int* fail = &s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntn = a.N / BN;
-    const int n0 = (int)(blockIdx.x % (unsigned)ntn) * BN, m0 = (int)(blockIdx.x / (unsigned)ntn) * kGemmBM;
+    const int tiles = ((a.M + kGemmBM - 1) / kGemmBM) * ntn;
+    const int nk = a.K / kGemmBK;
     const uint32_t base = (smem_u32(gsm) + 1023u) & ~1023u;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&s_full[s], 1);
             mbar_init(&s_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&s_accf[b], 1);
+            mbar_init(&s_acce[b], 8);  // one arrival per epilogue warp
         }
         mbar_init(&s_done, 1);
         s_fail = 0;
@@ -182,85 +195,126 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int nk = a.K / kGemmBK;
-    if (warp == 0 && lane == 0) {
-        // producer: keep up to S stages of operands in flight
-        int kc = 0;
-        for (; kc < nk; ++kc) {
-            const int s = kc % S, r = kc / S;
-            if (kc >= S && !mbar_wait(&s_empty[s], (uint32_t)(r - 1) & 1u)) {
-                *fail = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: K slices of every tile of this CTA, up to S in flight
+            int it = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
+                const int m0 = (t / ntn) * kGemmBM, n0 = (t % ntn) * BN;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % S, r = it / S;
+                    if ((it >= S && !mbar_wait(&s_empty[s], (uint32_t)(r - 1) & 1u)) || *fail) {
+                        *fail = 1;
+                        stop = true;
+                        break;
+                    }
+                    const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
+                    mbar_expect_tx(&s_full[s], Cfg::kStage);
+                    tma_load_2d(sa, &tA, kc * kGemmBK, m0, &s_full[s]);
+                    tma_load_2d(sa + Cfg::kA, &tB, kc * kGemmBK, n0, &s_full[s]);
+                }
             }
-            if (*fail) break;
-            const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
-            mbar_expect_tx(&s_full[s], Cfg::kStage);
-            tma_load_2d(sa, &tA, kc * kGemmBK, m0, &s_full[s]);
-            tma_load_2d(sa + Cfg::kA, &tB, kc * kGemmBK, n0, &s_full[s]);
+            s_issued = it;
         }
-        s_issued = kc;
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: one stage = four K = 16 MMAs, then free the stage
-        const uint32_t idesc = idesc_bf16_f32(kGemmBM, BN);
-        int kc = 0;
-        for (; kc < nk; ++kc) {
-            const int s = kc % S, r = kc / S;
-            if (!mbar_wait(&s_full[s], (uint32_t)r & 1u)) {
-                *fail = 1;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile j accumulates into buffer j & 1 once the
+            // epilogue has drained that buffer's previous tile
+            const uint32_t idesc = idesc_bf16_f32(kGemmBM, BN);
+            int it = 0, j = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++j) {
+                const int b = j & 1, u = j >> 1;
+                if (u > 0 && !mbar_wait(&s_acce[b], (uint32_t)(u - 1) & 1u)) {
+                    *fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)b * Cfg::kAccCols;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % S, r = it / S;
+                    if (!mbar_wait(&s_full[s], (uint32_t)r & 1u) || *fail) {
+                        *fail = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
+#pragma unroll
+                    for (int kk = 0; kk < kGemmBK / 16; ++kk) {
+                        const uint64_t ad = smem_desc_sw128(sa + (uint32_t)kk * 32u);
+                        const uint64_t bd = smem_desc_sw128(sa + Cfg::kA + (uint32_t)kk * 32u);
+                        tc_mma(acc, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    tc_commit(&s_empty[s]);
+                }
+                if (!stop) tc_commit(&s_accf[b]);
+            }
+            s_consumed = it;
+            tc_commit(&s_done);  // arrives when every MMA issued above has completed
+        }
+    } else if (warp >= 4) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (one
+        // output row per thread) and half of the tile's columns
+        const int quarter = warp & 3, half = (warp - 4) >> 2;
+        const int cw = BN >= 32 ? BN / 2 : BN;
+        const int cbeg = BN >= 32 ? half * cw : (half ? BN : 0);
+        int j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const int b = j & 1, u = j >> 1;
+            const bool got = mbar_wait(&s_accf[b], (uint32_t)u & 1u);
+            if (!__all_sync(0xFFFFFFFFu, got) || *fail) {
+                if (lane == 0) *fail = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
-#pragma unroll
-            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(sa + (uint32_t)kk * 32u);
-                const uint64_t bd = smem_desc_sw128(sa + Cfg::kA + (uint32_t)kk * 32u);
-                tc_mma(tmem, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-            }
-            tc_commit(&s_empty[s]);
-        }
-        s_consumed = kc;
-        tc_commit(&s_done);  // arrives when every MMA issued above has completed
-    }
-    __syncthreads();
-    // one verdict for the whole CTA: the epilogue's tcgen05.ld needs whole warps
-    const bool ok = __syncthreads_and(mbar_wait(&s_done, 0) && !*fail) != 0;
-    tc_fence_after();
-    if (!ok) {
-        if (tid == 0) {
-            // let the copies still in flight land before the CTA exits
-            for (int kc = s_consumed; kc < s_issued; ++kc) mbar_wait(&s_full[kc % S], (uint32_t)(kc / S) & 1u);
-            mbar_wait(&s_done, 0);
-            if (a.flags) atomicCAS(a.flags, 0, -4);  // DVC_E_TIMEOUT
-        }
-    } else {
-        const int row = m0 + warp * 32 + lane;
-        const bool live = row < a.M;
+            const int m0 = (t / ntn) * kGemmBM, n0 = (t % ntn) * BN;
+            const int row = m0 + quarter * 32 + lane;
+            const bool live = row < a.M;
+            const uint32_t acc = tmem + (uint32_t)b * Cfg::kAccCols + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (live) {
+            for (int c0 = cbeg; c0 < cbeg + cw && c0 < BN; c0 += 16) {
+                float v[16];
+                tc_ld16(acc + (uint32_t)c0, v);
+                if (live) {
+                    const int nb = n0 + c0;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int n = n0 + c0 + i;
-                    float x = v[i] + (a.bias ? a.bias[n] : 0.0f);
-                    if (a.Cf) a.Cf[(size_t)row * a.N + n] = x;
-                    if (a.act == kActGelu) x = gelu_erf(x);
-                    v[i] = x;
-                }
-                if (a.C) {
-                    __nv_bfloat16* dst = a.C + (size_t)row * a.N + n0 + c0;
+                    for (int i = 0; i < 16; ++i) v[i] += a.bias ? __ldg(a.bias + nb + i) : 0.0f;
+                    if (a.Cf) {
+                        float4* f = reinterpret_cast<float4*>(a.Cf + (size_t)row * a.N + nb);
 #pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        __nv_bfloat162 p;
-                        p.x = __float2bfloat16_rn(v[i]);
-                        p.y = __float2bfloat16_rn(v[i + 1]);
-                        *reinterpret_cast<__nv_bfloat162*>(dst + i) = p;
+                        for (int i = 0; i < 4; ++i) f[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    }
+                    if (a.act == kActGelu) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = gelu_erf(v[i]);
+                    }
+                    if (a.C) {
+                        uint32_t w[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                            w[i] = *reinterpret_cast<uint32_t*>(&p);
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(a.C + (size_t)row * a.N + nb);
+                        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_acce[b]);
         }
+    }
+    __syncthreads();
+    // every MMA has completed before tensor memory is freed; on failure the
+    // copies still in flight land first
+    const bool ok = __syncthreads_and(mbar_wait(&s_done, 0) && !*fail) != 0;
+    if (!ok && tid == 0) {
+        for (int it = s_consumed; it < s_issued; ++it) mbar_wait(&s_full[it % S], (uint32_t)(it / S) & 1u);
+        if (a.flags) atomicCAS(a.flags, 0, -4);  // DVC_E_TIMEOUT
     }
     tc_fence_before();
     __syncthreads();

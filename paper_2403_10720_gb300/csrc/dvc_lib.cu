@@ -18,7 +18,7 @@ using namespace dvc;
 using namespace dvc_host;
 
 namespace {
-constexpr int kMaxChains = 8;  // independent chains of the pipeline graph
+constexpr int kMaxChains = 16;  // independent chains of the pipeline graph
 
 // Default launch shape of an engine for n trees on `sms` SMs.  Pipeline: many
 // small rollout CTAs (16 warps, about 1.5 CTAs per SM per chain) in up to 8
@@ -27,7 +27,7 @@ constexpr int kMaxChains = 8;  // independent chains of the pipeline graph
 void default_shape(int n, int sms, int engine, int& T, int& W, int& chains) {
     const int S = std::max(sms, 1);
     if (engine == 2) {
-        chains = std::max(1, std::min(kMaxChains, n / (2 * S)));
+        chains = std::max(1, std::min(8, n / (2 * S)));
         T = std::max(1, std::min(64, 2 * n / (3 * chains * S)));
         W = 16;
     } else {
@@ -70,12 +70,12 @@ struct dvc_forest {
     double* csl;
     PipeBufs pipe;
     cudaStream_t cap_stream;  // capture stream for the pipeline graph
-    cudaStream_t chain_stream[7];  // chains 2.. of the pipeline graph (chain 1 runs on cap_stream)
-    cudaEvent_t fork_ev, join_ev[7];
+    cudaStream_t chain_stream[kMaxChains - 1];  // chains 2.. of the pipeline graph (chain 1 runs on cap_stream)
+    cudaEvent_t fork_ev, join_ev[kMaxChains - 1];
     cudaGraphExec_t chunk_exec;  // pipeline graph of kChunkIters iterations (captured on first use)
     cudaGraphExec_t value_exec;  // the same for value mode
     dvc_value_rows vrows;        // value mode: network activations, one slice per chain
-    int chains;               // independent chains in the pipeline graph (1..8)
+    int chains;               // independent chains in the pipeline graph (1..16)
     float* probs;             // value mode: win probabilities per tree
     int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
 };
@@ -687,7 +687,7 @@ void dvc_forest_destroy(dvc_forest* f) {
     if (f->value_exec) cudaGraphExecDestroy(f->value_exec);
     dvc_value_rows_free(&f->vrows);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < kMaxChains - 1; ++k) {
         if (f->chain_stream[k]) cudaStreamDestroy(f->chain_stream[k]);
         if (f->join_ev[k]) cudaEventDestroy(f->join_ev[k]);
     }
@@ -821,7 +821,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     }
     bool sok = cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&f->fork_ev, cudaEventDisableTiming) == cudaSuccess;
-    for (int k = 0; k < 7 && sok; ++k)
+    for (int k = 0; k < kMaxChains - 1 && sok; ++k)
         sok = cudaStreamCreateWithFlags(&f->chain_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&f->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
     if (!sok) {
@@ -1136,7 +1136,7 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     if (engine < 0 || engine > 2 || trees_per_cta < 0 || trees_per_cta > 64 || warps_per_cta < 0 ||
         warps_per_cta > 32 || chains < 0 || chains > kMaxChains)
         return fail(f->ctx, DVC_E_INVALID,
-                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..8");
+                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..16");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->ctx->device);
     const int eng = engine ? engine : f->engine;

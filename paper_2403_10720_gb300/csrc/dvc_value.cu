@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -49,69 +50,87 @@ namespace {
 
 __device__ __forceinline__ uint32_t unknown_mask(const G& g) { return g.tmask & ~g.hand(g.cur) & ~g.rev; }
 
-// One warp per state: X[row] = features (BF16), zero-padded to 640.
-__global__ void features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X, float* Xf) {
+// One warp per state: X[row] = features (BF16), zero-padded to 640.  The
+// warp sets the row's 640 bits in shared memory, then writes the row with
+// 16-byte stores (8 BF16 or 4 FP32 values each).  Blocks of 256 threads.
+__global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X,
+                                                       float* Xf) {
+    __shared__ uint32_t s_bits[8][VF / 32];
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
     if (row >= npad) return;
-    __nv_bfloat16* x = X ? X + (size_t)row * VF : nullptr;
-    float* xf = Xf ? Xf + (size_t)row * VF : nullptr;
-    for (int i = lane; i < VF; i += 32) {
-        if (x) x[i] = __float2bfloat16_rn(0.0f);
-        if (xf) xf[i] = 0.0f;
+    uint32_t* bits = s_bits[w];
+    if (lane < VF / 32) bits[lane] = 0u;
+    __syncwarp();
+    if (row < n) {
+        const G g = load_state(states[row]);
+        auto set = [&](int i) { atomicOr(&bits[i >> 5], 1u << (i & 31)); };
+        const uint32_t held = g.h0 | g.h1 | g.h2 | g.h3;
+        if (lane < 26 && ((g.tmask >> lane) & 1u) && ((held >> lane) & 1u)) {
+            uint32_t owner = 0;
+            for (uint32_t p = 0; p < g.np; ++p)
+                if ((g.hand(p) >> lane) & 1u) owner = p;
+            const uint32_t rel = (owner + g.np - g.cur) % g.np;
+            set(7 * lane + (int)rel);
+            set(7 * lane + 4 + (int)((g.rev >> lane) & 1u));
+            if ((uint32_t)lane == g.drawn) set(7 * lane + 6);
+        }
+        const uint32_t U = unknown_mask(g);
+        for (int pair = lane; pair < 33; pair += 32) {
+            const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
+            if (k >= g.np) continue;
+            const uint32_t q = (g.cur + k) % g.np;
+            const uint32_t len = __popc(g.hand(q));
+            if (s >= len) continue;
+            const int base = 182 + (int)(((k - 1u) * 11u + s) * 13u);
+            const uint32_t t = seq_tile(g, q, s);
+            if ((g.rev >> t) & 1u) {
+                set(base + (t < 24u ? (int)(t >> 1) : 12));
+                continue;
+            }
+            int lo = -1, hi = 24;
+            for (int j = (int)s - 1; j >= 0; --j) {
+                const uint32_t u = seq_tile(g, q, (uint32_t)j);
+                if (((g.rev >> u) & 1u) && u < 24u) {
+                    lo = (int)u;
+                    break;
+                }
+            }
+            for (uint32_t j = s + 1; j < len; ++j) {
+                const uint32_t u = seq_tile(g, q, j);
+                if (((g.rev >> u) & 1u) && u < 24u) {
+                    hi = (int)u;
+                    break;
+                }
+            }
+            // unknown numbered tiles strictly between lo and hi
+            const uint32_t above = lo < 0 ? 0x00FFFFFFu : (0x00FFFFFFu & ~((2u << lo) - 1u));
+            const uint32_t below = (1u << hi) - 1u;
+            const uint32_t m = U & above & below;
+            for (int v = 0; v < 12; ++v)
+                if ((m >> (2 * v)) & 3u) set(base + v);
+            if (U & kJokerMask) set(base + 12);
+        }
     }
     __syncwarp();
-    if (row >= n) return;
-    const G g = load_state(states[row]);
-    auto set = [&](int i) {
-        if (x) x[i] = __float2bfloat16_rn(1.0f);
-        if (xf) xf[i] = 1.0f;
-    };
-    const uint32_t held = g.h0 | g.h1 | g.h2 | g.h3;
-    if (lane < 26 && ((g.tmask >> lane) & 1u) && ((held >> lane) & 1u)) {
-        uint32_t owner = 0;
-        for (uint32_t p = 0; p < g.np; ++p)
-            if ((g.hand(p) >> lane) & 1u) owner = p;
-        const uint32_t rel = (owner + g.np - g.cur) % g.np;
-        set(7 * lane + (int)rel);
-        set(7 * lane + 4 + (int)((g.rev >> lane) & 1u));
-        if ((uint32_t)lane == g.drawn) set(7 * lane + 6);
+    if (X) {
+        uint4* dst = reinterpret_cast<uint4*>(X + (size_t)row * VF);
+        for (int c = lane; c < VF / 8; c += 32) {
+            const uint32_t byte = (bits[c >> 2] >> (8 * (c & 3))) & 0xFFu;
+            uint32_t wv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                wv[j] = (((byte >> (2 * j)) & 1u) ? 0x3F80u : 0u) | (((byte >> (2 * j + 1)) & 1u) ? 0x3F800000u : 0u);
+            dst[c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
     }
-    const uint32_t U = unknown_mask(g);
-    for (int pair = lane; pair < 33; pair += 32) {
-        const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
-        if (k >= g.np) continue;
-        const uint32_t q = (g.cur + k) % g.np;
-        const uint32_t len = __popc(g.hand(q));
-        if (s >= len) continue;
-        const int base = 182 + (int)(((k - 1u) * 11u + s) * 13u);
-        const uint32_t t = seq_tile(g, q, s);
-        if ((g.rev >> t) & 1u) {
-            set(base + (t < 24u ? (int)(t >> 1) : 12));
-            continue;
+    if (Xf) {
+        float4* dst = reinterpret_cast<float4*>(Xf + (size_t)row * VF);
+        for (int c = lane; c < VF / 4; c += 32) {
+            const uint32_t nib = (bits[c >> 3] >> (4 * (c & 7))) & 0xFu;
+            dst[c] = make_float4((float)(nib & 1u), (float)((nib >> 1) & 1u), (float)((nib >> 2) & 1u),
+                                 (float)((nib >> 3) & 1u));
         }
-        int lo = -1, hi = 24;
-        for (int j = (int)s - 1; j >= 0; --j) {
-            const uint32_t u = seq_tile(g, q, (uint32_t)j);
-            if (((g.rev >> u) & 1u) && u < 24u) {
-                lo = (int)u;
-                break;
-            }
-        }
-        for (uint32_t j = s + 1; j < len; ++j) {
-            const uint32_t u = seq_tile(g, q, j);
-            if (((g.rev >> u) & 1u) && u < 24u) {
-                hi = (int)u;
-                break;
-            }
-        }
-        // unknown numbered tiles strictly between lo and hi
-        const uint32_t above = lo < 0 ? 0x00FFFFFFu : (0x00FFFFFFu & ~((2u << lo) - 1u));
-        const uint32_t below = (1u << hi) - 1u;
-        const uint32_t m = U & above & below;
-        for (int v = 0; v < 12; ++v)
-            if ((m >> (2 * v)) & 3u) set(base + v);
-        if (U & kJokerMask) set(base + 12);
     }
 }
 
@@ -350,7 +369,11 @@ cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
     if (!encode_kmajor(&tA, a.A, a.M, a.K, kGemmBM) || !encode_kmajor(&tB, a.B, a.N, a.K, BN))
         return cudaErrorInvalidValue;
     const long long tiles = (long long)((a.M + kGemmBM - 1) / kGemmBM) * (a.N / BN);
-    gemm_bf16_tc_kernel<BN><<<(unsigned)tiles, 128, GemmCfg<BN>::kSmem, st>>>(tA, tB, a);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<long long>(tiles, std::max(sms, 1));
+    gemm_bf16_tc_kernel<BN><<<grid, kGemmThreads, GemmCfg<BN>::kSmem, st>>>(tA, tB, a);
     return cudaGetLastError();
 }
 
