@@ -20,6 +20,7 @@ own 4,096 trees).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -39,11 +40,11 @@ PHILOX_OPS_PER_WORD = 25  # Philox-4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 4
 VALUE_MACS_PER_LEAF = 640 * 512 + 2 * 512 * 512 + 512 * 4  # dense layers of the value network
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # DRAM bytes per launch of the pipeline's kernels at the default shape of the
-# 4,096-tree workload (8 chains of 512 trees; 2 trees x 16 warps per rollout
+# 4,096-tree workload (16 chains of 256 trees; 2 trees x 16 warps per rollout
 # CTA), from ncu full captures (cold cache) summarised under profiles/
 # (pipe_select_kernel / pipe_rollout_kernel / pipe_det_kernel _2p24_4096trees_64it.md).
-PROFILED_SHAPE = (8, 2, 16)
-DRAM_PER_LAUNCH = {"select": 450_816, "rollout": 98_048, "det": 517_376}
+PROFILED_SHAPE = (16, 2, 16)
+DRAM_PER_LAUNCH = {"select": 298_752, "rollout": 75_520, "det": 285_696}
 
 
 def _env_int(k, d):
@@ -191,6 +192,7 @@ def run_reference(args, w):
         times.append(dt)
         total += p
     value = total / sum(times)
+    p1, dt1 = oracle_sample(w, 1, 1)  # one tree on one thread
     sample = f"{n} of {w.n_trees} trees per step, each the full {w.budget} iterations x {w.playouts} playouts"
     line = {
         "impl": "reference", "metric": "playouts/s", "value": value, "unit": "playouts/s", "n_gpus": args.gpus,
@@ -198,7 +200,9 @@ def run_reference(args, w):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "trees": w.n_trees, "iterations": w.budget, "playouts_per_leaf": w.playouts,
                    "l2": "n/a (host)"},
-        "cpu_baseline": {"value": value, "unit": "playouts/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "playouts/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "single_thread": {"value": p1 / dt1, "unit": "playouts/s", "decisions_per_s": 1.0 / dt1,
+                                           "sample": "one tree on one host thread"}},
         "e2e": {"value": value, "unit": "playouts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "decisions_per_s": n * args.steps / sum(times),
     }
@@ -228,12 +232,12 @@ def run_ours(args, w):
     budgets = w.budgets()
     forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=shard_tree_ids(rank, n))
     # launch shape: the pipeline in CUDA graphs with the library's default
-    # shape -- min(8, n / (2 SMs)) overlapping chains, 2n / (3 chains SMs)
-    # trees and 16 warps per rollout CTA -- unless overridden
+    # shape -- round(n / (1.7 SMs)) overlapping chains (at most 16), at least
+    # 2 trees per rollout CTA, warps for one playout per thread -- unless overridden
     sms = props.multi_processor_count
-    chains = args.chains or max(1, min(8, n // (2 * sms)))
-    trees_per_cta = args.trees_per_cta or max(1, min(64, 2 * n // (3 * chains * sms)))
-    warps = args.warps or 16
+    chains = args.chains or max(1, min(16, round(n / (1.7 * sms))))
+    trees_per_cta = args.trees_per_cta or max(2, min(64, math.ceil(n / (chains * 0.85 * sms))))
+    warps = args.warps or max(4, min(16, (trees_per_cta * w.playouts + 31) // 32))
     forest.dvc_forest_tune(2, trees_per_cta, warps, chains)
     stats = torch.empty((n, 8), dtype=torch.int32, device=dev)
     words = torch.zeros(1, dtype=torch.int64, device=dev)

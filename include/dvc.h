@@ -233,8 +233,9 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
  * engine (the default is 2 for forests of at least two trees per SM, else 1).
  * trees_per_cta, warps_per_cta, chains 0 = the engine's defaults (fused:
  * ceil(n_trees / SMs) trees, at most 32, and one warp per tree up to 16;
- * pipeline: min(8, n_trees / (2 SMs)) chains, 2 n_trees / (3 chains SMs)
- * trees, at most 64, and 16 warps).  Changing
+ * pipeline: round(n_trees / (1.7 SMs)) chains, at most 16; at least 2 trees,
+ * ceil(n_trees / (0.85 chains SMs)), at most 64; warps for one playout per
+ * thread, 4 to 16).  Changing
  * trees_per_cta re-balances which trees share a CTA (longest budget first,
  * least-loaded CTA; equal budgets keep index order) and synchronises the
  * device once.  DVC_E_UNSUPPORTED if

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <deque>
 #include <cstring>
@@ -20,16 +21,18 @@ using namespace dvc_host;
 namespace {
 constexpr int kMaxChains = 16;  // independent chains of the pipeline graph
 
-// Default launch shape of an engine for n trees on `sms` SMs.  Pipeline: many
-// small rollout CTAs (16 warps, about 1.5 CTAs per SM per chain) in up to 8
-// chains, so that the tree walks of some chains run beside the playouts of
-// the others.  Fused: every SM holds a CTA, one warp per tree up to 16.
-void default_shape(int n, int sms, int engine, int& T, int& W, int& chains) {
+// Default launch shape of an engine for n trees on `sms` SMs with P playouts
+// per leaf.  Pipeline: small rollout CTAs of at least two trees, warps enough
+// for one playout per thread (4 to 16), and as many chains (up to 16) as give
+// each chain about 0.85 CTAs per SM, so that the tree walks of some chains
+// run beside the playouts of the others.  Fused: every SM holds a CTA, one
+// warp per tree up to 16.
+void default_shape(int n, int sms, int engine, int P, int& T, int& W, int& chains) {
     const int S = std::max(sms, 1);
     if (engine == 2) {
-        chains = std::max(1, std::min(8, n / (2 * S)));
-        T = std::max(1, std::min(64, 2 * n / (3 * chains * S)));
-        W = 16;
+        chains = std::max(1, std::min(kMaxChains, (int)std::lround(n / (1.7 * S))));
+        T = std::max(2, std::min(64, (int)std::ceil(n / (chains * 0.85 * S))));
+        W = std::max(4, std::min(16, (T * std::max(P, 1) + 31) / 32));
     } else {
         T = std::max(1, std::min(32, (n + S - 1) / S));
         W = std::min(T, 16);
@@ -740,7 +743,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     // enough trees to fill the GPU: the pipeline; small forests: the fused
     // lockstep kernel
     f->engine = n >= 2 * std::max(sms, 1) ? 2 : 1;
-    default_shape(n, sms, f->engine, f->trees_per_cta, f->warps_per_cta, f->chains);
+    default_shape(n, sms, f->engine, c->cfg.playouts, f->trees_per_cta, f->warps_per_cta, f->chains);
     std::vector<int32_t> order(n);
     {
         const int T = f->trees_per_cta;
@@ -1141,7 +1144,7 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->ctx->device);
     const int eng = engine ? engine : f->engine;
     int dT, dW, dC;
-    default_shape(f->n, sms, eng, dT, dW, dC);
+    default_shape(f->n, sms, eng, f->ctx->cfg.playouts, dT, dW, dC);
     const int T = trees_per_cta ? trees_per_cta : dT;
     const int W = warps_per_cta ? warps_per_cta : (trees_per_cta && eng == 1 ? std::min(T, 16) : dW);
     const int oldT = f->trees_per_cta, oldW = f->warps_per_cta, oldC = f->chains;
