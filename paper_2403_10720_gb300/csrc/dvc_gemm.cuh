@@ -8,7 +8,7 @@
 // full/empty mbarriers; warp 1 issues tcgen05.mma (K = 16 each, FP32
 // accumulators in tensor memory) as slices land and frees each stage by
 // tcgen05.commit; the accumulators are double-buffered in tensor memory, so
-// warps 4-11 drain tile i (tcgen05.ld, bias, activation, 16-byte stores)
+// warps 4-19 drain tile i (tcgen05.ld, bias, activation, 16-byte stores)
 // while the tensor cores compute tile i + 1.  Every wait on an mbarrier is
 // bounded: on time-out the kernel records an error, waits (bounded) for its
 // own copies and MMAs, frees its tensor memory and exits.
@@ -155,7 +155,8 @@ struct GemmCfg {
     static constexpr uint32_t kCols = 2u * kAccCols;  // a power of two, >= 64
 };
 
-constexpr int kGemmThreads = 384;  // warp 0 TMA, warp 1 MMA, warps 2-3 idle, warps 4-11 epilogue
+constexpr int kGemmEpiWarps = 16;                       // four per tensor-memory lane quarter
+constexpr int kGemmThreads = 32 * (4 + kGemmEpiWarps);  // warp 0 TMA, warp 1 MMA, warps 2-3 idle, then epilogue
 
 // BN in {16, 32, 64, 128, 256}.  tA: A as a (K, M) tensor, box (64, 128);
 // tB: B as (K, N), box (64, BN); both 128-byte swizzled.  Grid: at most one
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&s_accf[b], 1);
-            mbar_init(&s_acce[b], 8);  // one arrival per epilogue warp
+            mbar_init(&s_acce[b], kGemmEpiWarps);  // one arrival per epilogue warp
         }
         mbar_init(&s_done, 1);
         s_fail = 0;
@@ -256,10 +257,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
     } else if (warp >= 4) {
         // epilogue: warp w reads tensor-memory lanes 32 (w mod 4) .. +31 (one
-        // output row per thread) and half of the tile's columns
-        const int quarter = warp & 3, half = (warp - 4) >> 2;
-        const int cw = BN >= 32 ? BN / 2 : BN;
-        const int cbeg = BN >= 32 ? half * cw : (half ? BN : 0);
+        // output row per thread) and one of up to four column groups
+        constexpr int kGroups = BN / 16 < kGemmEpiWarps / 4 ? BN / 16 : kGemmEpiWarps / 4;
+        constexpr int cw = BN / kGroups;
+        const int quarter = warp & 3, group = (warp - 4) >> 2;
+        const int cbeg = group < kGroups ? group * cw : BN;
         int j = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int b = j & 1, u = j >> 1;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const bool live = row < a.M;
             const uint32_t acc = tmem + (uint32_t)b * Cfg::kAccCols + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-            for (int c0 = cbeg; c0 < cbeg + cw && c0 < BN; c0 += 16) {
+            for (int c0 = cbeg; c0 < cbeg + cw && c0 < BN; c0 += 16) {  // cw is a multiple of 16
                 float v[16];
                 tc_ld16(acc + (uint32_t)c0, v);
                 if (live) {
