@@ -56,6 +56,7 @@ __device__ __forceinline__ uint32_t unknown_mask(const G& g) { return g.tmask & 
 __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X,
                                                        float* Xf) {
     __shared__ uint32_t s_bits[8][VF / 32];
+    __shared__ uint8_t s_row[8][3][12];  // per warp: the opponents' rows (tile ids, 0xFF past the end)
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
     if (row >= npad) return;
@@ -76,6 +77,19 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
             if ((uint32_t)lane == g.drawn) set(7 * lane + 6);
         }
         const uint32_t U = unknown_mask(g);
+        // each lane places one (opponent, slot) of the rows, then reads its
+        // neighbours from shared memory
+        uint8_t(*rows)[12] = s_row[w];
+        for (int pair = lane; pair < 33; pair += 32) {
+            const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
+            uint32_t t = 0xFFu;
+            if (k < g.np) {
+                const uint32_t q = (g.cur + k) % g.np;
+                if (s < (uint32_t)__popc(g.hand(q))) t = seq_tile(g, q, s);
+            }
+            rows[k - 1u][s] = (uint8_t)t;
+        }
+        __syncwarp();
         for (int pair = lane; pair < 33; pair += 32) {
             const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
             if (k >= g.np) continue;
@@ -83,21 +97,22 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
             const uint32_t len = __popc(g.hand(q));
             if (s >= len) continue;
             const int base = 182 + (int)(((k - 1u) * 11u + s) * 13u);
-            const uint32_t t = seq_tile(g, q, s);
+            const uint8_t* seq = rows[k - 1u];
+            const uint32_t t = seq[s];
             if ((g.rev >> t) & 1u) {
                 set(base + (t < 24u ? (int)(t >> 1) : 12));
                 continue;
             }
             int lo = -1, hi = 24;
             for (int j = (int)s - 1; j >= 0; --j) {
-                const uint32_t u = seq_tile(g, q, (uint32_t)j);
+                const uint32_t u = seq[j];
                 if (((g.rev >> u) & 1u) && u < 24u) {
                     lo = (int)u;
                     break;
                 }
             }
             for (uint32_t j = s + 1; j < len; ++j) {
-                const uint32_t u = seq_tile(g, q, j);
+                const uint32_t u = seq[j];
                 if (((g.rev >> u) & 1u) && u < 24u) {
                     hi = (int)u;
                     break;
