@@ -484,6 +484,59 @@ def run_selfplay(args):
     }), flush=True)
 
 
+def run_policy(args):
+    """The ordering-aware playout policy against the uniform one: games
+    between the two playout agents at equal iteration budgets, and the search
+    throughput of each policy on the batched workload (one line of JSON)."""
+    import dataclasses
+
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build, selfplay
+    build.build()
+    w = BATCHED
+    speed = {}
+    for policy in (0, 1):
+        ctx = dvc.Context(dvc.Config(**dict(w.config_kwargs(), policy=policy)), 0)
+        n, it = w.n_trees, 512
+        roots = ctx.dvc_init_states(w.root_seed, n)
+        f = dvc.Forest(ctx, roots, [it] * n, w.seed)
+        f.dvc_mcts_step(it)
+        f.dvc_forest_reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f.dvc_mcts_step(it)
+        b.record()
+        torch.cuda.synchronize()
+        ctx.dvc_check()
+        ms = a.elapsed_time(b)
+        speed["ordered" if policy else "uniform"] = {"playouts_per_s": n * it * w.playouts / (ms * 1e-3),
+                                                     "ms": ms, "trees": n, "iterations": it}
+        f.close()
+    kw = dict(w.config_kwargs(), playouts=32, max_predraw=0)
+    ctx_u = dvc.Context(dvc.Config(**dict(kw, policy=0)), 0)
+    ctx_o = dvc.Context(dvc.Config(**dict(kw, policy=1)), 0)
+    hbm = int(args.hbm_gb * (1 << 30)) // 2
+    srv_u = dvc.Server(ctx_u, hbm, args.move_budget, seed=9)
+    srv_o = dvc.Server(ctx_o, hbm, args.move_budget, seed=9)
+    games = selfplay.play_agents(ctx_u, (srv_o, dvc.DVC_MODE_ROLLOUT, args.move_budget),
+                                 (srv_u, dvc.DVC_MODE_ROLLOUT, args.move_budget), args.games, root_seed=3003, seed=11,
+                                 poll_iters=args.move_budget)
+    srv_u.close()
+    srv_o.close()
+    print(json.dumps({
+        "metric": "ordered-policy agent win rate", "value": games["a_win_rate"], "unit": "fraction of games",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "2p24_ordered_vs_uniform_playouts_selfplay", "games": args.games,
+                   "iterations_per_move": args.move_budget, "playouts_per_leaf": 32, "players": 2, "tiles": 24},
+        "ci95": games["ci95"], "fair_share": games["fair_share"], "games_finished": games["games_finished"],
+        "turns": games["turns"], "selfplay_decisions_per_s": games["decisions_per_s"],
+        "search_throughput": speed,
+    }), flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals of move queries into a device-resident server."""
     import numpy as np
@@ -524,7 +577,7 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="pipeline chains (launch shape only; 0 = default)")
     ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve", "selfplay"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve", "selfplay", "policy"])
     ap.add_argument("--train-states", type=int, default=10_000_000, help="selfplay: training states")
     ap.add_argument("--epochs", type=int, default=4, help="selfplay: training epochs")
     ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
@@ -541,10 +594,10 @@ def main():
     if args.workload == "serve":
         run_serve(args)
         return
-    if args.workload == "selfplay":
+    if args.workload in ("selfplay", "policy"):
         if args.hbm_gb == 64.0:
             args.hbm_gb = 4.0
-        run_selfplay(args)
+        (run_selfplay if args.workload == "selfplay" else run_policy)(args)
         return
     w = BATCHED
     if args.trees or args.iterations:

@@ -94,7 +94,13 @@ typedef struct dvc_state {
  * random word is below cont_thr (2^31 = probability 1/2; 0 = never, and no
  * word is drawn); inside the tree the turn always ends (Sec. III-A).
  * d_max -- the expansion depth limit of Sec. III-A, in guess plies below the
- * root.  c_uct -- the UCB1 exploration constant.
+ * root.  c_uct -- the UCB1 exploration constant.  policy -- the playout guess
+ * rule: 0 = uniform over the legal guesses (Sec. II-B, the paper's random
+ * playout); 1 = ordering-aware, not the paper's: for each face-down slot only
+ * the identities that fit between its nearest face-up numbered neighbours in
+ * the sorted row (jokers anywhere), uniform over the kept (slot, identity)
+ * pairs in the same canonical order, one word per guess.  It changes
+ * playouts only; the tree's actions stay the legal guesses.
  */
 typedef struct dvc_config {
     int32_t nplayers;         /* 2..4 */
@@ -106,6 +112,7 @@ typedef struct dvc_config {
     double c_uct;             /* sqrt(2) */
     int32_t d_max;            /* 8 */
     int32_t playouts;         /* playouts per leaf in dvc_mcts_step (leaf parallelism) */
+    int32_t policy;           /* playout guesses: 0 uniform (default), 1 ordering-aware (see above) */
 } dvc_config;
 
 typedef struct dvc_ctx dvc_ctx;

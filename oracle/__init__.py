@@ -13,11 +13,13 @@ Pin status per function:
   init_states ....... pinned (rule invariants, deal sizes, history bounds)
   legal_count ....... pinned (88 root guesses of Sec. III-A, closed form I7)
   rollout / trace ... pinned (invariants, closed-form 1/k endgame, exact
-                      win probabilities of tiny endgames by enumeration)
+                      win probabilities of tiny endgames by enumeration,
+                      under both playout policies)
   det_count ......... pinned (brute-force enumeration of consistent deals)
   determinize ....... pinned (chi-square against uniform over those deals)
   mcts .............. pinned (UCB1 forced-win toy sequence, count invariants)
-  legal_actions ..... pinned (88 root guesses, canonical order written out)
+  legal_actions ..... pinned (88 root guesses, canonical order written out;
+                      ordering-aware policy: hand-made rows written out)
   play_move ......... pinned (hand-made positions: correct and wrong guesses,
                       elimination, empty pool, the draw that follows)
   value_features .... pinned (hand-made positions with features written out)
@@ -46,6 +48,7 @@ class _Cfg(ctypes.Structure):
         ("c_uct", ctypes.c_double),
         ("d_max", ctypes.c_int32),
         ("playouts", ctypes.c_int32),
+        ("policy", ctypes.c_int32),
     ]
 
 
@@ -60,10 +63,11 @@ class OracleConfig:
     c_uct: float = 1.4142135623730951
     d_max: int = 8
     playouts: int = 1
+    policy: int = 0
 
     def c(self) -> _Cfg:
         return _Cfg(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
-                    self.cont_thr, self.c_uct, self.d_max, self.playouts)
+                    self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy)
 
 
 def lib():
@@ -97,7 +101,7 @@ def lib():
         L.or_playout_trace.restype = ctypes.c_int
         L.or_play_move.argtypes = [u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u8p]
         L.or_play_move.restype = ctypes.c_int
-        L.or_legal_actions.argtypes = [u8p, i32p]
+        L.or_legal_actions.argtypes = [u8p, ctypes.c_int, i32p]
         L.or_legal_actions.restype = ctypes.c_int
         L.or_mcts.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i32p,
                               ctypes.POINTER(ctypes.c_int), i32p]
@@ -155,11 +159,12 @@ def legal_count(state) -> int:
     return lib().or_legal_count(_u8(s))
 
 
-def legal_actions(state) -> np.ndarray:
-    """Legal guesses in canonical order as action codes (seat << 10 | slot << 5 | identity)."""
+def legal_actions(state, policy: int = 0) -> np.ndarray:
+    """Legal guesses in canonical order as action codes (seat << 10 | slot << 5 | identity);
+    policy 1: only those the ordering-aware playout policy keeps."""
     s = _state(state)
     out = np.zeros(3 * 26 * 26, dtype=np.int32)
-    n = lib().or_legal_actions(_u8(s), _i32(out))
+    n = lib().or_legal_actions(_u8(s), int(policy), _i32(out))
     return out[:n].copy()
 
 

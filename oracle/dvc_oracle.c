@@ -58,6 +58,7 @@ typedef struct {
     uint32_t cont_thr; /* after a correct guess in a playout: guess again iff word < cont_thr; 0 = never, no word */
     double c_uct;
     int32_t d_max, playouts;
+    int32_t policy; /* playout guesses: 0 uniform over the legal guesses; 1 ordering-aware (see legal_list_policy) */
 } or_config;
 
 /* ------------------------------------------------------------------ Philox */
@@ -300,6 +301,41 @@ static int legal_list(const ost* s, int* lq, int* ls, int* lx) {
     return n;
 }
 
+/* The ordering-aware playout policy (not the paper's, a stronger playout
+ * for comparison): the same canonical enumeration, keeping for each face-down
+ * slot only the identities that fit its place in the sorted row -- a
+ * numbered identity must lie strictly between the nearest face-up numbered
+ * tiles to the slot's left and right in that row (by tile id, so black
+ * before white on equal values); a joker identity fits anywhere.  The slot's
+ * own tile always fits, so every face-down slot keeps at least one guess. */
+static int legal_list_policy(const ost* s, int policy, int* lq, int* ls, int* lx) {
+    if (policy == 0) return legal_list(s, lq, ls, lx);
+    int n = 0;
+    for (int off = 1; off < s->P; off++) {
+        int q = (s->cur + off) % s->P;
+        if (!s->alive[q]) continue;
+        for (int i = 0; i < s->len[q]; i++) {
+            if (s->rev[s->seq[q][i]]) continue;
+            int lo = -1, hi = 24;
+            for (int j = i - 1; j >= 0; j--) {
+                int u = s->seq[q][j];
+                if (s->rev[u] && u < 24) { lo = u; break; }
+            }
+            for (int j = i + 1; j < s->len[q]; j++) {
+                int u = s->seq[q][j];
+                if (s->rev[u] && u < 24) { hi = u; break; }
+            }
+            for (int x = 0; x < s->T; x++) {
+                if (s->owner[x] == s->cur || s->rev[x]) continue;
+                if (x < 24 && !(x > lo && x < hi)) continue;
+                lq[n] = q; ls[n] = i; lx[n] = x;
+                n++;
+            }
+        }
+    }
+    return n;
+}
+
 static int guess_is_legal(const ost* s, int q, int slot, int x) {
     if (q == s->cur || q >= s->P || !s->alive[q]) return 0;
     if (slot >= s->len[q] || s->rev[s->seq[q][slot]]) return 0;
@@ -352,9 +388,9 @@ static _Thread_local int legal_q[MAXLEGAL], legal_s[MAXLEGAL], legal_x[MAXLEGAL]
 
 /* One random playout from a state where the player to move is about to guess
  * (Sec. II-B): uniform guesses among the legal ones until one player is left. */
-static int playout(ost s, uint32_t cont_thr, stream* rng, uint8_t* trace, int* ntrace, int maxtrace) {
+static int playout(ost s, uint32_t cont_thr, int policy, stream* rng, uint8_t* trace, int* ntrace, int maxtrace) {
     for (;;) {
-        int n = legal_list(&s, legal_q, legal_s, legal_x);
+        int n = legal_list_policy(&s, policy, legal_q, legal_s, legal_x);
         int k = pick(next_word(rng), n);
         int r = resolve(&s, legal_q[k], legal_s[k], legal_x[k], 0, cont_thr, rng);
         if (r == TURN_OVER) next_turn(&s, rng);
@@ -749,7 +785,7 @@ int or_rollout(const or_config* cfg, const uint8_t* leaf, int P, uint64_t seed, 
     for (int j = 0; j < P; j++) {
         stream rng;
         stream_open(&rng, seed, tree, (uint32_t)j, leaf_id, TAG_ROLL);
-        int w = playout(s, cfg->cont_thr, &rng, NULL, NULL, 0);
+        int w = playout(s, cfg->cont_thr, cfg->policy, &rng, NULL, NULL, 0);
         wins[w]++;
         total += rng.words;
     }
@@ -764,7 +800,7 @@ int or_playout_trace(const or_config* cfg, const uint8_t* leaf, uint64_t seed, u
     stream rng;
     stream_open(&rng, seed, tree, j, leaf_id, TAG_ROLL);
     int n = 0;
-    playout(s, cfg->cont_thr, &rng, trace, &n, maxtrace);
+    playout(s, cfg->cont_thr, cfg->policy, &rng, trace, &n, maxtrace);
     return n;
 }
 
@@ -801,12 +837,13 @@ int or_play_move(const uint8_t* in, int code, uint64_t seed, uint32_t game, uint
 }
 
 /* The legal guesses of a state in canonical order (opponents from the mover
- * + 1, slots left to right, identities ascending) as action codes; returns
- * their number (at most 3 * 26 * 26). */
-int or_legal_actions(const uint8_t* state, int32_t* codes) {
+ * + 1, slots left to right, identities ascending) as action codes, all of
+ * them (policy 0) or those the ordering-aware playout policy keeps (policy
+ * 1); returns their number (at most 3 * 26 * 26). */
+int or_legal_actions(const uint8_t* state, int policy, int32_t* codes) {
     ost s;
     unpack(state, &s);
-    const int n = legal_list(&s, legal_q, legal_s, legal_x);
+    const int n = legal_list_policy(&s, policy, legal_q, legal_s, legal_x);
     for (int a = 0; a < n; a++) codes[a] = (legal_q[a] << 10) | (legal_s[a] << 5) | legal_x[a];
     return n;
 }

@@ -43,6 +43,7 @@ class dvc_config(ctypes.Structure):
         ("c_uct", ctypes.c_double),
         ("d_max", ctypes.c_int32),
         ("playouts", ctypes.c_int32),
+        ("policy", ctypes.c_int32),
     ]
 
 
@@ -58,10 +59,11 @@ class Config:
     c_uct: float = 1.4142135623730951
     d_max: int = 8
     playouts: int = 1
+    policy: int = 0  # playout guesses: 0 uniform, 1 ordering-aware
 
     def c(self) -> dvc_config:
         return dvc_config(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
-                          self.cont_thr, self.c_uct, self.d_max, self.playouts)
+                          self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy)
 
 
 class dvc_result(ctypes.Structure):

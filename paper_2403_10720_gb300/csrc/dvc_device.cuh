@@ -434,6 +434,55 @@ __device__ __forceinline__ int random_guess(G& g, R& r, uint32_t cont_thr, const
     return resolve(g, q, target, rank == i ? target : 0xFFu, false, cont_thr, r);
 }
 
+// The identities the ordering-aware playout policy keeps for the face-down
+// slot of player q that holds tile t: unknown numbered identities strictly
+// between the nearest face-up numbered tiles to the slot's left and right in
+// q's row (by id), and every unknown joker.  For a numbered t the row's
+// numbered tiles below t are exactly those to its left; a joker stands after
+// the first joker_gap numbered tiles.
+__device__ __forceinline__ uint32_t ordered_fit(const G& g, uint32_t q, uint32_t t, uint32_t U) {
+    const uint32_t hn = g.hand(q) & kNumMask;
+    const uint32_t left = t < 24u ? hn & ((1u << t) - 1u) : low_bits(hn, t == 24u ? g.jg0 : g.jg1);
+    const uint32_t lrev = left & g.rev, rrev = hn & ~left & ~(t < 24u ? 1u << t : 0u) & g.rev;
+    const uint32_t lo_mask = lrev ? (2u << (31 - __clz(lrev))) - 1u : 0u;       // identities <= left neighbour
+    const uint32_t hi_mask = rrev ? (1u << (__ffs(rrev) - 1)) - 1u : kNumMask;  // identities < right neighbour
+    return (U & kNumMask & hi_mask & ~lo_mask) | (U & kJokerMask);
+}
+
+// A uniform random guess under the ordering-aware playout policy (not the
+// paper's: a stronger playout to compare with).  Same canonical order and one
+// word per guess, restricted per slot by ordered_fit.
+template <class R>
+__device__ __forceinline__ int random_guess_ordered(G& g, R& r, uint32_t cont_thr) {
+    const uint32_t U = g.tmask & ~g.hand(g.cur) & ~g.rev;
+    uint32_t total = 0;
+    for (uint32_t off = 1; off < g.np; ++off) {
+        uint32_t q = g.cur + off;
+        q = q >= g.np ? q - g.np : q;
+        if (!((g.alive >> q) & 1u)) continue;
+        const uint32_t nh = __popc(g.hand(q) & ~g.rev);
+        for (uint32_t h = 0; h < nh; ++h) total += __popc(ordered_fit(g, q, hidden_slot(g, q, h), U));
+    }
+    uint32_t k = pick(r.next(), total);
+    for (uint32_t off = 1; off < g.np; ++off) {
+        uint32_t q = g.cur + off;
+        q = q >= g.np ? q - g.np : q;
+        if (!((g.alive >> q) & 1u)) continue;
+        const uint32_t nh = __popc(g.hand(q) & ~g.rev);
+        for (uint32_t h = 0; h < nh; ++h) {
+            const uint32_t t = hidden_slot(g, q, h);
+            const uint32_t F = ordered_fit(g, q, t, U);
+            const uint32_t c = __popc(F);
+            if (k < c) {
+                const uint32_t x = nth_set(F, k);
+                return resolve(g, q, t, x == t ? t : 0xFFu, false, cont_thr, r);
+            }
+            k -= c;
+        }
+    }
+    return resolve(g, g.cur, 0u, 0xFFu, false, cont_thr, r);  // unreachable: total counts every kept guess
+}
+
 // One playout to the end (Sec. II-B); returns the winner.  Every guess turns
 // one tile face up, so a game has at most 26 guesses; the cap only stops a
 // malformed record (result kNone, credited to nobody).
@@ -557,6 +606,64 @@ __device__ __forceinline__ int step_2p24(uint32_t& h0, uint32_t& h1, uint32_t& r
     const uint32_t i = k - s * nid;
     const uint32_t target = nth_set12(hidq, s, lut12);
     if (__popc(U & ((1u << target) - 1u)) == i) {
+        rev |= 1u << target;
+        if (hidq == (1u << target)) {
+            winner = cur;
+            return kGameOver;
+        }
+        if (cont_thr != 0u && r.next() < cont_thr) return kGuessAgain;
+    } else {
+        const uint32_t t = drawn != kNone ? drawn : (uint32_t)__ffs(hc & ~rev) - 1u;
+        rev |= 1u << t;
+        if (!(hc & ~rev)) {
+            winner = cur ^ 1u;
+            return kGameOver;
+        }
+    }
+    cur ^= 1u;
+    const uint32_t pool = kNumMask & ~(h0 | h1);
+    if (pool) {
+        const uint32_t t = nth_set12(pool, __umulhi(r.next(), __popc(pool)), lut12);
+        if (cur) h1 |= 1u << t;
+        else h0 |= 1u << t;
+        drawn = t;
+    } else {
+        drawn = kNone;
+    }
+    return kTurnOver;
+}
+
+// step_2p24 under the ordering-aware playout policy: the guess is uniform
+// over the (face-down slot, identity) pairs the policy keeps.  Without
+// jokers a row is in id order, so a slot's face-up neighbours are the
+// opponent's face-up tiles just below and just above its tile.
+template <class Q>
+__device__ __forceinline__ int step_2p24_ordered(uint32_t& h0, uint32_t& h1, uint32_t& rev, uint32_t& cur,
+                                                 uint32_t& drawn, uint32_t& winner, Q& r, uint32_t cont_thr,
+                                                 const unsigned long long* lut12) {
+    r.ensure(3);
+    const uint32_t hc = cur ? h1 : h0, hq = cur ? h0 : h1;
+    const uint32_t hidq = hq & ~rev, rq = hq & rev;
+    const uint32_t U = kNumMask & ~hc & ~rev;
+    auto fit = [&](uint32_t t) {
+        const uint32_t below = rq & ((1u << t) - 1u), above = rq & ~((2u << t) - 1u);
+        const uint32_t lo_mask = below ? (2u << (31 - __clz(below))) - 1u : 0u;
+        const uint32_t hi_mask = above ? (1u << (__ffs(above) - 1)) - 1u : kNumMask;
+        return U & hi_mask & ~lo_mask;
+    };
+    uint32_t total = 0;
+    for (uint32_t m = hidq; m; m &= m - 1u) total += __popc(fit(__ffs(m) - 1u));
+    uint32_t k = __umulhi(r.next(), total), target = 0u, x = 0u;
+    for (uint32_t m = hidq; m; m &= m - 1u) {
+        const uint32_t t = __ffs(m) - 1u, F = fit(t), c = __popc(F);
+        if (k < c) {
+            target = t;
+            x = nth_set12(F, k, lut12);
+            break;
+        }
+        k -= c;
+    }
+    if (x == target) {
         rev |= 1u << target;
         if (hidq == (1u << target)) {
             winner = cur;

@@ -186,8 +186,6 @@ __global__ void determinize_kernel(const dvc_state* roots, int n, int observer, 
     store_state(o, out[idx]);
 }
 
-// Leaf-parallel playouts: thread -> (leaf, playout).  Win counts are summed
-// with integer atomics, so the result is independent of scheduling.
 // One self-play move per game: the guess actions[i] on the true state, then
 // the next seat's draw on stream (seed, game id, turn, tag 5).
 __global__ void play_move_kernel(dvc_state* states, int n, const int32_t* actions, uint64_t seed,
@@ -208,6 +206,9 @@ __global__ void play_move_kernel(dvc_state* states, int n, const int32_t* action
     store_state(g, states[i]);
 }
 
+// Leaf-parallel playouts: thread -> (leaf, playout).  Win counts are summed
+// with integer atomics, so the result is independent of scheduling.
+template <bool ORD>
 __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uint64_t seed,
                                const uint32_t* tree_ids, const uint32_t* leaf_ids, uint32_t cont_thr, int32_t* wins,
                                unsigned long long* words) {
@@ -231,7 +232,11 @@ __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uin
             winner = kNone;
             for (int guard = 0; guard < 128; ++guard) {
                 r.ensure(4);
-                const int res = random_guess(g, r, cont_thr, s_magic);
+                int res;
+                if constexpr (ORD)
+                    res = random_guess_ordered(g, r, cont_thr);
+                else
+                    res = random_guess(g, r, cont_thr, s_magic);
                 if (res == kGameOver) {
                     winner = g.winner;
                     break;
@@ -525,6 +530,7 @@ SearchParams params_of(const dvc_forest* f) {
     sp.d_max = f->ctx->cfg.d_max;
     sp.playouts = f->ctx->cfg.playouts;
     sp.cont_thr = f->ctx->cfg.cont_thr;
+    sp.policy = f->ctx->cfg.policy;
     return sp;
 }
 
@@ -544,6 +550,7 @@ int dvc_create(dvc_ctx** out, const dvc_config* cfg, int device) {
     if (cfg->d_max < 0 || cfg->d_max > kPathMax - 2 || cfg->playouts < 1 || cfg->playouts > (1 << 20))
         return DVC_E_INVALID;
     if (!(cfg->c_uct >= 0.0)) return DVC_E_INVALID;
+    if (cfg->policy != 0 && cfg->policy != 1) return DVC_E_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -664,9 +671,14 @@ int dvc_rollout_batch(dvc_ctx* c, const dvc_state* d_leaves, int n_leaves, int p
     const int block = 256;
     long long blocks = (total + block - 1) / block;
     blocks = std::min<long long>(blocks, (long long)dev_sms * 64);
-    rollout_kernel<<<(unsigned)blocks, block, 0, st>>>(d_leaves, n_leaves, playouts_per_leaf, seed, d_tree_ids,
-                                                       d_leaf_ids, c->cfg.cont_thr, d_wins,
-                                                       (unsigned long long*)d_words);
+    if (c->cfg.policy)
+        rollout_kernel<true><<<(unsigned)blocks, block, 0, st>>>(d_leaves, n_leaves, playouts_per_leaf, seed,
+                                                                 d_tree_ids, d_leaf_ids, c->cfg.cont_thr, d_wins,
+                                                                 (unsigned long long*)d_words);
+    else
+        rollout_kernel<false><<<(unsigned)blocks, block, 0, st>>>(d_leaves, n_leaves, playouts_per_leaf, seed,
+                                                                  d_tree_ids, d_leaf_ids, c->cfg.cont_thr, d_wins,
+                                                                  (unsigned long long*)d_words);
     return check_launch(c, "rollout_kernel");
 }
 
@@ -861,22 +873,29 @@ int launch_fused(dvc_forest* f, int n_iterations, cudaStream_t st) {
     const int threads = 32 * W;
     const bool fast2 = c->cfg.nplayers == 2 && c->cfg.ntiles == 24;
     cudaError_t e;
-#define DVC_LAUNCH_POOL(MT, F2)                                                                                   \
+#define DVC_LAUNCH_POOL(MT, F2, ORD)                                                                              \
     do {                                                                                                          \
-        e = cudaFuncSetAttribute(mcts_pool_kernel<MT, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes); \
+        e = cudaFuncSetAttribute(mcts_pool_kernel<MT, F2, ORD>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                 (int)L.bytes);                                                                   \
         if (e == cudaSuccess)                                                                                     \
-            mcts_pool_kernel<MT, F2><<<grid, threads, L.bytes, st>>>(dev_of(f), params_of(f), n_iterations, f->order, \
-                                                                     f->n, T);                                    \
+            mcts_pool_kernel<MT, F2, ORD><<<grid, threads, L.bytes, st>>>(dev_of(f), params_of(f), n_iterations,  \
+                                                                          f->order, f->n, T);                     \
     } while (0)
-    if (threads <= 512) {
-        if (fast2) DVC_LAUNCH_POOL(512, true);
-        else DVC_LAUNCH_POOL(512, false);
+    if (c->cfg.policy && threads <= 512) {  // ordering-aware playouts
+        if (fast2) DVC_LAUNCH_POOL(512, true, true);
+        else DVC_LAUNCH_POOL(512, false, true);
+    } else if (c->cfg.policy) {
+        if (fast2) DVC_LAUNCH_POOL(1024, true, true);
+        else DVC_LAUNCH_POOL(1024, false, true);
+    } else if (threads <= 512) {
+        if (fast2) DVC_LAUNCH_POOL(512, true, false);
+        else DVC_LAUNCH_POOL(512, false, false);
     } else if (threads <= 768) {
-        if (fast2) DVC_LAUNCH_POOL(768, true);
-        else DVC_LAUNCH_POOL(768, false);
+        if (fast2) DVC_LAUNCH_POOL(768, true, false);
+        else DVC_LAUNCH_POOL(768, false, false);
     } else {
-        if (fast2) DVC_LAUNCH_POOL(1024, true);
-        else DVC_LAUNCH_POOL(1024, false);
+        if (fast2) DVC_LAUNCH_POOL(1024, true, false);
+        else DVC_LAUNCH_POOL(1024, false, false);
     }
 #undef DVC_LAUNCH_POOL
     if (e != cudaSuccess) return cuda_fail(c, e, "mcts_pool_kernel attributes");
@@ -896,12 +915,20 @@ int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
     if (i1 <= i0) return DVC_OK;
     pipe_select_kernel<<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
     const int threads = pipe_rollout_threads(f);
-    if (c->cfg.nplayers == 2 && c->cfg.ntiles == 24)
-        pipe_rollout_kernel<true><<<b1 - b0, threads, pipe_rollout_smem(L, threads, true), st>>>(
-            sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
+    const bool fast2 = c->cfg.nplayers == 2 && c->cfg.ntiles == 24;
+    const uint32_t smem = pipe_rollout_smem(L, threads, fast2);
+    if (fast2 && !sp.policy)
+        pipe_rollout_kernel<true, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
+                                                                        f->d_words);
+    else if (fast2)
+        pipe_rollout_kernel<true, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
+                                                                       f->d_words);
+    else if (!sp.policy)
+        pipe_rollout_kernel<false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
+                                                                         f->d_words);
     else
-        pipe_rollout_kernel<false><<<b1 - b0, threads, pipe_rollout_smem(L, threads, false), st>>>(
-            sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words);
+        pipe_rollout_kernel<false, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
+                                                                        f->d_words);
     return check_launch(c, "pipeline kernels");
 }
 
@@ -997,15 +1024,18 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     dvc_ctx* c = f->ctx;
     {
         const int threads = pipe_rollout_threads(f);
-        cudaError_t e = cudaFuncSetAttribute(pipe_rollout_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pipe_rollout_smem(f->trees_per_cta, threads, true));
-        // two 1024-thread CTAs per SM need the largest shared-memory carveout
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pipe_rollout_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pipe_rollout_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)pipe_rollout_smem(f->trees_per_cta, threads, false));
+        const int sm2 = (int)pipe_rollout_smem(f->trees_per_cta, threads, true);
+        const int smg = (int)pipe_rollout_smem(f->trees_per_cta, threads, false);
+        cudaError_t e = cudaSuccess;
+        // several rollout CTAs per SM need the largest shared-memory carveout
+        for (auto k : {pipe_rollout_kernel<true, false>, pipe_rollout_kernel<true, true>}) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+        }
+        for (auto k : {pipe_rollout_kernel<false, false>, pipe_rollout_kernel<false, true>})
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smg);
         if (e != cudaSuccess) return cuda_fail(c, e, "pipeline attributes");
     }
     if (int rc = clear_pipe_det(f, st)) return rc;

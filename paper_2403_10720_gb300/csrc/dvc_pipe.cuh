@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(128)
 // step), so lanes wait for the longest game only at the end of the pool.
 // Two-player 24-tile games queue their words in a shared-memory ring
 // (RingQueue) so that two 1024-thread CTAs fit on an SM.
-template <bool FAST2>
+// ORD: the ordering-aware playout policy (sp.policy == 1), compiled apart.
+template <bool FAST2, bool ORD = false>
 __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     pipe_rollout_kernel(SearchParams sp, int n, int L, int b0, const int32_t* order, const TreeMeta* meta, PipeBufs P,
                         unsigned long long* words_out) {
@@ -240,10 +241,16 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         if (busy) {
             int res;
             if constexpr (FAST2) {
-                res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
+                if constexpr (ORD)
+                    res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);
+                else
+                    res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
             } else {
                 r.ensure(4);
-                res = random_guess(g, r, sp.cont_thr, s_magic);
+                if constexpr (ORD)
+                    res = random_guess_ordered(g, r, sp.cont_thr);
+                else
+                    res = random_guess(g, r, sp.cont_thr, s_magic);
                 if (res == kTurnOver) next_turn(g, r);
                 winner = g.winner;
             }

@@ -61,7 +61,9 @@ struct PoolLayout {
     }
 };
 
-template <int MAXT, bool FAST2>
+// ORD: the ordering-aware playout policy (sp.policy == 1), compiled apart so
+// that the uniform playout loop keeps its registers.
+template <int MAXT, bool FAST2, bool ORD = false>
 __global__ void __launch_bounds__(MAXT, 1)
     mcts_pool_kernel(ForestDev F, SearchParams sp, int n_iter, const int32_t* order, int n_trees, int T) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -194,10 +196,16 @@ __global__ void __launch_bounds__(MAXT, 1)
                 if (busy) {
                     int res;
                     if constexpr (FAST2) {
-                        res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
+                        if constexpr (ORD)
+                            res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);
+                        else
+                            res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
                     } else {
                         r.ensure(4);
-                        res = random_guess(g, r, sp.cont_thr, s_magic);
+                        if constexpr (ORD)
+                            res = random_guess_ordered(g, r, sp.cont_thr);
+                        else
+                            res = random_guess(g, r, sp.cont_thr, s_magic);
                         if (res == kTurnOver) next_turn(g, r);
                         winner = g.winner;
                     }

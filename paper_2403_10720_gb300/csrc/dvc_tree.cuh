@@ -45,6 +45,7 @@ struct SearchParams {
     int32_t d_max;
     int32_t playouts;
     uint32_t cont_thr;
+    int32_t policy;  // playout guesses: 0 uniform, 1 ordering-aware
 };
 
 __device__ __forceinline__ uint32_t block_size(uint32_t k, bool is_root, uint32_t root_legal) {

@@ -16,9 +16,11 @@ from functools import lru_cache
 from itertools import permutations
 
 
-def exact_win_probs(hands, revealed, cur, drawn, ntiles, p_cont):
+def exact_win_probs(hands, revealed, cur, drawn, ntiles, p_cont, ordered=False):
     """hands: list of left-to-right tile lists; revealed: set.  The player to
-    move is about to guess.  Returns {player: Fraction}."""
+    move is about to guess.  ordered: guesses restricted to identities that
+    fit between the slot's nearest face-up numbered neighbours (jokers fit
+    anywhere).  Returns {player: Fraction}."""
     P = len(hands)
     p_cont = Fraction(p_cont)
     init = (tuple(tuple(h) for h in hands), frozenset(revealed),
@@ -71,8 +73,14 @@ def exact_win_probs(hands, revealed, cur, drawn, ntiles, p_cont):
             for i, t in enumerate(hs[q]):
                 if t in rv:
                     continue
+                left = [u for u in hs[q][:i] if u in rv and u < 24]
+                right = [u for u in hs[q][i + 1:] if u in rv and u < 24]
+                lo = left[-1] if left else -1
+                hi = right[0] if right else 24
                 for x in range(ntiles):
                     if x in own or x in rv:
+                        continue
+                    if ordered and x < 24 and not lo < x < hi:
                         continue
                     legal.append((q, i, x))
         acc = {}

@@ -319,3 +319,48 @@ def test_mcts_launch_shapes_agree(dvc, variant, shape):
     oroots = oracle.init_states(ocfg, 33, n)
     want = _oracle_trees(ocfg, oroots, 4, budgets, [2, 9])
     _check_forest(alt, alt.dvc_root_stats().cpu().numpy(), want, [2, 9])
+
+
+# ---------------------------------------------------------------- ordering-aware playout policy
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_rollout_ordered_policy_bit_exact(dvc, variant):
+    kw = dict(VARIANTS[variant], policy=1)
+    ocfg = oracle.OracleConfig(**kw)
+    leaves = oracle.init_states(ocfg, 14, 45)
+    n = len(leaves)
+    tree = np.arange(n, dtype=np.uint32) * 5 + 3
+    leaf = np.arange(n, dtype=np.uint32) * 11 + 1
+    ctx = _ctx(dvc, **kw)
+    words = torch.zeros(1, dtype=torch.int64, device="cuda")
+    wins = ctx.dvc_rollout_batch(torch.from_numpy(leaves).cuda(), 37, 78, _u32(tree), _u32(leaf), words=words)
+    wins = wins.cpu().numpy()
+    total, differs = 0, 0
+    for i in range(n):
+        w, wd = oracle.rollout(ocfg, leaves[i], 37, 78, int(tree[i]), int(leaf[i]))
+        assert (wins[i] == w).all(), i
+        total += wd
+        uniform, _ = oracle.rollout(oracle.OracleConfig(**VARIANTS[variant]), leaves[i], 37, 78, int(tree[i]),
+                                    int(leaf[i]))
+        differs += int((uniform != w).any())
+    assert int(words.item()) == total
+    assert differs > 0   # the policy does change the playouts
+
+
+@pytest.mark.parametrize("variant,shape", [("2p24", (1, 0, 0, 0)), ("2p24", (2, 2, 8, 2)), ("4p26j", (1, 0, 0, 0)),
+                                           ("4p26j", (2, 2, 4, 2))])
+def test_mcts_ordered_policy_bit_exact(dvc, variant, shape):
+    kw = dict(VARIANTS[variant], playouts=24, policy=1)
+    ocfg = oracle.OracleConfig(**kw)
+    n = 5
+    budgets = [90, 40, 1, 70, 66]
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(31, n)
+    oroots = oracle.init_states(ocfg, 31, n)
+    forest = dvc.Forest(ctx, roots, budgets, 6)
+    forest.dvc_forest_tune(*shape)
+    forest.dvc_mcts_step(max(budgets))
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    want = _oracle_trees(ocfg, oroots, 6, budgets, range(n))
+    _check_forest(forest, stats, want, range(n))
