@@ -468,6 +468,9 @@ def run_selfplay(args):
     server = dvc.Server(gctx, int(args.hbm_gb * (1 << 30)), args.move_budget, value_share_pct=50, seed=9)
     games = selfplay.play_games(gctx, server, args.games, args.move_budget, root_seed=3003, seed=11,
                                 poll_iters=args.move_budget)
+    # the value agent with half the iterations against the full-budget playout agent
+    half = selfplay.play_games(gctx, server, args.games, args.move_budget, root_seed=3003, seed=11,
+                               value_budget=args.move_budget // 2, poll_iters=args.move_budget)
     server.close()
     print(json.dumps({
         "metric": "value-agent win rate", "value": games["value_win_rate"], "unit": "fraction of games",
@@ -478,6 +481,8 @@ def run_selfplay(args):
         "ci95": games["ci95"], "fair_share": games["fair_share"], "games_finished": games["games_finished"],
         "turns": games["turns"], "selfplay_decisions_per_s": games["decisions_per_s"],
         "selfplay_wall_s": games["wall_s"],
+        "value_half_budget": {"value_iterations": args.move_budget // 2, "rollout_iterations": args.move_budget,
+                              "value_win_rate": half["value_win_rate"], "ci95": half["ci95"]},
         "winprob_abs_err_heldout": err, "move_agreement": agree,
         "gpu_ms_per_decision": per_dec,
         "train": {"label_s": t_label, "train_s": t_train, "loss_first_epoch": curve[0], "loss_last_epoch": curve[-1]},
@@ -537,6 +542,80 @@ def run_policy(args):
     }), flush=True)
 
 
+def run_scaling(args):
+    """The paper's scaling sweeps (Sec. IV: simulations per second against
+    CPU threads, GPU threads and warps; weak scaling) repeated for this
+    implementation on the 2-player 24-tile batched workload (one JSON line)."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build
+    build.build()
+    w = BATCHED
+    ctx = dvc.Context(dvc.Config(**w.config_kwargs()), 0)
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = E(), E()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    # GPU threads: standalone leaf-parallel playouts, 256 per leaf, one thread per playout
+    leaves_all = ctx.dvc_init_states(w.root_seed, 65536)
+    ids = torch.arange(65536, dtype=torch.int32, device=leaves_all.device)
+    threads = []
+    for n in (1, 4, 16, 64, 256, 1024, 4096, 16384, 65536):
+        sec = timed(lambda: ctx.dvc_rollout_batch(leaves_all[:n], 256, 5, ids[:n], ids[:n]))
+        threads.append({"leaves": n, "playouts": n * 256, "seconds": sec, "playouts_per_s": n * 256 / sec})
+    # warps per rollout CTA: the pipeline at 16 chains x 2 trees, 4,096 trees x 256 iterations
+    roots = ctx.dvc_init_states(w.root_seed, w.n_trees)
+    warps = []
+    for W in (1, 2, 4, 8, 16, 32):
+        f = dvc.Forest(ctx, roots, [256] * w.n_trees, w.seed)
+        f.dvc_forest_tune(2, 2, W, 16)
+
+        def step():
+            f.dvc_forest_reset()
+            f.dvc_mcts_step(256)
+        sec = timed(step, reps=2)
+        warps.append({"warps_per_cta": W, "seconds": sec, "playouts_per_s": w.n_trees * 256 * w.playouts / sec})
+        f.close()
+    # weak scaling: fixed work per tree (256 iterations x 256 playouts), growing forest
+    weak = []
+    for n in (38, 76, 152, 304, 608, 1216, 2432, 4096, 8192):
+        r = ctx.dvc_init_states(w.root_seed, n)
+        f = dvc.Forest(ctx, r, [256] * n, w.seed)
+
+        def step():
+            f.dvc_forest_reset()
+            f.dvc_mcts_step(256)
+        sec = timed(step, reps=2)
+        weak.append({"trees": n, "seconds": sec, "playouts_per_s": n * 256 * w.playouts / sec})
+        f.close()
+    ctx.dvc_check()
+    # CPU threads: the oracle, one 256-iteration tree per thread
+    small = dataclasses.replace(w, budget=256)
+    cpu = []
+    cores = os.cpu_count() or 1
+    for t in sorted({1, 2, 4, 8, 16, cores}):
+        if t > cores:
+            continue
+        p, dt = oracle_sample(small, t, t)
+        cpu.append({"threads": t, "playouts_per_s": p / dt})
+    print(json.dumps({"metric": "scaling sweeps", "workload": w.name, "gpu_threads": threads,
+                      "gpu_warps_per_rollout_cta": warps, "gpu_weak_scaling": weak, "cpu_oracle_threads": cpu}),
+          flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals of move queries into a device-resident server."""
     import numpy as np
@@ -577,7 +656,8 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="pipeline chains (launch shape only; 0 = default)")
     ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "serve", "selfplay", "policy"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "uneven", "serve", "selfplay", "policy", "scaling"])
     ap.add_argument("--train-states", type=int, default=10_000_000, help="selfplay: training states")
     ap.add_argument("--epochs", type=int, default=4, help="selfplay: training epochs")
     ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
@@ -593,6 +673,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "scaling":
+        run_scaling(args)
         return
     if args.workload in ("selfplay", "policy"):
         if args.hbm_gb == 64.0:
