@@ -542,6 +542,57 @@ def run_policy(args):
     }), flush=True)
 
 
+def run_fulltree(args):
+    """The full game tree of Fig. 2a (a correct guess keeps the turn; STOP is
+    an action) against the paper's simplified tree, as two agents playing the
+    full game at equal iteration budgets (one line of JSON)."""
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build, selfplay
+    build.build()
+    w = BATCHED
+    kw = dict(w.config_kwargs(), playouts=32, max_predraw=0)
+    game = dvc.Context(dvc.Config(**dict(kw, tree_continue=1)), 0)
+    ctx_full = dvc.Context(dvc.Config(**dict(kw, tree_continue=1)), 0)
+    ctx_simple = dvc.Context(dvc.Config(**dict(kw, tree_continue=0)), 0)
+    hbm = int(args.hbm_gb * (1 << 30)) // 2
+    srv_full = dvc.Server(ctx_full, hbm, args.move_budget, seed=9)
+    srv_simple = dvc.Server(ctx_simple, hbm, args.move_budget, seed=9)
+    games = selfplay.play_agents(game, (srv_full, dvc.DVC_MODE_ROLLOUT, args.move_budget),
+                                 (srv_simple, dvc.DVC_MODE_ROLLOUT, args.move_budget), args.games, root_seed=3003,
+                                 seed=11, poll_iters=args.move_budget)
+    srv_full.close()
+    srv_simple.close()
+    # search throughput of each tree on the batched roots
+    speed = {}
+    for name, cont in (("full", 1), ("simplified", 0)):
+        ctx = dvc.Context(dvc.Config(**dict(w.config_kwargs(), tree_continue=cont)), 0)
+        roots = ctx.dvc_init_states(w.root_seed, w.n_trees)
+        f = dvc.Forest(ctx, roots, [512] * w.n_trees, w.seed)
+        f.dvc_mcts_step(512)
+        f.dvc_forest_reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f.dvc_mcts_step(512)
+        b.record()
+        torch.cuda.synchronize()
+        ctx.dvc_check()
+        speed[name] = {"playouts_per_s": w.n_trees * 512 * w.playouts / (a.elapsed_time(b) * 1e-3)}
+        f.close()
+    print(json.dumps({
+        "metric": "full-tree agent win rate", "value": games["a_win_rate"], "unit": "fraction of games",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "2p24_full_vs_simplified_tree_selfplay", "games": args.games,
+                   "iterations_per_move": args.move_budget, "playouts_per_leaf": 32, "players": 2, "tiles": 24,
+                   "game": "full (a correct guess keeps the turn)"},
+        "ci95": games["ci95"], "fair_share": games["fair_share"], "games_finished": games["games_finished"],
+        "moves": games["turns"], "decisions": {"full": games["decisions_a"], "simplified": games["decisions_b"]},
+        "selfplay_decisions_per_s": games["decisions_per_s"], "search_throughput": speed,
+    }), flush=True)
+
+
 def run_scaling(args):
     """The paper's scaling sweeps (Sec. IV: simulations per second against
     CPU threads, GPU threads and warps; weak scaling) repeated for this
@@ -657,7 +708,7 @@ def main():
     ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "uneven", "serve", "selfplay", "policy", "scaling"])
+                    choices=["batched", "uneven", "serve", "selfplay", "policy", "scaling", "fulltree"])
     ap.add_argument("--train-states", type=int, default=10_000_000, help="selfplay: training states")
     ap.add_argument("--epochs", type=int, default=4, help="selfplay: training epochs")
     ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
@@ -677,10 +728,10 @@ def main():
     if args.workload == "scaling":
         run_scaling(args)
         return
-    if args.workload in ("selfplay", "policy"):
+    if args.workload in ("selfplay", "policy", "fulltree"):
         if args.hbm_gb == 64.0:
             args.hbm_gb = 4.0
-        (run_selfplay if args.workload == "selfplay" else run_policy)(args)
+        {"selfplay": run_selfplay, "policy": run_policy, "fulltree": run_fulltree}[args.workload](args)
         return
     w = BATCHED
     if args.trees or args.iterations:

@@ -71,14 +71,16 @@ extern "C" {
  * player holds; its left-to-right order is derived: numbered tiles ascend by
  * id (black before white on equal values), each joker stands after joker_gap
  * numbered tiles, and two jokers of one hand with the same gap are ordered
- * black first unless bit 0 of flags is set.  The pool is every tile of the
- * game held by nobody.
+ * black first unless bit 0 of flags is set.  Bit 1 of flags marks a seat
+ * to move that has guessed correctly this turn and may stop (the full game
+ * tree, dvc_config.tree_continue).  The pool is every tile of the game held
+ * by nobody.
  */
 typedef struct dvc_state {
     uint32_t hand[4];     /* tile bitmask per seat (unused seats 0) */
     uint32_t revealed;    /* face-up tiles */
     uint8_t joker_gap[2]; /* numbered tiles left of joker 24 / 25 in its owner's hand; 0 in the pool */
-    uint8_t flags;        /* bit 0: both jokers share owner and gap and the white one is first */
+    uint8_t flags;        /* bit 0: jokers share owner and gap, white first; bit 1: may stop (see above) */
     uint8_t cur;          /* seat to move; it has drawn and is about to guess */
     uint8_t drawn;        /* tile drawn this turn, 0xFF if the pool was empty */
     uint8_t alive;        /* bitmask of seats with a face-down tile */
@@ -101,6 +103,11 @@ typedef struct dvc_state {
  * the sorted row (jokers anywhere), uniform over the kept (slot, identity)
  * pairs in the same canonical order, one word per guess.  It changes
  * playouts only; the tree's actions stay the legal guesses.
+ * tree_continue -- 0: inside the tree a correct guess ends the turn (Sec.
+ * III-A, simplification 2); 1: the full game tree of Fig. 2a: after a correct
+ * guess that does not end the game the player keeps the turn, and its node
+ * offers STOP (action code 0xFFF, first in canonical order) beside the legal
+ * guesses; STOP passes the turn.  The same rule governs dvc_play_move.
  */
 typedef struct dvc_config {
     int32_t nplayers;         /* 2..4 */
@@ -113,6 +120,7 @@ typedef struct dvc_config {
     int32_t d_max;            /* 8 */
     int32_t playouts;         /* playouts per leaf in dvc_mcts_step (leaf parallelism) */
     int32_t policy;           /* playout guesses: 0 uniform (default), 1 ordering-aware (see above) */
+    int32_t tree_continue;    /* 0: the simplified tree (default); 1: the full game tree (see above) */
 } dvc_config;
 
 typedef struct dvc_ctx dvc_ctx;

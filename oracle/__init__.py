@@ -21,7 +21,11 @@ Pin status per function:
   legal_actions ..... pinned (88 root guesses, canonical order written out;
                       ordering-aware policy: hand-made rows written out)
   play_move ......... pinned (hand-made positions: correct and wrong guesses,
-                      elimination, empty pool, the draw that follows)
+                      elimination, empty pool, the draw that follows; STOP and
+                      a kept turn in the full game of Fig. 2a)
+  mcts, full tree ... pinned (a correct in-tree guess keeps the turn: STOP nodes
+                      below it; visit-count invariants; the playout coin at a
+                      may-stop leaf against exact enumeration)
   value_features .... pinned (hand-made positions with features written out)
   value_forward ..... pinned (closed form with zero hidden weights)
   value_loss_grad ... pinned (central finite differences in double)
@@ -49,6 +53,7 @@ class _Cfg(ctypes.Structure):
         ("d_max", ctypes.c_int32),
         ("playouts", ctypes.c_int32),
         ("policy", ctypes.c_int32),
+        ("tree_continue", ctypes.c_int32),
     ]
 
 
@@ -64,10 +69,11 @@ class OracleConfig:
     d_max: int = 8
     playouts: int = 1
     policy: int = 0
+    tree_continue: int = 0
 
     def c(self) -> _Cfg:
         return _Cfg(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
-                    self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy)
+                    self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy, self.tree_continue)
 
 
 def lib():
@@ -99,7 +105,8 @@ def lib():
         L.or_playout_trace.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_uint32, u8p, ctypes.c_int]
         L.or_playout_trace.restype = ctypes.c_int
-        L.or_play_move.argtypes = [u8p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, u8p]
+        L.or_play_move.argtypes = [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_uint32, u8p]
         L.or_play_move.restype = ctypes.c_int
         L.or_legal_actions.argtypes = [u8p, ctypes.c_int, i32p]
         L.or_legal_actions.restype = ctypes.c_int
@@ -168,11 +175,15 @@ def legal_actions(state, policy: int = 0) -> np.ndarray:
     return out[:n].copy()
 
 
-def play_move(state, code: int, seed: int, game: int, turn: int):
-    """Returns (rc, next state): rc 0 played, 1 game already over, -1 illegal guess."""
+STOP = 0xFFF  # end a turn after a correct guess (full game tree, Fig. 2a)
+
+
+def play_move(state, code: int, seed: int, game: int, turn: int, cont: int = 0):
+    """Returns (rc, next state): rc 0 played, 1 game already over, -1 illegal
+    action.  cont = 1: a correct guess keeps the turn (the player may STOP)."""
     s = _state(state)
     out = np.zeros(32, dtype=np.uint8)
-    rc = lib().or_play_move(_u8(s), int(code), seed, game, turn, _u8(out))
+    rc = lib().or_play_move(_u8(s), int(code), int(cont), seed, game, turn, _u8(out))
     return rc, out
 
 

@@ -53,12 +53,18 @@
 
 enum { TAG_INIT = 1, TAG_DET = 2, TAG_TREE = 3, TAG_ROLL = 4, TAG_PLAY = 5 };
 
+/* STOP (Fig. 2a): end a turn after a correct guess; the first of a node's
+ * actions in canonical order.  Guesses are coded seat << 10 | slot << 5 |
+ * identity. */
+enum { STOP = 0xFFF };
+
 typedef struct {
     int32_t nplayers, ntiles, deal, max_predraw, max_revealed;
     uint32_t cont_thr; /* after a correct guess in a playout: guess again iff word < cont_thr; 0 = never, no word */
     double c_uct;
     int32_t d_max, playouts;
     int32_t policy; /* playout guesses: 0 uniform over the legal guesses; 1 ordering-aware (see legal_list_policy) */
+    int32_t tree_continue; /* in the tree: 0 a correct guess ends the turn (Sec. III-A); 1 the player may go on (Fig. 2a) */
 } or_config;
 
 /* ------------------------------------------------------------------ Philox */
@@ -139,12 +145,14 @@ typedef struct {
     int owner[MAXT]; /* -1 = in the pool */
     int alive[MAXP];
     int cur, drawn, winner; /* drawn: tile drawn this turn or -1; winner -1 while running */
+    int mstop;              /* 1: cur has guessed correctly this turn and may stop or guess again */
 } ost;
 
 /* Boundary format (32 bytes, little endian): hand[4] u32 tile bitmasks at 0,
  * revealed u32 at 16, joker gaps u8[2] at 20 (numbered tiles left of each
  * joker in its owner's hand, 0 when in the pool), flags u8 at 22 (bit 0: both
- * jokers share an owner and a gap and the white one is first), cur at 23,
+ * jokers share an owner and a gap and the white one is first; bit 1: the
+ * player to move has guessed correctly this turn and may stop), cur at 23,
  * drawn at 24 (0xFF none), alive mask at 25, players at 26, tiles at 27,
  * winner at 28 (0xFF while running), zero padding 29..31. */
 static uint32_t rd32(const uint8_t* p) {
@@ -180,6 +188,7 @@ static void pack(const ost* s, uint8_t* out) {
         out[20 + j] = (uint8_t)numbered_before(s, p, jpos[j]);
     }
     if (jown[0] >= 0 && jown[0] == jown[1] && out[20] == out[21] && jpos[1] < jpos[0]) out[22] = 1;
+    if (s->mstop) out[22] |= 2;
     out[23] = (uint8_t)s->cur;
     out[24] = s->drawn < 0 ? 0xFF : (uint8_t)s->drawn;
     uint8_t al = 0;
@@ -223,6 +232,7 @@ static void unpack(const uint8_t* in, ost* s) {
     s->cur = in[23];
     s->drawn = in[24] == 0xFF ? -1 : in[24];
     s->winner = in[28] == 0xFF ? -1 : in[28];
+    s->mstop = (in[22] >> 1) & 1;
 }
 
 static int nalive(const ost* s) {
@@ -384,11 +394,46 @@ static void next_turn(ost* s, stream* rng) {
     draw_for(s, p, rng);
 }
 
+/* One action inside the tree (Sec. III-A) or one self-play move: STOP passes
+ * the turn; a guess is resolved with no playout coin, and after a correct
+ * guess that does not end the game the player keeps the turn (and may stop)
+ * when cont is set -- the full game tree of Fig. 2a -- else the turn passes. */
+static void tree_step(ost* s, int code, int cont, stream* trng) {
+    if (code == STOP) {
+        s->mstop = 0;
+        next_turn(s, trng);
+        return;
+    }
+    const int q = code >> 10, slot = (code >> 5) & 31, x = code & 31;
+    const int correct = s->seq[q][slot] == x;
+    if (resolve(s, q, slot, x, 1, 0, NULL) == GAME_OVER) {
+        s->mstop = 0;
+        return;
+    }
+    if (correct && cont) {
+        s->mstop = 1;
+        return;
+    }
+    s->mstop = 0;
+    next_turn(s, trng);
+}
+
+static int action_is_legal(const ost* s, int code) {
+    if (code == STOP) return s->mstop;
+    return guess_is_legal(s, code >> 10, (code >> 5) & 31, code & 31);
+}
+
 static _Thread_local int legal_q[MAXLEGAL], legal_s[MAXLEGAL], legal_x[MAXLEGAL];
 
 /* One random playout from a state where the player to move is about to guess
  * (Sec. II-B): uniform guesses among the legal ones until one player is left. */
 static int playout(ost s, uint32_t cont_thr, int policy, stream* rng, uint8_t* trace, int* ntrace, int maxtrace) {
+    if (s.winner >= 0) return s.winner;
+    if (s.mstop) {
+        /* after a correct guess a playout goes on iff the next word is below cont_thr */
+        s.mstop = 0;
+        if (!(cont_thr != 0u && next_word(rng) < cont_thr)) next_turn(&s, rng);
+    }
     for (;;) {
         int n = legal_list_policy(&s, policy, legal_q, legal_s, legal_x);
         int k = pick(next_word(rng), n);
@@ -811,27 +856,27 @@ int or_legal_count(const uint8_t* state) {
 }
 
 /* One move of a game played out by search agents (the workload's self-play
- * games between two leaf evaluators), under the game model the tree searches
- * (Sec. III-A, simplification 2): the seat to move makes the guess `code`
- * (seat << 10 | slot << 5 | identity) on the true state, the turn ends after
- * it whether or not it was correct, and the next seat still in draws on the
- * stream (seed, game, turn, tag 5).  Returns 0; 1 if the game was already
- * over; -1 if the guess is not legal (the state is copied unchanged). */
-int or_play_move(const uint8_t* in, int code, uint64_t seed, uint32_t game, uint32_t turn, uint8_t* out) {
+ * games), under the game model the trees search: the seat to move makes the
+ * guess `code` (seat << 10 | slot << 5 | identity) on the true state, or STOP
+ * when it may; with cont = 0 the turn ends after any guess (Sec. III-A,
+ * simplification 2), with cont = 1 a correct guess keeps the turn (Fig. 2a);
+ * when the turn passes the next seat still in draws on the stream (seed,
+ * game, turn, tag 5).  Returns 0; 1 if the game was already over; -1 if the
+ * action is not legal (the state is copied unchanged). */
+int or_play_move(const uint8_t* in, int code, int cont, uint64_t seed, uint32_t game, uint32_t turn, uint8_t* out) {
     ost s;
     unpack(in, &s);
     if (s.winner >= 0) {
         pack(&s, out);
         return 1;
     }
-    const int q = code >> 10, slot = (code >> 5) & 31, x = code & 31;
-    if (code < 0 || !guess_is_legal(&s, q, slot, x)) {
+    if (code < 0 || !action_is_legal(&s, code)) {
         pack(&s, out);
         return -1;
     }
     stream rng;
     stream_open(&rng, seed, game, 0, turn, TAG_PLAY);
-    if (resolve(&s, q, slot, x, 1, 0, NULL) != GAME_OVER) next_turn(&s, &rng);
+    tree_step(&s, code, cont, &rng);
     pack(&s, out);
     return 0;
 }
@@ -881,8 +926,9 @@ static double uct_score(double c_sqrt_lnN, int32_t w, int32_t n) {
 }
 
 static int canon_rank(int code, int cur, int P) {
+    if (code == STOP) return 0;
     int q = code >> 10;
-    return ((((q - cur - 1) % P + P) % P) << 10) | (code & 1023);
+    return 1 + (((((q - cur - 1) % P + P) % P) << 10) | (code & 1023));
 }
 
 typedef struct {
@@ -938,20 +984,19 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
         mover[np++] = obs;
         int node = 0, depth = 0;
         while (s.winner < 0 && depth < cfg->d_max) {
+            /* the node's actions in canonical order: STOP when the mover may stop, then the legal guesses */
             int n = legal_list(&s, legal_q, legal_s, legal_x);
-            int fresh = -1;
-            for (int a = 0; a < n && fresh < 0; a++) {
-                int code = (legal_q[a] << 10) | (legal_s[a] << 5) | legal_x[a];
+            int fresh_code = -1;
+            for (int a = s.mstop ? -1 : 0; a < n && fresh_code < 0; a++) {
+                int code = a < 0 ? STOP : (legal_q[a] << 10) | (legal_s[a] << 5) | legal_x[a];
                 int found = 0;
                 for (int c = t.child[node]; c >= 0; c = t.sib[c]) found |= t.action[c] == code;
-                if (!found) fresh = a;
+                if (!found) fresh_code = code;
             }
             int who = s.cur;
-            if (fresh >= 0) {
-                int code = (legal_q[fresh] << 10) | (legal_s[fresh] << 5) | legal_x[fresh];
-                int c = tree_new_node(&t, node, code);
-                if (resolve(&s, legal_q[fresh], legal_s[fresh], legal_x[fresh], 1, 0, NULL) != GAME_OVER)
-                    next_turn(&s, &trng);
+            if (fresh_code >= 0) {
+                int c = tree_new_node(&t, node, fresh_code);
+                tree_step(&s, fresh_code, cfg->tree_continue, &trng);
                 path[np] = c;
                 mover[np++] = who;
                 break;
@@ -962,15 +1007,14 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
             double best_score = 0.0;
             for (int c = t.child[node]; c >= 0; c = t.sib[c]) {
                 int code = t.action[c];
-                if (!guess_is_legal(&s, code >> 10, (code >> 5) & 31, code & 31)) continue;
+                if (!action_is_legal(&s, code)) continue;
                 double sc = uct_score(csl, t.wins[c], t.visits[c]);
                 int rank = canon_rank(code, s.cur, s.P);
                 if (best < 0 || sc > best_score || (sc == best_score && rank < best_rank)) {
                     best = c; best_score = sc; best_rank = rank;
                 }
             }
-            int code = t.action[best];
-            if (resolve(&s, code >> 10, (code >> 5) & 31, code & 31, 1, 0, NULL) != GAME_OVER) next_turn(&s, &trng);
+            tree_step(&s, t.action[best], cfg->tree_continue, &trng);
             path[np] = best;
             mover[np++] = who;
             node = best;

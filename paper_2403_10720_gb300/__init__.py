@@ -44,6 +44,7 @@ class dvc_config(ctypes.Structure):
         ("d_max", ctypes.c_int32),
         ("playouts", ctypes.c_int32),
         ("policy", ctypes.c_int32),
+        ("tree_continue", ctypes.c_int32),
     ]
 
 
@@ -60,10 +61,11 @@ class Config:
     d_max: int = 8
     playouts: int = 1
     policy: int = 0  # playout guesses: 0 uniform, 1 ordering-aware
+    tree_continue: int = 0  # 1: the full game tree (a correct in-tree guess keeps the turn)
 
     def c(self) -> dvc_config:
         return dvc_config(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
-                          self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy)
+                          self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy, self.tree_continue)
 
 
 class dvc_result(ctypes.Structure):

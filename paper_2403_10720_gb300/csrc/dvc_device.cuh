@@ -19,6 +19,12 @@ constexpr uint32_t kNumMask = 0x00FFFFFFu;  // numbered tiles 0..23
 constexpr uint32_t kJokerMask = 0x03000000u;
 constexpr uint32_t kNone = 0xFFu;
 constexpr uint32_t kTagInit = 1, kTagDet = 2, kTagTree = 3, kTagRoll = 4, kTagPlay = 5;
+// STOP (Fig. 2a): end a turn after a correct guess.  Guesses are coded
+// seat << 10 | slot << 5 | identity.
+constexpr uint32_t kStop = 0xFFFu;
+// Two-player fast path: `winner` holds kPend while a playout that began where
+// the mover may stop has still to draw its continue coin.
+constexpr uint32_t kPend = 0xFEu;
 
 // ------------------------------------------------------------------ Philox
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -58,6 +64,7 @@ struct Rng {
         left = 0;
         count = 0;
     }
+    __device__ __forceinline__ void ensure(uint32_t) {}  // next() refills by itself
     __device__ __forceinline__ void refill() {
         uint32_t a = blk, b = j, c = i, d = tw;
         philox10(a, b, c, d, k0, k1);
@@ -186,6 +193,7 @@ struct G {
     uint32_t jg0, jg1, jflag;  // joker gaps, white-first flag
     uint32_t cur, drawn, alive, winner;
     uint32_t np, tmask;
+    uint32_t mstop;  // 1: cur guessed correctly this turn and may stop (full game tree)
 
     __device__ __forceinline__ uint32_t hand(uint32_t p) const {
         uint32_t v = h0;
@@ -219,6 +227,7 @@ __device__ __forceinline__ G load_state(const dvc_state& s) {
     g.jg0 = s.joker_gap[0] <= 24 ? s.joker_gap[0] : 24u;
     g.jg1 = s.joker_gap[1] <= 24 ? s.joker_gap[1] : 24u;
     g.jflag = s.flags & 1u;
+    g.mstop = (s.flags >> 1) & 1u;
     g.cur = s.cur < g.np ? s.cur : 0u;
     g.drawn = s.drawn < 26 ? s.drawn : kNone;
     g.alive = s.alive & ((1u << g.np) - 1u);
@@ -234,7 +243,7 @@ __device__ __forceinline__ void store_state(const G& g, dvc_state& s) {
     s.revealed = g.rev;
     s.joker_gap[0] = (uint8_t)g.jg0;
     s.joker_gap[1] = (uint8_t)g.jg1;
-    s.flags = (uint8_t)g.jflag;
+    s.flags = (uint8_t)(g.jflag | (g.mstop << 1));
     s.cur = (uint8_t)g.cur;
     s.drawn = (uint8_t)g.drawn;
     s.alive = (uint8_t)g.alive;
@@ -691,6 +700,29 @@ __device__ __forceinline__ int step_2p24_ordered(uint32_t& h0, uint32_t& h1, uin
     return kTurnOver;
 }
 
+// The first step of a two-player 24-tile playout that begins where the mover
+// may stop (winner == kPend): the continue coin; on "stop" the turn passes
+// and the next mover draws, on "go on" the next step is an ordinary guess.
+template <class Q>
+__device__ __forceinline__ int step_2p24_pending(uint32_t& h0, uint32_t& h1, uint32_t& cur, uint32_t& drawn,
+                                                 uint32_t& winner, Q& r, uint32_t cont_thr,
+                                                 const unsigned long long* lut12) {
+    r.ensure(2);
+    winner = kNone;
+    if (cont_thr != 0u && r.next() < cont_thr) return kGuessAgain;
+    cur ^= 1u;
+    const uint32_t pool = kNumMask & ~(h0 | h1);
+    if (pool) {
+        const uint32_t t = nth_set12(pool, __umulhi(r.next(), __popc(pool)), lut12);
+        if (cur) h1 |= 1u << t;
+        else h0 |= 1u << t;
+        drawn = t;
+    } else {
+        drawn = kNone;
+    }
+    return kTurnOver;
+}
+
 // Is action (q, slot s, identity x) legal for the seat to move?
 __device__ __forceinline__ bool guess_legal(const G& g, uint32_t q, uint32_t s, uint32_t x) {
     if (q == g.cur || q >= g.np || !((g.alive >> q) & 1u)) return false;
@@ -702,19 +734,57 @@ __device__ __forceinline__ bool guess_legal(const G& g, uint32_t q, uint32_t s, 
     return true;
 }
 
-// In-tree transition for action code (q << 10 | s << 5 | x): resolve with no
-// extra guess, then the next seat draws on the tree stream.
-__device__ __forceinline__ void tree_apply(G& g, uint32_t code, Rng& tr) {
-    const uint32_t q = code >> 10, s = (code >> 5) & 31u, x = code & 31u;
-    const uint32_t target = seq_tile(g, q, s);
-    if (resolve(g, q, target, x, true, 0u, tr) != kGameOver) next_turn(g, tr);
+// Is `code` a legal action for the seat to move: STOP when it may stop, or a
+// legal guess?
+__device__ __forceinline__ bool action_legal(const G& g, uint32_t code) {
+    if (code == kStop) return g.mstop != 0u;
+    return guess_legal(g, code >> 10, (code >> 5) & 31u, code & 31u);
 }
 
+// In-tree transition (and self-play move) for an action: STOP passes the
+// turn; a guess is resolved with no playout coin, and after a correct guess
+// that does not end the game the player keeps the turn and may stop when
+// cont is set (the full game tree of Fig. 2a), else the turn passes; when it
+// passes, the next seat draws on the tree stream.
+__device__ __forceinline__ void tree_apply(G& g, uint32_t code, Rng& tr, bool cont = false) {
+    if (code == kStop) {
+        g.mstop = 0u;
+        next_turn(g, tr);
+        return;
+    }
+    const uint32_t q = code >> 10, s = (code >> 5) & 31u, x = code & 31u;
+    const uint32_t target = seq_tile(g, q, s);
+    if (resolve(g, q, target, x, true, 0u, tr) == kGameOver) {
+        g.mstop = 0u;
+        return;
+    }
+    if (cont && target == x) {
+        g.mstop = 1u;
+        return;
+    }
+    g.mstop = 0u;
+    next_turn(g, tr);
+}
+
+// Canonical rank of an action at a node whose mover is cur: STOP first, then
+// guesses by opponent (from cur + 1), slot, identity.
 __device__ __forceinline__ uint32_t canon_rank(uint32_t code, uint32_t cur, uint32_t np) {
+    if (code == kStop) return 0u;
     const uint32_t q = code >> 10;
     uint32_t d = q + np - cur - 1u;
     d = d >= np ? d - np : d;
-    return (d << 10) | (code & 1023u);
+    return 1u + ((d << 10) | (code & 1023u));
+}
+
+// A playout that starts where the mover may stop first draws the continue
+// coin (a playout guesses again after a correct guess iff the next word is
+// below cont_thr).
+template <class R>
+__device__ __forceinline__ void playout_begin(G& g, R& r, uint32_t cont_thr) {
+    if (!g.mstop || g.winner != kNone) return;
+    g.mstop = 0u;
+    r.ensure(4);
+    if (!(cont_thr != 0u && r.next() < cont_thr)) next_turn(g, r);
 }
 
 // ------------------------------------------------------------------- UCT

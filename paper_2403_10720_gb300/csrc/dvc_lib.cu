@@ -121,7 +121,7 @@ __global__ void init_kernel(dvc_config cfg, uint64_t seed, int n, dvc_state* out
         G g;
         g.h0 = g.h1 = g.h2 = g.h3 = 0u;
         g.rev = 0u;
-        g.jg0 = g.jg1 = g.jflag = 0u;
+        g.jg0 = g.jg1 = g.jflag = g.mstop = 0u;
         g.drawn = kNone;
         g.alive = (1u << np) - 1u;
         g.winner = kNone;
@@ -189,20 +189,20 @@ __global__ void determinize_kernel(const dvc_state* roots, int n, int observer, 
 // One self-play move per game: the guess actions[i] on the true state, then
 // the next seat's draw on stream (seed, game id, turn, tag 5).
 __global__ void play_move_kernel(dvc_state* states, int n, const int32_t* actions, uint64_t seed,
-                                 const uint32_t* game_ids, uint32_t turn, int32_t* flags) {
+                                 const uint32_t* game_ids, uint32_t turn, bool cont, int32_t* flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t code = actions[i];
     G g = load_state(states[i]);
     if (code < 0 || g.winner != kNone) return;  // no move, or the game is over
-    const uint32_t c = (uint32_t)code, q = c >> 10, s = (c >> 5) & 31u, x = c & 31u;
-    if (q > 3u || !guess_legal(g, q, s, x)) {
+    const uint32_t c = (uint32_t)code;
+    if (c > kStop || !action_legal(g, c)) {
         atomicCAS(&flags[0], 0, DVC_E_INVALID);
         return;
     }
     Rng tr;
     tr.open(seed, game_ids ? game_ids[i] : (uint32_t)i, 0u, turn, kTagPlay);
-    tree_apply(g, c, tr);
+    tree_apply(g, c, tr, cont);
     store_state(g, states[i]);
 }
 
@@ -229,6 +229,7 @@ __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uin
             G g = load_state(ls);
             WordQueue r;
             r.open(seed, tree_ids[l], (uint32_t)j, leaf_ids[l], kTagRoll);
+            playout_begin(g, r, cont_thr);
             winner = kNone;
             for (int guard = 0; guard < 128; ++guard) {
                 r.ensure(4);
@@ -282,7 +283,7 @@ __global__ void mcts_select_kernel(ForestDev F, SearchParams sp, int n, Descent*
 }
 
 __global__ void mcts_expand_kernel(ForestDev F, int n, Descent* work, int32_t* paths, uint8_t* movers,
-                                   dvc_state* leaves, uint32_t* leaf_tree, uint32_t* leaf_iter) {
+                                   dvc_state* leaves, uint32_t* leaf_tree, uint32_t* leaf_iter, bool cont) {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= n) return;
     const uint32_t lane = threadIdx.x & 31u;
@@ -304,7 +305,7 @@ __global__ void mcts_expand_kernel(ForestDev F, int n, Descent* work, int32_t* p
     bool ok = true;
     if (d.found)
         ok = expand_child(d, F.nodes + tm.node_off, F.link + tm.node_off, F.created + tm.node_off, tm, next_free,
-                          used, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax);
+                          used, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, cont);
     if (lane == 0) {
         tmr.next_free = next_free;
         tmr.used = used;
@@ -531,6 +532,7 @@ SearchParams params_of(const dvc_forest* f) {
     sp.playouts = f->ctx->cfg.playouts;
     sp.cont_thr = f->ctx->cfg.cont_thr;
     sp.policy = f->ctx->cfg.policy;
+    sp.tree_continue = f->ctx->cfg.tree_continue;
     return sp;
 }
 
@@ -551,6 +553,7 @@ int dvc_create(dvc_ctx** out, const dvc_config* cfg, int device) {
         return DVC_E_INVALID;
     if (!(cfg->c_uct >= 0.0)) return DVC_E_INVALID;
     if (cfg->policy != 0 && cfg->policy != 1) return DVC_E_INVALID;
+    if (cfg->tree_continue != 0 && cfg->tree_continue != 1) return DVC_E_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -691,7 +694,7 @@ int dvc_play_move(dvc_ctx* c, dvc_state* d_states, int n, const int32_t* d_actio
         return fail(c, DVC_E_INVALID, "dvc_play_move: pointers must be device memory");
     if (int rc = set_device(c)) return rc;
     play_move_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_states, n, d_actions, seed, d_game_ids, turn,
-                                                                         c->d_flags);
+                                                                         c->cfg.tree_continue != 0, c->d_flags);
     return check_launch(c, "play_move_kernel");
 }
 
@@ -1238,7 +1241,8 @@ int dvc_mcts_expand(dvc_forest* f, void* stream) {
     if (!f) return DVC_E_INVALID;
     if (int rc = set_device(f->ctx)) return rc;
     mcts_expand_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
-        dev_of(f), f->n, f->work, f->paths, f->movers, f->leaves, f->leaf_tree, f->leaf_iter);
+        dev_of(f), f->n, f->work, f->paths, f->movers, f->leaves, f->leaf_tree, f->leaf_iter,
+        f->ctx->cfg.tree_continue != 0);
     return check_launch(f->ctx, "mcts_expand_kernel");
 }
 

@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(128)
             d, tree0);
     bool ok = true;
     int32_t next_free = tm.next_free, used = tm.used;
-    if (d.found) ok = expand_child(d, nodes, link, F.created + tm.node_off, tm, next_free, used, it, path, mover);
+    if (d.found)
+        ok = expand_child(d, nodes, link, F.created + tm.node_off, tm, next_free, used, it, path, mover,
+                          sp.tree_continue != 0);
     if (lane == 0) {
         tmr.next_free = next_free;
         tmr.used = used;
@@ -209,17 +211,18 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         k = Pp > 1u ? __umulhi(p, mP) : p;
         if (k * Pp > p) --k;
         const dvc_state& ls = s_leaf[k];
+        r.open(sp.seed, s_tid[k], p - k * Pp, s_it[k], kTagRoll);
         if constexpr (FAST2) {
             h0 = ls.hand[0];
             h1 = ls.hand[1];
             rev = ls.revealed;
             cur = ls.cur;
             drawn = ls.drawn;
-            winner = kNone;
+            winner = (ls.flags & 2u) ? kPend : kNone;  // may stop: continue coin first
         } else {
             g = load_state(ls);
+            playout_begin(g, r, sp.cont_thr);
         }
-        r.open(sp.seed, s_tid[k], p - k * Pp, s_it[k], kTagRoll);
         steps = 0;
     };
     // the lanes in `want` take consecutive playout indices (all lanes call)
@@ -241,7 +244,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         if (busy) {
             int res;
             if constexpr (FAST2) {
-                if constexpr (ORD)
+                if (winner == kPend)
+                    res = step_2p24_pending(h0, h1, cur, drawn, winner, r, sp.cont_thr, s_lut12);
+                else if constexpr (ORD)
                     res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);
                 else
                     res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);

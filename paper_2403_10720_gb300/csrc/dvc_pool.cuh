@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(MAXT, 1)
             bool ok = true;
             if (d.found) {
                 int32_t next_free = tm.next_free, used = tm.used;
-                ok = expand_child(d, nodes, link, created, tm, next_free, used, it, path, mover);
+                ok = expand_child(d, nodes, link, created, tm, next_free, used, it, path, mover, sp.tree_continue != 0);
                 if (lane == 0) {
                     tm.next_free = next_free;
                     tm.used = used;
@@ -176,17 +176,18 @@ __global__ void __launch_bounds__(MAXT, 1)
                 const int k = p / P;
                 slot = s_misc[4 * k + 3];
                 const dvc_state& ls = s_leaf[slot];
+                r.open(sp.seed, s_tm[slot].tree_id, (uint32_t)(p - k * P), (uint32_t)s_tm[slot].done, kTagRoll);
                 if constexpr (FAST2) {
                     h0 = ls.hand[0];
                     h1 = ls.hand[1];
                     rev = ls.revealed;
                     cur = ls.cur;
                     drawn = ls.drawn;
-                    winner = kNone;
+                    winner = (ls.flags & 2u) ? kPend : kNone;  // may stop: continue coin first
                 } else {
                     g = load_state(ls);
+                    playout_begin(g, r, sp.cont_thr);
                 }
-                r.open(sp.seed, s_tm[slot].tree_id, (uint32_t)(p - k * P), (uint32_t)s_tm[slot].done, kTagRoll);
                 steps = 0;
             };
             int p = atomicAdd(&cnt[1], 1);
@@ -196,7 +197,9 @@ __global__ void __launch_bounds__(MAXT, 1)
                 if (busy) {
                     int res;
                     if constexpr (FAST2) {
-                        if constexpr (ORD)
+                        if (winner == kPend)
+                            res = step_2p24_pending(h0, h1, cur, drawn, winner, r, sp.cont_thr, s_lut12);
+                        else if constexpr (ORD)
                             res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);
                         else
                             res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);

@@ -45,7 +45,8 @@ struct SearchParams {
     int32_t d_max;
     int32_t playouts;
     uint32_t cont_thr;
-    int32_t policy;  // playout guesses: 0 uniform, 1 ordering-aware
+    int32_t policy;         // playout guesses: 0 uniform, 1 ordering-aware
+    int32_t tree_continue;  // 1: a correct in-tree guess keeps the turn (Fig. 2a)
 };
 
 __device__ __forceinline__ uint32_t block_size(uint32_t k, bool is_root, uint32_t root_legal) {
@@ -110,6 +111,7 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         uint32_t best_code = 0;
         int32_t blk = nd.child;
         uint32_t seen = 0, k = 0;
+        bool stop_child = false;  // this lane saw the node's STOP child
         d.last_blk = -1;
         d.last_size = 0;
         d.last_cnt = 0;
@@ -122,8 +124,9 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
                 const double2 u = ucb[blk + (int32_t)e];  // set by the child's first backprop
                 const uint32_t code = ch.meta & 0xFFFu;
                 const uint32_t q = code >> 10, sl = (code >> 5) & 31u, x = code & 31u;
-                if (sl < 26u) atomicOr(&E[q * 26u + sl], 1u << x);
-                if (guess_legal(d.s, q, sl, x)) {
+                stop_child |= code == kStop;
+                if (code != kStop && sl < 26u) atomicOr(&E[q * 26u + sl], 1u << x);
+                if (action_legal(d.s, code)) {
                     const double sc = __dadd_rn(u.x, __dmul_rn(csl, u.y));
                     const uint32_t rk = canon_rank(code, cur, d.s.np);
                     if (best_slot < 0 || sc > best_sc || (sc == best_sc && rk < best_rank)) {
@@ -144,9 +147,13 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         d.nblocks = (int32_t)k;
         d.nchild = (int32_t)nchild;
         __syncwarp();
-        // first legal action without a child, canonical order
+        // first legal action without a child, canonical order (STOP first)
         uint32_t act = 0;
         bool found = false;
+        if (d.s.mstop && !__any_sync(0xFFFFFFFFu, stop_child)) {
+            act = kStop;
+            found = true;
+        }
         for (uint32_t off = 1; off < d.s.np && !found; ++off) {
             uint32_t q = cur + off;
             q = q >= d.s.np ? q - d.s.np : q;
@@ -191,7 +198,7 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
             }
         }
         const uint32_t who = d.s.cur;
-        tree_apply(d.s, best_code, d.tr);
+        tree_apply(d.s, best_code, d.tr, sp.tree_continue != 0);
         if (lane == 0) {
             path[d.np] = best_slot;
             mover[d.np] = (uint8_t)who;
@@ -207,7 +214,7 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
 // (uniform register copy).  Returns false if the arena is exhausted.
 __device__ __forceinline__ bool expand_child(Descent& d, Node* nodes, int32_t* link, int32_t* created,
                                              const TreeMeta& tm, int32_t& next_free, int32_t& used, uint32_t it,
-                                             int32_t* path, uint8_t* mover) {
+                                             int32_t* path, uint8_t* mover, bool cont) {
     const uint32_t lane = threadIdx.x & 31u;
     int32_t slot;
     if (d.nchild == 0 || d.last_cnt >= d.last_size) {
@@ -238,7 +245,7 @@ __device__ __forceinline__ bool expand_child(Descent& d, Node* nodes, int32_t* l
         path[d.np] = slot;
         mover[d.np] = (uint8_t)d.s.cur;
     }
-    tree_apply(d.s, d.act, d.tr);
+    tree_apply(d.s, d.act, d.tr, cont);
     d.np++;
     d.node = slot;
     ++used;

@@ -16,11 +16,13 @@ from functools import lru_cache
 from itertools import permutations
 
 
-def exact_win_probs(hands, revealed, cur, drawn, ntiles, p_cont, ordered=False):
+def exact_win_probs(hands, revealed, cur, drawn, ntiles, p_cont, ordered=False, may_stop=False):
     """hands: list of left-to-right tile lists; revealed: set.  The player to
     move is about to guess.  ordered: guesses restricted to identities that
     fit between the slot's nearest face-up numbered neighbours (jokers fit
-    anywhere).  Returns {player: Fraction}."""
+    anywhere).  may_stop: the player to move has just guessed correctly, so
+    with probability p_cont it guesses again and otherwise the turn passes.
+    Returns {player: Fraction}."""
     P = len(hands)
     p_cont = Fraction(p_cont)
     init = (tuple(tuple(h) for h in hands), frozenset(revealed),
@@ -118,6 +120,13 @@ def exact_win_probs(hands, revealed, cur, drawn, ntiles, p_cont, ordered=False):
         return acc
 
     hs, rv, alive, c, dr = init
+    if may_stop:
+        acc = {}
+        if p_cont > 0:
+            merge(acc, guess(hs, rv, alive, c, dr), p_cont)
+        if p_cont < 1:
+            merge(acc, new_turn(hs, rv, alive, c), 1 - p_cont)
+        return acc
     return guess(hs, rv, alive, c, dr)
 
 

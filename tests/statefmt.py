@@ -6,7 +6,8 @@ invariant checks.  No game rule lives here.
 
 Layout: hand[4] u32 tile bitmasks (bytes 0..15), revealed u32 (16..19),
 joker gaps u8[2] (20, 21: numbered tiles left of joker 24 / 25 in its owner's
-hand), flags u8 (22, bit 0: jokers share owner and gap and 25 comes first),
+hand), flags u8 (22, bit 0: jokers share owner and gap and 25 comes first;
+bit 1: the player to move guessed correctly this turn and may stop),
 cur (23), drawn (24, 0xFF none), alive mask (25), players (26), tiles (27),
 winner (28, 0xFF running), padding (29..31).
 """
@@ -15,7 +16,7 @@ import numpy as np
 JB, JW = 24, 25
 
 
-def encode(hands, revealed, cur, drawn=None, ntiles=24, alive=None, winner=None):
+def encode(hands, revealed, cur, drawn=None, ntiles=24, alive=None, winner=None, may_stop=False):
     """hands: list of per-player left-to-right tile-id lists; revealed: set of ids."""
     P = len(hands)
     b = np.zeros(32, dtype=np.uint8)
@@ -40,6 +41,8 @@ def encode(hands, revealed, cur, drawn=None, ntiles=24, alive=None, winner=None)
             b[20 + j] = sum(1 for u in h[:pos[t]] if u < 24)
     if JB in owner and JW in owner and owner[JB] == owner[JW] and b[20] == b[21] and pos[JW] < pos[JB]:
         b[22] = 1
+    if may_stop:
+        b[22] |= 2
     b[23] = cur
     b[24] = 0xFF if drawn is None else drawn
     if alive is None:
@@ -81,4 +84,5 @@ def decode(b):
         "P": P,
         "T": T,
         "winner": None if b[28] == 0xFF else int(b[28]),
+        "may_stop": bool(b[22] & 2),
     }

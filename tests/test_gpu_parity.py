@@ -364,3 +364,46 @@ def test_mcts_ordered_policy_bit_exact(dvc, variant, shape):
     ctx.dvc_check()
     want = _oracle_trees(ocfg, oroots, 6, budgets, range(n))
     _check_forest(forest, stats, want, range(n))
+
+
+# ---------------------------------------------------------------- full game tree (Fig. 2a)
+
+@pytest.mark.parametrize("variant,shape", [("2p24", (1, 0, 0, 0)), ("2p24", (2, 2, 8, 2)), ("4p26j", (1, 0, 0, 0)),
+                                           ("4p26j", (2, 2, 4, 2))])
+def test_mcts_full_tree_bit_exact(dvc, variant, shape):
+    kw = dict(VARIANTS[variant], playouts=16, tree_continue=1)
+    ocfg = oracle.OracleConfig(**kw)
+    n = 5
+    budgets = [100, 30, 1, 80, 66]
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(35, n)
+    oroots = oracle.init_states(ocfg, 35, n)
+    forest = dvc.Forest(ctx, roots, budgets, 8)
+    forest.dvc_forest_tune(*shape)
+    forest.dvc_mcts_step(max(budgets))
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    want = _oracle_trees(ocfg, oroots, 8, budgets, range(n))
+    _check_forest(forest, stats, want, range(n))
+    if variant == "2p24":   # with two players a correct in-tree guess is common: STOP nodes were built
+        assert any((want[t][0][:, 0] == oracle.STOP).any() for t in range(n))
+
+
+@pytest.mark.parametrize("variant", ["2p24", "4p26j"])
+def test_rollout_from_may_stop_leaves_bit_exact(dvc, variant):
+    kw = VARIANTS[variant]
+    ocfg = oracle.OracleConfig(**kw)
+    leaves = oracle.init_states(ocfg, 16, 40)
+    leaves[::2, 22] |= 2    # every other leaf: the mover has just guessed right and may stop
+    n = len(leaves)
+    ids = np.arange(n, dtype=np.uint32)
+    ctx = _ctx(dvc, **kw)
+    words = torch.zeros(1, dtype=torch.int64, device="cuda")
+    wins = ctx.dvc_rollout_batch(torch.from_numpy(leaves).cuda(), 29, 51, _u32(ids), _u32(ids), words=words)
+    wins = wins.cpu().numpy()
+    total = 0
+    for i in range(n):
+        w, wd = oracle.rollout(ocfg, leaves[i], 29, 51, i, i)
+        assert (wins[i] == w).all(), i
+        total += wd
+    assert int(words.item()) == total

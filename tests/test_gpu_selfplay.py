@@ -121,3 +121,36 @@ def test_move_agreement_fractions(dvc):
     for k in ("value_vs_strong", "rollout_vs_strong", "value_vs_rollout"):
         assert 0.0 <= ag[k] <= 1.0
     assert ag["positions"] == 64
+
+
+@pytest.mark.parametrize("variant", ["2p24", "4p26j"])
+def test_play_move_full_game_bit_exact(dvc, variant):
+    """The full game (Fig. 2a): a correct guess keeps the turn and STOP passes
+    it; random actions, STOP included when allowed, match the oracle."""
+    kw = dict(VARIANTS[variant], tree_continue=1)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    n, seed = 200, 0x51
+    states = ctx.dvc_init_states(43, n)
+    want = oracle.init_states(oracle.OracleConfig(**kw), 43, n)
+    rng = np.random.default_rng(9)
+    stops = 0
+    for turn in range(120):
+        act = np.full(n, -1, dtype=np.int32)
+        for g in range(n):
+            if want[g][28] != 0xFF:
+                continue
+            legal = oracle.legal_actions(want[g]).tolist()
+            if want[g][22] & 2:
+                legal.append(oracle.STOP)
+            act[g] = legal[rng.integers(len(legal))]
+            stops += int(act[g] == oracle.STOP)
+        ctx.dvc_play_move(states, torch.from_numpy(act).cuda(), seed, turn)
+        for g in range(n):
+            if act[g] >= 0:
+                rc, want[g] = oracle.play_move(want[g], int(act[g]), seed, g, turn, cont=1)
+                assert rc == 0
+        ctx.dvc_check()
+        assert (states.cpu().numpy() == want).all(), turn
+        if (want[:, 28] != 0xFF).all():
+            break
+    assert stops > 0
