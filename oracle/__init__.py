@@ -23,6 +23,9 @@ Pin status per function:
   play_move ......... pinned (hand-made positions: correct and wrong guesses,
                       elimination, empty pool, the draw that follows; STOP and
                       a kept turn in the full game of Fig. 2a)
+  mcts, vanilla ..... pinned (plausible-set nodes against the determinizer's
+                      samples: count, creation order, visits; the decision
+                      summed over sets)
   mcts, full tree ... pinned (a correct in-tree guess keeps the turn: STOP nodes
                       below it; visit-count invariants; the playout coin at a
                       may-stop leaf against exact enumeration)
@@ -54,6 +57,7 @@ class _Cfg(ctypes.Structure):
         ("playouts", ctypes.c_int32),
         ("policy", ctypes.c_int32),
         ("tree_continue", ctypes.c_int32),
+        ("vanilla", ctypes.c_int32),
     ]
 
 
@@ -70,10 +74,12 @@ class OracleConfig:
     playouts: int = 1
     policy: int = 0
     tree_continue: int = 0
+    vanilla: int = 0
 
     def c(self) -> _Cfg:
         return _Cfg(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
-                    self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy, self.tree_continue)
+                    self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy, self.tree_continue,
+                    self.vanilla)
 
 
 def lib():
@@ -176,6 +182,7 @@ def legal_actions(state, policy: int = 0) -> np.ndarray:
 
 
 STOP = 0xFFF  # end a turn after a correct guess (full game tree, Fig. 2a)
+SET = 0xFFE   # a plausible-number-set node of vanilla MCTS-dvc (Sec. III-A)
 
 
 def play_move(state, code: int, seed: int, game: int, turn: int, cont: int = 0):

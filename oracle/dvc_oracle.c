@@ -58,6 +58,11 @@ enum { TAG_INIT = 1, TAG_DET = 2, TAG_TREE = 3, TAG_ROLL = 4, TAG_PLAY = 5 };
  * identity. */
 enum { STOP = 0xFFF };
 
+/* SET: a plausible-number-set node of vanilla MCTS-dvc (Sec. III-A): a child
+ * of the root standing for one assignment of the tiles the observer cannot
+ * see. */
+enum { SET = 0xFFE };
+
 typedef struct {
     int32_t nplayers, ntiles, deal, max_predraw, max_revealed;
     uint32_t cont_thr; /* after a correct guess in a playout: guess again iff word < cont_thr; 0 = never, no word */
@@ -65,6 +70,7 @@ typedef struct {
     int32_t d_max, playouts;
     int32_t policy; /* playout guesses: 0 uniform over the legal guesses; 1 ordering-aware (see legal_list_policy) */
     int32_t tree_continue; /* in the tree: 0 a correct guess ends the turn (Sec. III-A); 1 the player may go on (Fig. 2a) */
+    int32_t vanilla; /* 1: the root's children are plausible-number sets (vanilla MCTS-dvc, Sec. III-A) */
 } or_config;
 
 /* ------------------------------------------------------------------ Philox */
@@ -934,7 +940,22 @@ static int canon_rank(int code, int cur, int P) {
 typedef struct {
     int n, cap;
     int32_t *action, *parent, *visits, *wins, *child, *sib, *last;
+    uint64_t* key; /* SET nodes: the assignment they stand for (set_key) */
 } otree;
+
+/* The plausible-number set of a determinization seen by observer obs: every
+ * other seat's hand (bitmask), then the joker gaps and the white-first flag,
+ * in two words. */
+static void set_key(const ost* s, int obs, uint64_t key[2]) {
+    uint8_t b[32];
+    pack(s, b);
+    uint64_t h[3] = {0, 0, 0};
+    int k = 0;
+    for (int p = 0; p < s->P; p++)
+        if (p != obs) h[k++] = rd32(b + 4 * p);
+    key[0] = h[0] | (h[1] << 32);
+    key[1] = h[2] | ((uint64_t)b[20] << 32) | ((uint64_t)b[21] << 40) | ((uint64_t)(b[22] & 1u) << 48);
+}
 
 static int tree_new_node(otree* t, int parent, int code) {
     int id = t->n++;
@@ -968,7 +989,8 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
     t.cap = budget + 1;
     t.n = 0;
     int32_t* mem = (int32_t*)malloc(sizeof(int32_t) * 7 * (size_t)t.cap);
-    if (!mem) return -1;
+    t.key = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (size_t)t.cap);
+    if (!mem || !t.key) { free(mem); free(t.key); return -1; }
     t.action = mem; t.parent = mem + t.cap; t.visits = mem + 2 * t.cap; t.wins = mem + 3 * t.cap;
     t.child = mem + 4 * t.cap; t.sib = mem + 5 * t.cap; t.last = mem + 6 * t.cap;
     tree_new_node(&t, -1, 0);
@@ -983,6 +1005,25 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
         path[np] = 0;
         mover[np++] = obs;
         int node = 0, depth = 0;
+        if (cfg->vanilla) {
+            /* the root's child for this determinization's plausible set, or
+             * a new one (this iteration's expansion; its leaf is the root
+             * determinized) */
+            uint64_t key[2];
+            set_key(&s, obs, key);
+            int c = t.child[0];
+            while (c >= 0 && !(t.key[2 * c] == key[0] && t.key[2 * c + 1] == key[1])) c = t.sib[c];
+            int fresh = c < 0;
+            if (fresh) {
+                c = tree_new_node(&t, 0, SET);
+                t.key[2 * c] = key[0];
+                t.key[2 * c + 1] = key[1];
+            }
+            path[np] = c;
+            mover[np++] = obs;
+            node = c;
+            if (fresh) depth = cfg->d_max; /* no descent below a node created in this iteration */
+        }
         while (s.winner < 0 && depth < cfg->d_max) {
             /* the node's actions in canonical order: STOP when the mover may stop, then the legal guesses */
             int n = legal_list(&s, legal_q, legal_s, legal_x);
@@ -1043,7 +1084,7 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
             }
         }
         if (n_nodes_out) *n_nodes_out = t.n;
-        if (best_out) {
+        if (best_out && !cfg->vanilla) {
             /* decision: most visits, ties to the lowest canonical rank */
             int best = -1;
             for (int c = t.child[0]; c >= 0; c = t.sib[c]) {
@@ -1056,9 +1097,31 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
             best_out[1] = best < 0 ? 0 : t.visits[best];
             best_out[2] = best < 0 ? 0 : t.wins[best];
             best_out[3] = t.visits[0];
+        } else if (best_out) {
+            /* vanilla: an action's visits and wins summed over every plausible set */
+            static _Thread_local int32_t av[4096], aw[4096];
+            memset(av, 0, sizeof(av));
+            memset(aw, 0, sizeof(aw));
+            for (int c = t.child[0]; c >= 0; c = t.sib[c])
+                for (int g = t.child[c]; g >= 0; g = t.sib[g]) {
+                    av[t.action[g]] += t.visits[g];
+                    aw[t.action[g]] += t.wins[g];
+                }
+            int best = -1;
+            for (int a = 0; a < 4096; a++) {
+                if (av[a] == 0) continue;
+                if (best < 0 || av[a] > av[best] ||
+                    (av[a] == av[best] && canon_rank(a, obs, root.P) < canon_rank(best, obs, root.P)))
+                    best = a;
+            }
+            best_out[0] = best;
+            best_out[1] = best < 0 ? 0 : av[best];
+            best_out[2] = best < 0 ? 0 : aw[best];
+            best_out[3] = t.visits[0];
         }
     }
     free(mem);
+    free(t.key);
     return rc;
 }
 
