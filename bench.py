@@ -593,6 +593,70 @@ def run_fulltree(args):
     }), flush=True)
 
 
+def run_vanilla(args):
+    """Vanilla MCTS-dvc (the root's children are plausible-number sets, Sec.
+    III-A) against the paper's MCTS-dvc on two-player 24-tile positions: how
+    the root's statistics spread over sets, search throughput, agreement with
+    a strong MCTS-dvc search (16x the iterations), and games between the two
+    agents at equal iteration budgets (one line of JSON)."""
+    import numpy as np
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build, selfplay
+    build.build()
+    w = BATCHED
+    B = args.move_budget
+    E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    positions = {}
+    for pos, mp in (("opening", 0), ("mid_game", w.config_kwargs()["max_predraw"])):
+        kw = dict(w.config_kwargs(), max_predraw=mp)
+        res = {}
+        ctx0 = dvc.Context(dvc.Config(**kw), 0)
+        roots = ctx0.dvc_init_states(w.root_seed, w.n_trees)
+        strong = dvc.Forest(ctx0, roots, [16 * B] * w.n_trees, w.seed + 1)
+        strong.dvc_mcts_step(16 * B)
+        ref = strong.dvc_root_stats()[:, 0].cpu().numpy()
+        strong.close()
+        for name, van in (("vanilla", 1), ("mcts_dvc", 0)):
+            ctx = dvc.Context(dvc.Config(**dict(kw, vanilla=van)), 0)
+            f = dvc.Forest(ctx, roots, [B] * w.n_trees, w.seed)
+            f.dvc_mcts_step(B)
+            f.dvc_forest_reset()
+            torch.cuda.synchronize()
+            a, b = E(), E()
+            a.record()
+            f.dvc_mcts_step(B)
+            b.record()
+            torch.cuda.synchronize()
+            st = f.dvc_root_stats().cpu().numpy().astype(np.int64)
+            ctx.dvc_check()
+            f.close()
+            res[name] = {
+                "playouts_per_s": w.n_trees * B * w.playouts / (a.elapsed_time(b) * 1e-3),
+                "root_children_mean": float(st[:, 4].mean()),
+                "root_children_max": int(st[:, 4].max()),
+                "visits_per_root_child": float((st[:, 3] / np.maximum(st[:, 4], 1)).mean()),
+                "best_action_visit_share": float((st[:, 1] / np.maximum(st[:, 3], 1)).mean()),
+                "agreement_with_strong_mcts_dvc": float((st[:, 0] == ref).mean()),
+            }
+        positions[pos] = res
+    kw = dict(w.config_kwargs(), playouts=32, max_predraw=0)
+    game = dvc.Context(dvc.Config(**kw), 0)
+    van = dvc.Context(dvc.Config(**dict(kw, vanilla=1)), 0)
+    games = selfplay.play_forest_agents(game, (van, B), (game, B), args.games, root_seed=3003, seed=11)
+    print(json.dumps({
+        "metric": "vanilla agent win rate", "value": games["a_win_rate"], "unit": "fraction of games",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "2p24_vanilla_vs_mcts_dvc", "games": args.games, "iterations_per_move": B,
+                   "playouts_per_leaf_games": 32, "trees_per_position_kind": w.n_trees,
+                   "playouts_per_leaf_search": w.playouts, "strong_iterations": 16 * B, "players": 2, "tiles": 24},
+        "ci95": games["ci95"], "fair_share": games["fair_share"], "games_finished": games["games_finished"],
+        "moves": games["turns"], "decisions": {"vanilla": games["decisions_a"], "mcts_dvc": games["decisions_b"]},
+        "selfplay_decisions_per_s": games["decisions_per_s"], "positions": positions,
+    }), flush=True)
+
+
 def run_scaling(args):
     """The paper's scaling sweeps (Sec. IV: simulations per second against
     CPU threads, GPU threads and warps; weak scaling) repeated for this
@@ -708,7 +772,7 @@ def main():
     ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "uneven", "serve", "selfplay", "policy", "scaling", "fulltree"])
+                    choices=["batched", "uneven", "serve", "selfplay", "policy", "scaling", "fulltree", "vanilla"])
     ap.add_argument("--train-states", type=int, default=10_000_000, help="selfplay: training states")
     ap.add_argument("--epochs", type=int, default=4, help="selfplay: training epochs")
     ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
@@ -728,10 +792,11 @@ def main():
     if args.workload == "scaling":
         run_scaling(args)
         return
-    if args.workload in ("selfplay", "policy", "fulltree"):
+    if args.workload in ("selfplay", "policy", "fulltree", "vanilla"):
         if args.hbm_gb == 64.0:
             args.hbm_gb = 4.0
-        {"selfplay": run_selfplay, "policy": run_policy, "fulltree": run_fulltree}[args.workload](args)
+        {"selfplay": run_selfplay, "policy": run_policy, "fulltree": run_fulltree,
+         "vanilla": run_vanilla}[args.workload](args)
         return
     w = BATCHED
     if args.trees or args.iterations:

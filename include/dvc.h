@@ -108,6 +108,16 @@ typedef struct dvc_state {
  * guess that does not end the game the player keeps the turn, and its node
  * offers STOP (action code 0xFFF, first in canonical order) beside the legal
  * guesses; STOP passes the turn.  The same rule governs dvc_play_move.
+ * vanilla -- 0: the paper's MCTS-dvc tree, whose root's children are the
+ * guesses (Sec. III-A); 1: vanilla MCTS-dvc, the baseline Sec. III-A sets it
+ * against: the root's children are plausible-number sets (action code 0xFFE),
+ * one per distinct assignment of the tiles the observer cannot see (every
+ * other seat's hand with its jokers' places); each iteration enters the set
+ * of its determinization, and a set not seen before is that iteration's
+ * expansion, scored from the determinized root.  Below a set the tree is the
+ * usual guess tree (d_max counts plies below the set).  The decision sums
+ * each action's visits and wins over all sets (dvc_root_stats).  Forests
+ * only: dvc_server_create returns DVC_E_UNSUPPORTED.
  */
 typedef struct dvc_config {
     int32_t nplayers;         /* 2..4 */
@@ -121,6 +131,7 @@ typedef struct dvc_config {
     int32_t playouts;         /* playouts per leaf in dvc_mcts_step (leaf parallelism) */
     int32_t policy;           /* playout guesses: 0 uniform (default), 1 ordering-aware (see above) */
     int32_t tree_continue;    /* 0: the simplified tree (default); 1: the full game tree (see above) */
+    int32_t vanilla;          /* 0: MCTS-dvc (default); 1: plausible-set root children (see above) */
 } dvc_config;
 
 typedef struct dvc_ctx dvc_ctx;
@@ -199,7 +210,9 @@ int dvc_play_move(dvc_ctx* ctx, dvc_state* d_states, int n, const int32_t* d_act
  * streams keyed (seed, h_tree_ids ? h_tree_ids[t] : t).  d_roots is copied
  * on `stream`; h_budgets and h_tree_ids are host arrays read during the call.
  * Device memory per tree: a node arena of 641 + 4 * budget 48-byte slots
- * (node 16 B, cached UCB1 terms 24 B, child link 4 B, creation stamp 4 B), a
+ * (node 16 B, cached UCB1 terms 24 B, child link 4 B, creation stamp 4 B;
+ * vanilla: 1 + 5 * budget slots, plus a plausible-set table of 2 * budget
+ * 20-byte cells), a
  * determinization table of 2,048 cells (2 players) or 32,768 cells (3-4
  * players) of 8 bytes, and 64 determinized roots with the first block of
  * their in-tree random streams (3 KB) sampled ahead by engine 2.  The root
@@ -277,7 +290,8 @@ int dvc_forest_leaves(dvc_forest* f, dvc_state** d_leaves, uint32_t** d_tree_ids
  * -- best action (most visits, ties to the lowest canonical action; -1 if
  * none), its visits, its wins, root visits, root children, nodes used,
  * iterations done, 0.  Action code = seat << 10 | slot << 5 | identity.
- * d_out: n_trees x 8 int32.
+ * Vanilla trees: an action's visits and wins are summed over the plausible
+ * sets, and root children counts the sets.  d_out: n_trees x 8 int32.
  */
 int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream);
 
@@ -364,7 +378,7 @@ int dvc_gemm_bf16(dvc_ctx* ctx, const void* d_A, const void* d_B, const float* d
  * value network), so admission is by memory.  A query's search is keyed by
  * (seed, low 32 bits of its id) and runs exactly as it would alone: results do
  * not depend on what else is resident.  Host-side calls; poll synchronises
- * the server's own stream.
+ * the server's own stream.  A vanilla context returns DVC_E_UNSUPPORTED.
  */
 typedef struct dvc_server dvc_server;
 typedef struct dvc_result {

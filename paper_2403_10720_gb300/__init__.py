@@ -45,6 +45,7 @@ class dvc_config(ctypes.Structure):
         ("playouts", ctypes.c_int32),
         ("policy", ctypes.c_int32),
         ("tree_continue", ctypes.c_int32),
+        ("vanilla", ctypes.c_int32),
     ]
 
 
@@ -62,10 +63,12 @@ class Config:
     playouts: int = 1
     policy: int = 0  # playout guesses: 0 uniform, 1 ordering-aware
     tree_continue: int = 0  # 1: the full game tree (a correct in-tree guess keeps the turn)
+    vanilla: int = 0  # 1: the root's children are plausible-number sets (vanilla MCTS-dvc)
 
     def c(self) -> dvc_config:
         return dvc_config(self.nplayers, self.ntiles, self.deal, self.max_predraw, self.max_revealed,
-                          self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy, self.tree_continue)
+                          self.cont_thr, self.c_uct, self.d_max, self.playouts, self.policy, self.tree_continue,
+                          self.vanilla)
 
 
 class dvc_result(ctypes.Structure):

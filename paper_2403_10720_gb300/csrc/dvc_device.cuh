@@ -22,6 +22,7 @@ constexpr uint32_t kTagInit = 1, kTagDet = 2, kTagTree = 3, kTagRoll = 4, kTagPl
 // STOP (Fig. 2a): end a turn after a correct guess.  Guesses are coded
 // seat << 10 | slot << 5 | identity.
 constexpr uint32_t kStop = 0xFFFu;
+constexpr uint32_t kSet = 0xFFEu;  // action code of a plausible-number-set node (vanilla MCTS-dvc)
 // Two-player fast path: `winner` holds kPend while a playout that began where
 // the mover may stop has still to draw its continue coin.
 constexpr uint32_t kPend = 0xFEu;

@@ -71,6 +71,8 @@ struct dvc_forest {
     int engine;              // 1: fused lockstep kernel, 2: three-kernel pipeline
     double2* ucb;
     double* csl;
+    uint4* set_key;      // vanilla: plausible-set tables (2 * budget cells per tree)
+    int32_t* set_slot;
     PipeBufs pipe;
     cudaStream_t cap_stream;  // capture stream for the pipeline graph
     cudaStream_t chain_stream[kMaxChains - 1];  // chains 2.. of the pipeline graph (chain 1 runs on cap_stream)
@@ -278,7 +280,8 @@ __global__ void mcts_select_kernel(ForestDev F, SearchParams sp, int n, Descent*
     det_sample(F.plans[t], F.tables + tm.table_off, root, dr, det);
     Descent dd;
     descend(det, root.cur, F.nodes + tm.node_off, F.link + tm.node_off, F.ucb + tm.node_off, F.csl + tm.node_off, tm,
-            sp, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, s_E[wl], dd);
+            sp, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, s_E[wl], dd, nullptr,
+            set_table(F, tm));
     if (lane == 0) d = dd;
 }
 
@@ -305,7 +308,8 @@ __global__ void mcts_expand_kernel(ForestDev F, int n, Descent* work, int32_t* p
     bool ok = true;
     if (d.found)
         ok = expand_child(d, F.nodes + tm.node_off, F.link + tm.node_off, F.created + tm.node_off, tm, next_free,
-                          used, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, cont);
+                          used, (uint32_t)tm.done, paths + (size_t)t * kPathMax, movers + (size_t)t * kPathMax, cont,
+                          set_table(F, tm));
     if (lane == 0) {
         tmr.next_free = next_free;
         tmr.used = used;
@@ -344,7 +348,7 @@ __global__ void root_stats_kernel(ForestDev F, int n, int32_t* out) {
     const Node* nodes = F.nodes + tm.node_off;
     const G root = load_state(F.roots[t]);
     const Node r = nodes[0];
-    const uint32_t nchild = (r.meta >> 12) & 0xFFFu;
+    const uint32_t nchild = r.meta >> 12;
     int32_t best = -1, bv = 0, bw = 0;
     uint32_t brank = 0xFFFFFFFFu;
     int32_t blk = r.child;
@@ -376,6 +380,69 @@ __global__ void root_stats_kernel(ForestDev F, int n, int32_t* out) {
     o[5] = tm.used;
     o[6] = tm.done;
     o[7] = tm.failed;
+}
+
+// Vanilla MCTS-dvc decision (one CTA per tree): an action's visits and wins
+// summed over every plausible set's child with that action; most visits
+// wins, ties to the lowest canonical rank.  Root children = sets.
+__global__ void __launch_bounds__(256) root_stats_vanilla_kernel(ForestDev F, int n, int32_t* out) {
+    __shared__ int32_t s_v[4096], s_w[4096];
+    __shared__ unsigned long long s_best;
+    const int t = blockIdx.x;
+    if (t >= n) return;
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t a = tid; a < 4096u; a += blockDim.x) s_v[a] = s_w[a] = 0;
+    if (tid == 0) s_best = 0ull;
+    __syncthreads();
+    const TreeMeta tm = F.meta[t];
+    const Node* nodes = F.nodes + tm.node_off;
+    const int32_t* link = F.link + tm.node_off;
+    const G root = load_state(F.roots[t]);
+    const Node r = nodes[0];
+    const uint32_t nsets = r.meta >> 12;
+    for (uint32_t i = tid; i < nsets; i += blockDim.x) {
+        const Node sn = nodes[r.child + (int32_t)i];
+        const uint32_t nchild = sn.meta >> 12;
+        int32_t blk = sn.child;
+        uint32_t seen = 0, k = 0;
+        while (seen < nchild) {
+            const uint32_t size = block_size(k, false, 0u);
+            const uint32_t cnt = min(size, nchild - seen);
+            for (uint32_t e = 0; e < cnt; ++e) {
+                const Node c = nodes[blk + (int32_t)e];
+                const uint32_t code = c.meta & 0xFFFu;
+                atomicAdd(&s_v[code], c.visits);
+                atomicAdd(&s_w[code], c.wins);
+            }
+            seen += cnt;
+            ++k;
+            if (seen < nchild) blk = link[blk];
+        }
+    }
+    __syncthreads();
+    // order key: visits, then the complement of the canonical rank (< 2^13), then the code
+    unsigned long long best = 0ull;
+    for (uint32_t a = tid; a < 4096u; a += blockDim.x) {
+        if (s_v[a] <= 0) continue;
+        const unsigned long long key = (unsigned long long)(uint32_t)s_v[a] << 32 |
+                                       (unsigned long long)(0x1FFFu - canon_rank(a, root.cur, root.np)) << 12 | a;
+        best = key > best ? key : best;
+    }
+    if (best) atomicMax(&s_best, best);
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned long long b = s_best;
+        const int32_t code = b ? (int32_t)(b & 0xFFFu) : -1;
+        int32_t* o = out + 8 * t;
+        o[0] = code;
+        o[1] = b ? s_v[code] : 0;
+        o[2] = b ? s_w[code] : 0;
+        o[3] = r.visits;
+        o[4] = (int32_t)nsets;
+        o[5] = tm.used;
+        o[6] = tm.done;
+        o[7] = tm.failed;
+    }
 }
 
 // Export of one tree in creation order (row 0 = root).  Nodes carry the
@@ -413,7 +480,7 @@ __global__ void export_rows_kernel(ForestDev F, int t, const int32_t* iter_rank,
             out[4 * prow + 2] = nd.visits;
             out[4 * prow + 3] = nd.wins;
         }
-        const uint32_t nchild = (nd.meta >> 12) & 0xFFFu;
+        const uint32_t nchild = nd.meta >> 12;
         int32_t blk = nd.child;
         uint32_t seen = 0, k = 0;
         while (seen < nchild) {
@@ -455,7 +522,8 @@ __device__ void init_tree(ForestDev& F, int t, DetPlan* plans, unsigned long lon
         uint32_t slots = 0;
         for (uint32_t q = 0; q < g.np; ++q)
             if (q != g.cur && ((g.alive >> q) & 1u)) slots += __popc(g.hand(q) & ~g.rev);
-        tm.root_legal = (int32_t)(slots * __popc(U));
+        // vanilla: the root's one child block holds every plausible set
+        tm.root_legal = tm.set_cells ? tm.budget : (int32_t)(slots * __popc(U));
         tm.done = 0;
         tm.next_free = 1;
         tm.used = 1;
@@ -471,6 +539,7 @@ __device__ void init_tree(ForestDev& F, int t, DetPlan* plans, unsigned long lon
         F.created[tm.node_off] = -1;
         pipe_np[t] = -1;  // no pipeline backprop pending
     }
+    for (int32_t c = (int32_t)lane; c < tm.set_cells; c += 32) F.set_slot[tm.set_off + c] = -1;
     __syncwarp();
 }
 
@@ -521,6 +590,8 @@ ForestDev dev_of(dvc_forest* f) {
     d.csl = f->csl;
     d.flags = f->ctx->d_flags;
     d.words = f->d_words;
+    d.set_key = f->set_key;
+    d.set_slot = f->set_slot;
     return d;
 }
 
@@ -554,6 +625,7 @@ int dvc_create(dvc_ctx** out, const dvc_config* cfg, int device) {
     if (!(cfg->c_uct >= 0.0)) return DVC_E_INVALID;
     if (cfg->policy != 0 && cfg->policy != 1) return DVC_E_INVALID;
     if (cfg->tree_continue != 0 && cfg->tree_continue != 1) return DVC_E_INVALID;
+    if (cfg->vanilla != 0 && cfg->vanilla != 1) return DVC_E_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -710,7 +782,8 @@ void dvc_forest_destroy(dvc_forest* f) {
         if (f->join_ev[k]) cudaEventDestroy(f->join_ev[k]);
     }
     if (f->fork_ev) cudaEventDestroy(f->fork_ev);
-    void* ptrs[] = {f->roots,     f->meta,      f->plans,     f->tables,         f->nodes,         f->link,
+    void* ptrs[] = {f->set_key,   f->set_slot,
+                    f->roots,     f->meta,      f->plans,     f->tables,         f->nodes,         f->link,
                     f->created,   f->work,      f->paths,     f->movers,         f->leaves,        f->leaf_tree,
                     f->leaf_iter, f->d_words,   f->export_scratch, f->order,     f->ucb,           f->csl,
                     f->pipe.leaf, f->pipe.path, f->pipe.mover, f->pipe.np,       f->pipe.wins,     f->pipe.step_end,
@@ -739,16 +812,21 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     f->table_cap = c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<TreeMeta> hm(n);
-    long long slots = 0;
+    long long slots = 0, cells = 0;
+    const bool vanilla = c->cfg.vanilla != 0;
     for (int t = 0; t < n; ++t) {
         TreeMeta& m = hm[t];
         std::memset(&m, 0, sizeof(m));
         m.node_off = slots;
         m.table_off = (long long)t * f->table_cap;
-        m.cap = 1 + kRootReserve + 4 * f->h_budgets[t];
+        // vanilla: the root's block holds up to one plausible set per iteration
+        m.cap = 1 + (vanilla ? f->h_budgets[t] : kRootReserve) + 4 * f->h_budgets[t];
         m.budget = f->h_budgets[t];
         m.tree_id = h_tree_ids ? h_tree_ids[t] : (uint32_t)t;
+        m.set_off = cells;
+        m.set_cells = vanilla ? 2 * f->h_budgets[t] : 0;
         slots += m.cap;
+        cells += m.set_cells;
     }
     f->total_slots = slots;
     // Longest budget first, each tree to the least-loaded CTA that has a free
@@ -816,7 +894,9 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         alloc((void**)&f->pipe.wins, sizeof(int32_t) * 4 * n) && alloc((void**)&f->pipe.step_end, sizeof(int32_t) * n) &&
         alloc((void**)&f->pipe.det, sizeof(dvc_state) * kDetAhead * (size_t)n) &&
         alloc((void**)&f->pipe.tree0, sizeof(uint4) * kDetAhead * (size_t)n) &&
-        alloc((void**)&f->pipe.det_base, sizeof(int32_t) * n);
+        alloc((void**)&f->pipe.det_base, sizeof(int32_t) * n) &&
+        (!vanilla || (alloc((void**)&f->set_key, sizeof(uint4) * (size_t)cells) &&
+                      alloc((void**)&f->set_slot, sizeof(int32_t) * (size_t)cells)));
     if (!ok) {
         dvc_forest_destroy(f);
         return fail(c, DVC_E_OOM, "dvc_forest_create: device allocation of " + std::to_string(slots) + " node slots");
@@ -919,10 +999,15 @@ int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
     pipe_select_kernel<<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
     const int threads = pipe_rollout_threads(f);
     const bool fast2 = c->cfg.nplayers == 2 && c->cfg.ntiles == 24;
+    // may-stop leaves possible: the full tree, or leaves that can be the root itself
+    const bool pend = c->cfg.tree_continue || c->cfg.d_max == 0 || c->cfg.vanilla;
     const uint32_t smem = pipe_rollout_smem(L, threads, fast2);
-    if (fast2 && !sp.policy)
-        pipe_rollout_kernel<true, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
-                                                                        f->d_words);
+    if (fast2 && !sp.policy && !pend)
+        pipe_rollout_kernel<true, false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta,
+                                                                               f->pipe, f->d_words);
+    else if (fast2 && !sp.policy)
+        pipe_rollout_kernel<true, false, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta,
+                                                                              f->pipe, f->d_words);
     else if (fast2)
         pipe_rollout_kernel<true, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
                                                                        f->d_words);
@@ -1031,7 +1116,8 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
         const int smg = (int)pipe_rollout_smem(f->trees_per_cta, threads, false);
         cudaError_t e = cudaSuccess;
         // several rollout CTAs per SM need the largest shared-memory carveout
-        for (auto k : {pipe_rollout_kernel<true, false>, pipe_rollout_kernel<true, true>}) {
+        for (auto k : {pipe_rollout_kernel<true, false, false>, pipe_rollout_kernel<true, false, true>,
+                       pipe_rollout_kernel<true, true, true>}) {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1278,6 +1364,10 @@ int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream) {
     if (!f) return DVC_E_INVALID;
     if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_root_stats: d_out must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
+    if (f->ctx->cfg.vanilla) {
+        root_stats_vanilla_kernel<<<f->n, 256, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_out);
+        return check_launch(f->ctx, "root_stats_vanilla_kernel");
+    }
     root_stats_kernel<<<(f->n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_out);
     return check_launch(f->ctx, "root_stats_kernel");
 }
@@ -1408,6 +1498,7 @@ int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_s
     if (!out || max_budget < 1 || max_budget > (1 << 24) || value_share_pct < 0 || value_share_pct > 100)
         return fail(c, DVC_E_INVALID, "dvc_server_create: max_budget 1..2^24, value_share_pct 0..100");
     *out = nullptr;
+    if (c->cfg.vanilla) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_create: vanilla trees are searched by forests only");
     if (int rc = set_device(c)) return rc;
     // device bytes per search slot: node arena (48 B per slot: node, UCB terms,
     // link, creation stamp), counting table, plan, meta and pipeline buffers

@@ -118,13 +118,14 @@ __global__ void __launch_bounds__(128)
     Descent d;
     int32_t* path = P.path + (size_t)t * kPathMax;
     uint8_t* mover = P.mover + (size_t)t * kPathMax;
+    const SetTable st = set_table(F, tm);
     descend(det, root.cur, nodes, link, F.ucb + tm.node_off, F.csl + tm.node_off, tm, sp, it, path, mover, s_E[wl],
-            d, tree0);
+            d, tree0, st);
     bool ok = true;
     int32_t next_free = tm.next_free, used = tm.used;
     if (d.found)
         ok = expand_child(d, nodes, link, F.created + tm.node_off, tm, next_free, used, it, path, mover,
-                          sp.tree_continue != 0);
+                          sp.tree_continue != 0, st);
     if (lane == 0) {
         tmr.next_free = next_free;
         tmr.used = used;
@@ -152,7 +153,10 @@ __global__ void __launch_bounds__(128)
 // Two-player 24-tile games queue their words in a shared-memory ring
 // (RingQueue) so that two 1024-thread CTAs fit on an SM.
 // ORD: the ordering-aware playout policy (sp.policy == 1), compiled apart.
-template <bool FAST2, bool ORD = false>
+// PEND: leaves may begin where the mover may stop (the full game tree, or
+// d_max = 0); without it that check is compiled out of the playout loop,
+// since an in-tree action always clears the may-stop bit otherwise.
+template <bool FAST2, bool ORD = false, bool PEND = true>
 __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     pipe_rollout_kernel(SearchParams sp, int n, int L, int b0, const int32_t* order, const TreeMeta* meta, PipeBufs P,
                         unsigned long long* words_out) {
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         if (busy) {
             int res;
             if constexpr (FAST2) {
-                if (winner == kPend)
+                if (PEND && winner == kPend)
                     res = step_2p24_pending(h0, h1, cur, drawn, winner, r, sp.cont_thr, s_lut12);
                 else if constexpr (ORD)
                     res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);

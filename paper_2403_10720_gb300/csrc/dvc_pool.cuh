@@ -33,7 +33,13 @@ struct ForestDev {
     double* csl;   // per slot: c * sqrt(ln n)
     int32_t* flags;
     unsigned long long* words;
+    uint4* set_key;    // vanilla: plausible-set tables of all trees (TreeMeta::set_off)
+    int32_t* set_slot;
 };
+
+__device__ __forceinline__ SetTable set_table(const ForestDev& F, const TreeMeta& tm) {
+    return SetTable{F.set_key + tm.set_off, F.set_slot + tm.set_off, (uint32_t)tm.set_cells};
+}
 
 __device__ __forceinline__ void latch_error(int32_t* flags, int32_t code) { atomicCAS(&flags[0], 0, code); }
 
@@ -125,12 +131,14 @@ __global__ void __launch_bounds__(MAXT, 1)
             Descent d;
             int32_t* path = s_path + s * kPathMax;
             uint8_t* mover = s_mover + s * kPathMax;
+            const SetTable st = set_table(F, tm);
             descend(det, root.cur, nodes, link, F.ucb + tm.node_off, F.csl + tm.node_off, tm, sp, it, path, mover,
-                    s_E + warp * 104u, d);
+                    s_E + warp * 104u, d, nullptr, st);
             bool ok = true;
             if (d.found) {
                 int32_t next_free = tm.next_free, used = tm.used;
-                ok = expand_child(d, nodes, link, created, tm, next_free, used, it, path, mover, sp.tree_continue != 0);
+                ok = expand_child(d, nodes, link, created, tm, next_free, used, it, path, mover, sp.tree_continue != 0,
+                                  st);
                 if (lane == 0) {
                     tm.next_free = next_free;
                     tm.used = used;

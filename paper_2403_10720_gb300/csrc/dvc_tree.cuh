@@ -10,6 +10,12 @@
 // with one coalesced load.  A block's successor is recorded in `link` at the
 // block's first slot.  With blocks no larger than four times the children
 // they hold, root block + 4 * budget slots always suffice.
+//
+// Vanilla MCTS-dvc (Sec. III-A): the root's children are plausible-number
+// sets, one per distinct assignment of the tiles the observer cannot see, and
+// the guess tree of each hangs below it.  The root's single child block then
+// holds `budget` slots (at most one set per iteration), and a per-tree open-
+// addressing table maps an assignment to its set node.
 #pragma once
 #include "dvc_det.cuh"
 
@@ -33,7 +39,68 @@ struct TreeMeta {
     uint32_t tree_id;     // stream key
     int32_t failed;       // arena exhausted, or view too large to determinize
     int32_t used;         // nodes in the tree
+    long long set_off;    // vanilla: first cell of its plausible-set table
+    int32_t set_cells;    // vanilla: cells of that table (2 * budget); 0 otherwise
+    int32_t pad_;
 };
+
+// A tree's plausible-set table: open addressing with linear probing, cell i
+// holds an assignment's key and the slot of its set node (-1: empty).  At
+// most `budget` keys in 2 * budget cells, so an empty cell always ends a probe.
+struct SetTable {
+    uint4* key;
+    int32_t* slot;
+    uint32_t cells;  // 0: not a vanilla tree
+};
+
+// Key of a determinization's plausible-number set as seen by seat obs: the
+// other seats' hands in seat order (three words, unused seats zero), then the
+// joker gaps and the white-first flag, which place the jokers in the rows.
+__device__ __forceinline__ uint4 set_key(const G& g, uint32_t obs) {
+    uint32_t h[3] = {0u, 0u, 0u};
+    uint32_t k = 0;
+#pragma unroll
+    for (uint32_t p = 0; p < 4; ++p)
+        if (p < g.np && p != obs) h[k++] = g.hand(p);
+    return make_uint4(h[0], h[1], h[2], g.jg0 | (g.jg1 << 8) | ((g.jflag & 1u) << 16));
+}
+
+// First probe cell of a key: a 64-bit mix (xor-shift-multiply rounds) of its
+// words, scaled to the cell count by a multiply-high.
+__device__ __forceinline__ uint32_t set_home(const uint4& k, uint32_t cells) {
+    unsigned long long a = ((unsigned long long)k.y << 32 | k.x) ^ (((unsigned long long)k.w << 32 | k.z) * 0x9E3779B97F4A7C15ull);
+    a ^= a >> 31;
+    a *= 0xD6E8FEB86659FD93ull;
+    a ^= a >> 32;
+    return (uint32_t)(((unsigned long long)(uint32_t)a * cells) >> 32);
+}
+
+// Warp-parallel probe: lane j looks at the j-th cell of each round of 32; the
+// first cell in probe order that is empty or holds the key ends the probe.
+// Returns the set node's slot (-1 if absent) and the cell it sits in, or
+// would be inserted into.  Lane-uniform.
+__device__ __forceinline__ int32_t set_find(const SetTable& st, const uint4& k, uint32_t& cell) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t home = set_home(k, st.cells);
+    for (uint32_t r = 0; r < st.cells; r += 32u) {
+        uint32_t c = home + r + lane;
+        c = c % st.cells;
+        const int32_t s = st.slot[c];
+        bool stop = s < 0;
+        if (!stop) {
+            const uint4 q = st.key[c];
+            stop = q.x == k.x && q.y == k.y && q.z == k.z && q.w == k.w;
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, stop);
+        if (bal) {
+            const uint32_t L = __ffs(bal) - 1u;
+            cell = __shfl_sync(0xFFFFFFFFu, c, L);
+            return __shfl_sync(0xFFFFFFFFu, s, L);
+        }
+    }
+    cell = 0xFFFFFFFFu;  // unreachable while keys <= cells / 2
+    return -1;
+}
 
 // Slots reserved for the root's child block: its legal-guess count is
 // (face-down slots of opponents) x (unknown identities) <= 25 * 25.
@@ -65,6 +132,8 @@ struct Descent {
     int32_t nchild;   // children of `node`
     int32_t last_blk, last_size, last_cnt, nblocks;
     int32_t np;       // path length
+    uint32_t set_cell;  // vanilla, act == kSet: the table cell for the new set
+    uint4 set_key;      // vanilla, act == kSet: its key
 };
 
 // Warp-cooperative descent from the root for iteration `it`.  All 32 lanes
@@ -77,10 +146,14 @@ struct Descent {
 // values a scan would compute from the counts.
 // tree0 (optional): the first block of the iteration's tree stream, computed
 // ahead of time (the same four words the stream would generate).
+// st: the plausible-set table of a vanilla tree.  The determinization's set
+// node is the first step below the root; a set not seen before is this
+// iteration's expansion (act = kSet) and its leaf is the determinized root.
 __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* nodes, const int32_t* link,
                                         const double2* ucb, const double* csl_of, const TreeMeta& tm,
                                         const SearchParams& sp, uint32_t it, int32_t* path, uint8_t* mover,
-                                        uint32_t* E, Descent& d, const uint4* tree0 = nullptr) {
+                                        uint32_t* E, Descent& d, const uint4* tree0 = nullptr,
+                                        const SetTable& st = SetTable{nullptr, nullptr, 0u}) {
     const uint32_t lane = threadIdx.x & 31u;
     d.s = det;
     d.tr.open(sp.seed, tm.tree_id, 0u, it, kTagTree);
@@ -93,13 +166,39 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         mover[0] = (uint8_t)obs;
     }
     uint32_t depth = 0;
+    if (st.cells) {
+        const uint4 key = set_key(d.s, obs);
+        uint32_t cell;
+        const int32_t slot = set_find(st, key, cell);
+        if (slot < 0) {
+            // a new set: appended to the root's single child block
+            const Node r = nodes[0];
+            const int32_t nsets = (int32_t)(r.meta >> 12);
+            d.found = 1;
+            d.act = kSet;
+            d.set_cell = cell;
+            d.set_key = key;
+            d.nchild = nsets;
+            d.nblocks = nsets ? 1 : 0;
+            d.last_blk = nsets ? r.child : -1;
+            d.last_size = tm.root_legal;
+            d.last_cnt = nsets;
+            return;
+        }
+        if (lane == 0) {
+            path[1] = slot;
+            mover[1] = (uint8_t)obs;
+        }
+        d.np = 2;
+        d.node = slot;
+    }
     while (d.s.winner == kNone && depth < (uint32_t)sp.d_max) {
         // loads that do not depend on one another are issued together: the
         // node and its exploration term; below, each child with its UCB1
         // terms, and the next block's start before this block is scanned
         const Node nd = nodes[d.node];
         const double csl_node = csl_of[d.node];  // any slot's entry exists; used only if it has children
-        const uint32_t nchild = (nd.meta >> 12) & 0xFFFu;
+        const uint32_t nchild = nd.meta >> 12;
         const uint32_t cur = d.s.cur;
         const uint32_t U = d.s.tmask & ~d.s.hand(cur) & ~d.s.rev;
         for (uint32_t e = lane; e < 104u; e += 32u) E[e] = 0u;
@@ -209,12 +308,14 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
     }
 }
 
-// Create the child found by descend() and step the state through its action.
-// Lane-uniform; lane 0 writes memory.  next_free is the tree's allocator
-// (uniform register copy).  Returns false if the arena is exhausted.
+// Create the child found by descend() and step the state through its action
+// (a new plausible set is entered in the tree's set table and leaves the state
+// as it is).  Lane-uniform; lane 0 writes memory.  next_free is the tree's
+// allocator (uniform register copy).  Returns false if the arena is exhausted.
 __device__ __forceinline__ bool expand_child(Descent& d, Node* nodes, int32_t* link, int32_t* created,
                                              const TreeMeta& tm, int32_t& next_free, int32_t& used, uint32_t it,
-                                             int32_t* path, uint8_t* mover, bool cont) {
+                                             int32_t* path, uint8_t* mover, bool cont,
+                                             const SetTable& st = SetTable{nullptr, nullptr, 0u}) {
     const uint32_t lane = threadIdx.x & 31u;
     int32_t slot;
     if (d.nchild == 0 || d.last_cnt >= d.last_size) {
@@ -244,8 +345,12 @@ __device__ __forceinline__ bool expand_child(Descent& d, Node* nodes, int32_t* l
         nodes[d.node].meta += 1u << 12;
         path[d.np] = slot;
         mover[d.np] = (uint8_t)d.s.cur;
+        if (d.act == kSet) {
+            st.key[d.set_cell] = d.set_key;
+            st.slot[d.set_cell] = slot;
+        }
     }
-    tree_apply(d.s, d.act, d.tr, cont);
+    if (d.act != kSet) tree_apply(d.s, d.act, d.tr, cont);
     d.np++;
     d.node = slot;
     ++used;

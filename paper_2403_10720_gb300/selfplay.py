@@ -3,7 +3,8 @@
 Games follow the model the tree searches (Sec. III-A): the seat to move
 draws, makes one guess chosen by a UCT search from its own view, and the turn
 passes.  Every move of every live game is a query to a dvc_server (searches of
-all games run together on the device); the decisions are applied to the true
+all games run together on the device), or, for agents a server does not hold
+(vanilla MCTS-dvc), one tree of a per-turn forest; the decisions are applied to the true
 states with dvc_play_move.  In game g agent A plays seat g mod P and agent B
 the other seats, so each agent moves first in its share of the games.  An
 agent is a server (its context fixes the playout policy) with a leaf mode and
@@ -70,6 +71,57 @@ def play_agents(ctx, agent_a, agent_b, n_games, root_seed, seed, max_turns=400, 
         ctx.dvc_play_move(states, actions, seed, turn, game_ids)
         turn += 1
     ctx.dvc_check()
+    wall = time.perf_counter() - t0
+    h = states.cpu().numpy()
+    winners = h[:, 28].astype(np.int64)
+    done = winners != 0xFF
+    wins = int((winners[done] == a_seat[done]).sum())
+    n_done = int(done.sum())
+    rate = wins / max(n_done, 1)
+    half = 1.96 * math.sqrt(max(rate * (1 - rate), 1e-12) / max(n_done, 1))
+    return {
+        "winners": winners, "a_seat": a_seat, "turns": turn, "games_finished": n_done,
+        "a_wins": wins, "a_win_rate": rate, "ci95": [rate - half, rate + half],
+        "fair_share": 1.0 / nplayers, "decisions_a": decisions[0], "decisions_b": decisions[1],
+        "wall_s": wall, "decisions_per_s": (decisions[0] + decisions[1]) / wall,
+    }
+
+
+def play_forest_agents(game, agent_a, agent_b, n_games, root_seed, seed, max_turns=400):
+    """play_agents for agents a server does not hold (vanilla trees): each
+    turn, every agent searches all positions where it is to move as one
+    forest.  An agent is (ctx, budget): its context fixes the tree and the
+    playout policy.  The search of game g at turn k is keyed by tree id
+    k * n_games + g.  Same return dict as play_agents."""
+    from . import Forest
+    states = game.dvc_init_states(root_seed, n_games)
+    nplayers = int(states[0, 26].item())
+    a_seat = np.arange(n_games) % nplayers
+    game_ids = torch.arange(n_games, dtype=torch.int32, device=states.device)
+    actions = torch.empty(n_games, dtype=torch.int32, device=states.device)
+    decisions = [0, 0]
+    t0 = time.perf_counter()
+    turn = 0
+    while turn < max_turns:
+        h = states.cpu().numpy()
+        live = np.nonzero(h[:, 28] == 0xFF)[0]
+        if len(live) == 0:
+            break
+        act = np.full(n_games, -1, dtype=np.int32)
+        for who, (ctx, budget) in enumerate((agent_a, agent_b)):
+            mine = live[(h[live, 23] == a_seat[live]) == (who == 0)]
+            if len(mine) == 0:
+                continue
+            roots = states[torch.from_numpy(mine).to(states.device)].contiguous()
+            forest = Forest(ctx, roots, [budget] * len(mine), seed, tree_ids=turn * n_games + mine)
+            forest.dvc_mcts_step(budget)
+            act[mine] = forest.dvc_root_stats()[:, 0].cpu().numpy()
+            forest.close()
+            decisions[who] += len(mine)
+        actions.copy_(torch.from_numpy(act))
+        game.dvc_play_move(states, actions, seed, turn, game_ids)
+        turn += 1
+    game.dvc_check()
     wall = time.perf_counter() - t0
     h = states.cpu().numpy()
     winners = h[:, 28].astype(np.int64)
