@@ -13,8 +13,11 @@ import os
 import numpy as np
 import torch
 
+# The last five give each rollout CTA exactly one warp per 32 playouts of its
+# trees: with few playouts per leaf and uneven budgets, idle warps would hold
+# registers until the CTA's longest game ends.
 CANDIDATES = [(2, 0, 0, 0), (2, 2, 16, 8), (2, 4, 16, 4), (2, 4, 16, 8), (2, 2, 8, 8), (2, 0, 32, 2), (1, 0, 16, 0),
-              (1, 0, 32, 0)]
+              (1, 0, 32, 0), (2, 1, 1, 16), (2, 1, 1, 8), (2, 2, 2, 8), (2, 2, 2, 16), (2, 4, 4, 8)]
 _CACHE = os.path.join(os.path.expanduser("~"), ".cache", "dvc", "autotune.json")
 
 

@@ -996,12 +996,15 @@ int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
     const int n = f->n, L = f->trees_per_cta;
     const int i0 = std::min(n, b0 * L), i1 = std::min(n, b1 * L);
     if (i1 <= i0) return DVC_OK;
-    pipe_select_kernel<<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
+    if (c->cfg.vanilla)
+        pipe_select_kernel<true><<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
+    else
+        pipe_select_kernel<false><<<((i1 - i0) * 32 + 127) / 128, 128, 0, st>>>(fd, sp, i0, i1, f->order, f->pipe);
     const int threads = pipe_rollout_threads(f);
     const bool fast2 = c->cfg.nplayers == 2 && c->cfg.ntiles == 24;
     // may-stop leaves possible: the full tree, or leaves that can be the root itself
     const bool pend = c->cfg.tree_continue || c->cfg.d_max == 0 || c->cfg.vanilla;
-    const uint32_t smem = pipe_rollout_smem(L, threads, fast2);
+    const uint32_t smem = pipe_rollout_smem(L, threads);
     if (fast2 && !sp.policy && !pend)
         pipe_rollout_kernel<true, false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta,
                                                                                f->pipe, f->d_words);
@@ -1112,19 +1115,17 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
     dvc_ctx* c = f->ctx;
     {
         const int threads = pipe_rollout_threads(f);
-        const int sm2 = (int)pipe_rollout_smem(f->trees_per_cta, threads, true);
-        const int smg = (int)pipe_rollout_smem(f->trees_per_cta, threads, false);
+        const int sm = (int)pipe_rollout_smem(f->trees_per_cta, threads);
         cudaError_t e = cudaSuccess;
         // several rollout CTAs per SM need the largest shared-memory carveout
         for (auto k : {pipe_rollout_kernel<true, false, false>, pipe_rollout_kernel<true, false, true>,
-                       pipe_rollout_kernel<true, true, true>}) {
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+                       pipe_rollout_kernel<true, true, true>, pipe_rollout_kernel<false, false, true>,
+                       pipe_rollout_kernel<false, true, true>}) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared);
         }
-        for (auto k : {pipe_rollout_kernel<false, false>, pipe_rollout_kernel<false, true>})
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smg);
         if (e != cudaSuccess) return cuda_fail(c, e, "pipeline attributes");
     }
     if (int rc = clear_pipe_det(f, st)) return rc;
@@ -1169,8 +1170,12 @@ int enqueue_value_iteration(dvc_forest* f, int k, int chains, cudaStream_t st) {
     int t0, t1, row0;
     value_chain(f, k, chains, t0, t1, row0);
     if (t1 <= t0) return DVC_OK;
-    pipe_select_kernel<<<((t1 - t0) * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), t0, t1, nullptr,
-                                                                      f->pipe);
+    if (c->cfg.vanilla)
+        pipe_select_kernel<true><<<((t1 - t0) * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), t0, t1,
+                                                                                nullptr, f->pipe);
+    else
+        pipe_select_kernel<false><<<((t1 - t0) * 32 + 127) / 128, 128, 0, st>>>(dev_of(f), params_of(f), t0, t1,
+                                                                                 nullptr, f->pipe);
     if (int rc = check_launch(c, "pipe_select_kernel")) return rc;
     if (int rc = dvc_value_forward_rows(c, f->pipe.leaf + t0, t1 - t0, &f->vrows, row0, f->probs + 4 * (size_t)t0, st))
         return rc;

@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(128)
 // Finish the previous iteration of tree t (backprop) and run its next
 // selection and expansion.
 // Trees order[i0 .. i1-1] (trees i0 .. i1-1 if order is null), one warp each.
+// VANILLA: the trees have a plausible-set layer (compiled apart, so that the
+// MCTS-dvc walk carries none of its code).
+template <bool VANILLA>
 __global__ void __launch_bounds__(128)
     pipe_select_kernel(ForestDev F, SearchParams sp, int i0, int i1, const int32_t* order, PipeBufs P) {
     __shared__ uint32_t s_E[4][104];
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(128)
     Descent d;
     int32_t* path = P.path + (size_t)t * kPathMax;
     uint8_t* mover = P.mover + (size_t)t * kPathMax;
-    const SetTable st = set_table(F, tm);
+    const SetTable st = VANILLA ? set_table(F, tm) : SetTable{nullptr, nullptr, 0u};
     descend(det, root.cur, nodes, link, F.ucb + tm.node_off, F.csl + tm.node_off, tm, sp, it, path, mover, s_E[wl],
             d, tree0, st);
     bool ok = true;
@@ -150,8 +153,9 @@ __global__ void __launch_bounds__(128)
 // The CTA's L x P playouts form one pool: a lane whose game ends takes the
 // next playout index (warp-aggregated: one shared-memory atomic per warp and
 // step), so lanes wait for the longest game only at the end of the pool.
-// Two-player 24-tile games queue their words in a shared-memory ring
-// (RingQueue) so that two 1024-thread CTAs fit on an SM.
+// Every lane queues its words in a shared-memory ring (RingQueue), refilled
+// warp-wide, so that the Philox rounds run for most lanes at once; for
+// two-player 24-tile games it also lets two 1024-thread CTAs fit on an SM.
 // ORD: the ordering-aware playout policy (sp.policy == 1), compiled apart.
 // PEND: leaves may begin where the mover may stop (the full game tree, or
 // d_max = 0); without it that check is compiled out of the playout loop,
@@ -164,8 +168,8 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     __shared__ uint32_t s_magic[32];
     __shared__ unsigned long long s_lut12[FAST2 ? 4096 : 1];
     __shared__ int32_t s_n, s_next;
-    uint32_t* s_ring = (uint32_t*)smem;                            // FAST2: 16 words per thread
-    int32_t* s_tree = (int32_t*)(smem + (FAST2 ? 64u * blockDim.x : 0u));  // listed leaves: tree index
+    uint32_t* s_ring = (uint32_t*)smem;                   // 16 words per thread
+    int32_t* s_tree = (int32_t*)(smem + 64u * blockDim.x);  // listed leaves: tree index
     int32_t* s_wins = s_tree + L;                                  // 4 per listed leaf
     uint32_t* s_tid = (uint32_t*)(s_wins + 4 * L);
     uint32_t* s_it = s_tid + L;
@@ -203,12 +207,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     const uint32_t mP = Pp > 1u ? 0xFFFFFFFFu / Pp + 1u : 0u;
     unsigned long long words = 0ull;
     uint32_t k = 0, steps = 0;
-    using Queue = typename std::conditional<FAST2, RingQueue, WordQueue>::type;
-    Queue r;
-    if constexpr (FAST2) {
-        r.ring = s_ring + tid;
-        r.stride = blockDim.x;
-    }
+    RingQueue r;
+    r.ring = s_ring + tid;
+    r.stride = blockDim.x;
     G g;
     uint32_t h0 = 0, h1 = 0, rev = 0, cur = 0, drawn = kNone, winner = kNone;
     auto start = [&](uint32_t p) {
@@ -312,10 +313,10 @@ __global__ void pipe_value_wins_kernel(int t0, int t1, PipeBufs P, const float* 
     for (int s = 0; s < 4; ++s) w[s] = (int32_t)(probs[4 * t + s] * (float)playouts + 0.5f);
 }
 
-// Dynamic shared memory of pipe_rollout_kernel: the word rings (two-player
-// 24-tile games) and the listed leaves.
-__host__ __device__ inline uint32_t pipe_rollout_smem(int L, int threads, bool fast2) {
-    return (uint32_t)((fast2 ? 64 * threads : 0) + 4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
+// Dynamic shared memory of pipe_rollout_kernel: the word rings and the
+// listed leaves.
+__host__ __device__ inline uint32_t pipe_rollout_smem(int L, int threads) {
+    return (uint32_t)(64 * threads + 4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
 }
 
 }  // namespace dvc
