@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # CTA), from ncu full captures (cold cache) summarised under profiles/
 # (pipe_select_kernel / pipe_rollout_kernel / pipe_det_kernel _2p24_4096trees_64it.md).
 PROFILED_SHAPE = (16, 2, 16)
-DRAM_PER_LAUNCH = {"select": 298_752, "rollout": 75_520, "det": 285_696}
+DRAM_PER_LAUNCH = {"select": 306_432, "rollout": 81_536, "det": 289_792}
 
 
 def _env_int(k, d):
@@ -376,12 +376,18 @@ def run_uneven(args, w):
     from paper_2403_10720_gb300 import autotune, build
     build.build()
     ctx = dvc.Context(dvc.Config(**w.config_kwargs()), 0)
-    roots = ctx.dvc_init_states(w.root_seed, w.n_trees)
-    budgets = w.budgets()
-    shape = autotune.tune(dvc, ctx, roots, budgets, w.seed, scale=0.02)
+    n = args.trees or w.n_trees
+    roots = ctx.dvc_init_states(w.root_seed, n)
+    budgets = w.budgets(n)
+    if args.iterations:  # small profiling cases: budgets capped
+        budgets = np.minimum(budgets, args.iterations).astype(np.int32)
+    if args.chains or args.trees_per_cta or args.warps:
+        shape = (2, args.trees_per_cta, args.warps, args.chains)
+    else:
+        shape = autotune.tune(dvc, ctx, roots, budgets, w.seed, scale=0.02)
     forest = dvc.Forest(ctx, roots, budgets, w.seed)
     forest.dvc_forest_tune(*shape)
-    stats = torch.empty((w.n_trees, 8), dtype=torch.int32, device=roots.device)
+    stats = torch.empty((n, 8), dtype=torch.int32, device=roots.device)
     it = int(budgets.max())
     for _ in range(args.warmup):
         forest.dvc_forest_reset()
@@ -408,11 +414,12 @@ def run_uneven(args, w):
         "metric": "playouts/s", "value": playouts / total_s, "unit": "playouts/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w.name, "trees": w.n_trees, "iterations_total": int(budgets.sum()),
+        "config": {"workload": w.name if n == w.n_trees and not args.iterations else f"{w.name}_first{n}_cap{args.iterations}",
+                   "trees": n, "iterations_total": int(budgets.sum()),
                    "budget_range": [int(budgets.min()), int(budgets.max())], "playouts_per_leaf": w.playouts,
                    "players": w.nplayers, "tiles": w.ntiles, "launch_shape": list(shape),
                    "l2": "working set (node arenas) far above L2"},
-        "decisions_per_s": w.n_trees * args.steps / total_s, "clocks": clk}), flush=True)
+        "decisions_per_s": n * args.steps / total_s, "clocks": clk}), flush=True)
 
 
 def run_selfplay(args):
