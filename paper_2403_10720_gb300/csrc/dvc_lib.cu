@@ -1547,8 +1547,9 @@ int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_s
             rc = check_launch(c, "forest_set_budget_kernel");
         }
         // resident searches start and end at any time: the fused engine, one
-        // launch per poll over the CTAs that hold resident slots only
-        if (rc == DVC_OK && m == 0) rc = dvc_forest_tune(sv->f[m], 1, 16, 16, 0);
+        // launch per poll over the CTAs that hold resident slots only; four
+        // slots per CTA, so a search waits on three others per iteration
+        if (rc == DVC_OK && m == 0) rc = dvc_forest_tune(sv->f[m], 1, 4, 4, 0);
         if (rc == DVC_OK) sv->slots[m].assign(n, ServerSlot());
     }
     if (rc == DVC_OK && cudaStreamSynchronize(sv->st) != cudaSuccess) rc = fail(c, DVC_E_CUDA, "dvc_server_create sync");
