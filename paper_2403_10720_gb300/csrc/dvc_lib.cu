@@ -962,7 +962,8 @@ int launch_fused(dvc_forest* f, int n_iterations, cudaStream_t st) {
                                  (int)L.bytes);                                                                   \
         if (e == cudaSuccess)                                                                                     \
             mcts_pool_kernel<MT, F2, ORD><<<grid, threads, L.bytes, st>>>(dev_of(f), params_of(f), n_iterations,  \
-                                                                          f->order, f->n, T);                     \
+                                                                          f->order, f->n, T, f->pipe.det,         \
+                                                                          f->pipe.tree0);                         \
     } while (0)
     if (c->cfg.policy && threads <= 512) {  // ordering-aware playouts
         if (fast2) DVC_LAUNCH_POOL(512, true, true);

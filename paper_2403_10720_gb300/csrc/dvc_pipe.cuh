@@ -15,8 +15,6 @@
 
 namespace dvc {
 
-constexpr int kDetAhead = 64;  // determinizations sampled ahead per tree
-
 struct PipeBufs {
     dvc_state* leaf;    // per tree
     int32_t* path;      // per tree, kPathMax slots

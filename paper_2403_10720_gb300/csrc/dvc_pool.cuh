@@ -1,9 +1,11 @@
 // dvc_pool.cuh -- the fused search step: several trees per CTA in lockstep.
 //
-// A CTA owns T trees (its slots) and W warps.  One iteration of every tree the
-// CTA owns runs as:
-//   1. tree phase -- warp w walks slots w, w+W, ...: determinize the root view,
-//      descend by UCB1, expand one child, and publish the leaf;
+// A CTA owns T trees (its slots) and W warps.  Every kDetAhead iterations all
+// threads sample the next kDetAhead determinizations of every slot, one
+// thread each (a determinization depends only on the root view, the seed, the
+// tree and the iteration).  One iteration of every tree the CTA owns runs as:
+//   1. tree phase -- warp w walks slots w, w+W, ...: take the iteration's
+//      determinization, descend by UCB1, expand one child, and publish the leaf;
 //   2. playout phase -- the P playouts of every published leaf form one pool;
 //      each lane takes the next playout of the pool as soon as its previous one
 //      ends (one guess, plus the draw that follows, per loop step), so lanes stay
@@ -20,6 +22,7 @@
 namespace dvc {
 
 constexpr int kPathMax = 20;
+constexpr int kDetAhead = 64;  // determinizations sampled ahead per tree
 
 struct ForestDev {
     const dvc_state* roots;
@@ -45,7 +48,7 @@ __device__ __forceinline__ void latch_error(int32_t* flags, int32_t code) { atom
 
 // Shared-memory layout of one CTA with T slots and W warps.
 struct PoolLayout {
-    uint32_t pl, meta, root, leaf, path, mover, wins, misc, E, cnt, bytes;
+    uint32_t pl, meta, root, leaf, path, mover, wins, misc, base, E, cnt, bytes;
     __host__ __device__ PoolLayout(int T, int W) {
         uint32_t o = 0;
         auto take = [&](uint32_t n) {
@@ -61,6 +64,7 @@ struct PoolLayout {
         mover = take((uint32_t)kPathMax * T);
         wins = take(16u * T);
         misc = take(16u * T);  // per slot: np, end, tree index, 0
+        base = take(4u * T);   // per slot: first iteration sampled ahead
         E = take(4u * 104u * W);
         cnt = take(4u * 8u);   // [parity][nleaf, next, ntrees, 0]
         bytes = o;
@@ -69,9 +73,13 @@ struct PoolLayout {
 
 // ORD: the ordering-aware playout policy (sp.policy == 1), compiled apart so
 // that the uniform playout loop keeps its registers.
+// det_ahead / tree0_ahead: kDetAhead determinized roots and first in-tree
+// stream blocks per tree (the forest's pipeline buffers; rewritten at the
+// start of every launch).
 template <int MAXT, bool FAST2, bool ORD = false>
 __global__ void __launch_bounds__(MAXT, 1)
-    mcts_pool_kernel(ForestDev F, SearchParams sp, int n_iter, const int32_t* order, int n_trees, int T) {
+    mcts_pool_kernel(ForestDev F, SearchParams sp, int n_iter, const int32_t* order, int n_trees, int T,
+                     dvc_state* det_ahead, uint4* tree0_ahead) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_magic[32];
     __shared__ unsigned long long s_lut12[FAST2 ? 4096 : 1];
@@ -85,6 +93,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     uint8_t* s_mover = (uint8_t*)(smem + L.mover);
     int32_t* s_wins = (int32_t*)(smem + L.wins);
     int32_t* s_misc = (int32_t*)(smem + L.misc);
+    int32_t* s_base = (int32_t*)(smem + L.base);
     uint32_t* s_E = (uint32_t*)(smem + L.E);
     int32_t* s_cnt = (int32_t*)(smem + L.cnt);
 
@@ -115,6 +124,30 @@ __global__ void __launch_bounds__(MAXT, 1)
     unsigned long long words = 0ull;
     for (int iter = 0;; ++iter) {
         int32_t* cnt = s_cnt + 4 * (iter & 1);
+        if (iter % kDetAhead == 0) {
+            // ---- 0. the next kDetAhead determinizations of every running slot
+            __syncthreads();
+            for (int idx = (int)tid; idx < nslot * kDetAhead; idx += (int)blockDim.x) {
+                const int s = idx / kDetAhead, k = idx - s * kDetAhead;
+                const TreeMeta& tm = s_tm[s];
+                if (k == 0) s_base[s] = tm.done;
+                if (tm.done + k >= s_misc[4 * s + 1]) continue;
+                const uint32_t it = (uint32_t)(tm.done + k);
+                const size_t a = (size_t)s_misc[4 * s + 2] * kDetAhead + (size_t)k;
+                const G root = load_state(s_root[s]);
+                Rng dr;
+                dr.open(sp.seed, tm.tree_id, 0u, it, kTagDet);
+                G det;
+                det_sample(s_pl[s], F.tables + tm.table_off, root, dr, det);
+                dvc_state ds;
+                store_state(det, ds);
+                det_ahead[a] = ds;
+                Rng tr;
+                tr.open(sp.seed, tm.tree_id, 0u, it, kTagTree);
+                tree0_ahead[a] = tr.block0();
+            }
+            __syncthreads();
+        }
         // ---- 1. tree phase
         for (int s = (int)warp; s < nslot; s += W) {
             TreeMeta& tm = s_tm[s];
@@ -124,16 +157,14 @@ __global__ void __launch_bounds__(MAXT, 1)
             int32_t* link = F.link + tm.node_off;
             int32_t* created = F.created + tm.node_off;
             const G root = load_state(s_root[s]);
-            Rng dr;
-            dr.open(sp.seed, tm.tree_id, 0u, it, kTagDet);
-            G det;
-            det_sample(s_pl[s], F.tables + tm.table_off, root, dr, det);
+            const size_t a = (size_t)s_misc[4 * s + 2] * kDetAhead + (it - (uint32_t)s_base[s]);
+            const G det = load_state(det_ahead[a]);
             Descent d;
             int32_t* path = s_path + s * kPathMax;
             uint8_t* mover = s_mover + s * kPathMax;
             const SetTable st = set_table(F, tm);
             descend(det, root.cur, nodes, link, F.ucb + tm.node_off, F.csl + tm.node_off, tm, sp, it, path, mover,
-                    s_E + warp * 104u, d, nullptr, st);
+                    s_E + warp * 104u, d, tree0_ahead + a, st);
             bool ok = true;
             if (d.found) {
                 int32_t next_free = tm.next_free, used = tm.used;
