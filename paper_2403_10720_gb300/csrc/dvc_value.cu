@@ -118,13 +118,23 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
                     break;
                 }
             }
-            // unknown numbered tiles strictly between lo and hi
+            // unknown numbered tiles strictly between lo and hi, as values:
+            // bit v of the 12-bit field <- tile bits 2v | 2v+1 (even bits
+            // gathered by halving shifts), bit 12 <- an unknown joker; the
+            // 13-bit field is or-ed into at most two words
             const uint32_t above = lo < 0 ? 0x00FFFFFFu : (0x00FFFFFFu & ~((2u << lo) - 1u));
             const uint32_t below = (1u << hi) - 1u;
             const uint32_t m = U & above & below;
-            for (int v = 0; v < 12; ++v)
-                if ((m >> (2 * v)) & 3u) set(base + v);
-            if (U & kJokerMask) set(base + 12);
+            uint32_t x = (m | (m >> 1)) & 0x00555555u;
+            x = (x | (x >> 1)) & 0x00333333u;
+            x = (x | (x >> 2)) & 0x000F0F0Fu;
+            x = ((x | (x >> 4)) & 0x000000FFu) | ((x >> 8) & 0x00000F00u);
+            const uint32_t field = x | ((U & kJokerMask) ? 1u << 12 : 0u);
+            const uint32_t w0 = (uint32_t)base >> 5, sh = (uint32_t)base & 31u;
+            if (field) {
+                atomicOr(&bits[w0], field << sh);
+                if (sh > 19u) atomicOr(&bits[w0 + 1u], field >> (32u - sh));
+            }
         }
     }
     __syncwarp();
