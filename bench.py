@@ -388,10 +388,15 @@ def run_uneven(args, w):
     forest = dvc.Forest(ctx, roots, budgets, w.seed)
     forest.dvc_forest_tune(*shape)
     stats = torch.empty((n, 8), dtype=torch.int32, device=roots.device)
-    it = int(budgets.max())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cut = autotune.tail_start(budgets, sms)
+
+    def search():
+        # the tuned shape while many trees run, one tree per fused CTA for the tail
+        autotune.step_with_tail(forest, budgets, shape, sms)
     for _ in range(args.warmup):
         forest.dvc_forest_reset()
-        forest.dvc_mcts_step(it)
+        search()
     torch.cuda.synchronize()
     ev = []
     clocks = ClockSampler(0)
@@ -400,7 +405,7 @@ def run_uneven(args, w):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         forest.dvc_forest_reset()
-        forest.dvc_mcts_step(it)
+        search()
         forest.dvc_root_stats(out=stats)
         b.record()
         ev.append((a, b))
@@ -418,6 +423,7 @@ def run_uneven(args, w):
                    "trees": n, "iterations_total": int(budgets.sum()),
                    "budget_range": [int(budgets.min()), int(budgets.max())], "playouts_per_leaf": w.playouts,
                    "players": w.nplayers, "tiles": w.ntiles, "launch_shape": list(shape),
+                   "tail": {"from_iteration": cut, "launch_shape": list(autotune.TAIL_SHAPE)},
                    "l2": "working set (node arenas) far above L2"},
         "decisions_per_s": n * args.steps / total_s, "clocks": clk}), flush=True)
 
