@@ -215,7 +215,7 @@ int dvc_play_move(dvc_ctx* ctx, dvc_state* d_states, int n, const int32_t* d_act
  * 20-byte cells), a
  * determinization table of 2,048 cells (2 players) or 32,768 cells (3-4
  * players) of 8 bytes, and 64 determinized roots with the first block of
- * their in-tree random streams (3 KB) sampled ahead by engine 2.  The root
+ * their in-tree random streams (3 KB) sampled ahead by both engines.  The root
  * views are planned on the device without a host synchronisation; a view
  * whose table does not fit latches
  * DVC_E_UNSUPPORTED and its tree does no work.  DVC_E_OOM if memory runs out.
@@ -251,7 +251,8 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
  * Engine and launch shape of dvc_mcts_step (no effect on results).
  * engine 1: one fused kernel; each CTA runs trees_per_cta trees in lockstep
  * with warps_per_cta warps (every warp walks a tree, then all lanes share the
- * leaves' playouts).  engine 2: per iteration two launches (backprop of the
+ * leaves' playouts; every 64 iterations all threads sample the next 64
+ * determinizations of every tree, one thread each).  engine 2: per iteration two launches (backprop of the
  * previous iteration + select, then pooled rollouts) in a CUDA graph of 64
  * iterations; rollout CTAs pool trees_per_cta trees with warps_per_cta warps,
  * and the CTAs are split into `chains` (1..16) independent chains on
