@@ -40,11 +40,11 @@ PHILOX_OPS_PER_WORD = 25  # Philox-4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 4
 VALUE_MACS_PER_LEAF = 640 * 512 + 2 * 512 * 512 + 512 * 4  # dense layers of the value network
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # DRAM bytes per launch of the pipeline's kernels at the default shape of the
-# 4,096-tree workload (16 chains of 256 trees; 2 trees x 16 warps per rollout
-# CTA), from ncu full captures (cold cache) summarised under profiles/
-# (pipe_select_kernel / pipe_rollout_kernel / pipe_det_kernel _2p24_4096trees_64it.md).
-PROFILED_SHAPE = (16, 2, 16)
-DRAM_PER_LAUNCH = {"select": 306_432, "rollout": 81_536, "det": 289_792}
+# 4,096-tree workload (24 chains of 170 or 171 trees; 2 trees x 16 warps per
+# rollout CTA), from ncu captures (cold cache) summarised under profiles/
+# (dram_per_launch_2p24_4096trees_24chains.md).
+PROFILED_SHAPE = (24, 2, 16)
+DRAM_PER_LAUNCH = {"select": 399_941, "rollout": 73_061, "det": 206_464}
 
 
 def _env_int(k, d):
@@ -232,10 +232,10 @@ def run_ours(args, w):
     budgets = w.budgets()
     forest = dvc.Forest(ctx, roots, budgets, w.seed, tree_ids=shard_tree_ids(rank, n))
     # launch shape: the pipeline in CUDA graphs with the library's default
-    # shape -- round(n / (1.7 SMs)) overlapping chains (at most 16), at least
+    # shape -- round(n / (1.12 SMs)) overlapping chains (at most 24), at least
     # 2 trees per rollout CTA, warps for one playout per thread -- unless overridden
     sms = props.multi_processor_count
-    chains = args.chains or max(1, min(16, round(n / (1.7 * sms))))
+    chains = args.chains or max(1, min(24, round(n / (1.12 * sms))))
     trees_per_cta = args.trees_per_cta or max(2, min(64, math.ceil(n / (chains * 0.85 * sms))))
     warps = args.warps or max(4, min(16, (trees_per_cta * w.playouts + 31) // 32))
     forest.dvc_forest_tune(2, trees_per_cta, warps, chains)

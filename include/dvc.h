@@ -255,14 +255,14 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
  * determinizations of every tree, one thread each).  engine 2: per iteration two launches (backprop of the
  * previous iteration + select, then pooled rollouts) in a CUDA graph of 64
  * iterations; rollout CTAs pool trees_per_cta trees with warps_per_cta warps,
- * and the CTAs are split into `chains` (1..16) independent chains on
+ * and the CTAs are split into `chains` (1..32) independent chains on
  * separate streams so that one chain's tree walks run beside another chain's
  * playouts.  The determinizations of the graph's 64 iterations are sampled
  * up front, one thread per tree and iteration.  engine 0 keeps the current
  * engine (the default is 2 for forests of at least two trees per SM, else 1).
  * trees_per_cta, warps_per_cta, chains 0 = the engine's defaults (fused:
  * ceil(n_trees / SMs) trees, at most 32, and one warp per tree up to 16;
- * pipeline: round(n_trees / (1.7 SMs)) chains, at most 16; at least 2 trees,
+ * pipeline: round(n_trees / (1.12 SMs)) chains, at most 24; at least 2 trees,
  * ceil(n_trees / (0.85 chains SMs)), at most 64; warps for one playout per
  * thread, 4 to 16).  Changing
  * trees_per_cta re-balances which trees share a CTA (longest budget first,

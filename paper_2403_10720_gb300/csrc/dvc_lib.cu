@@ -19,7 +19,8 @@ using namespace dvc;
 using namespace dvc_host;
 
 namespace {
-constexpr int kMaxChains = 16;  // independent chains of the pipeline graph
+constexpr int kMaxChains = 32;  // independent chains of the pipeline graph
+constexpr int kValueChains = 16;  // at most, in value mode (each chain pads its leaves to 128 rows)
 
 // Default launch shape of an engine for n trees on `sms` SMs with P playouts
 // per leaf.  Pipeline: small rollout CTAs of at least two trees, warps enough
@@ -30,7 +31,7 @@ constexpr int kMaxChains = 16;  // independent chains of the pipeline graph
 void default_shape(int n, int sms, int engine, int P, int& T, int& W, int& chains) {
     const int S = std::max(sms, 1);
     if (engine == 2) {
-        chains = std::max(1, std::min(kMaxChains, (int)std::lround(n / (1.7 * S))));
+        chains = std::max(1, std::min(24, (int)std::lround(n / (1.12 * S))));
         T = std::max(2, std::min(64, (int)std::ceil(n / (chains * 0.85 * S))));
         W = std::max(4, std::min(16, (T * std::max(P, 1) + 31) / 32));
     } else {
@@ -1162,7 +1163,7 @@ void value_chain(const dvc_forest* f, int k, int chains, int& t0, int& t1, int& 
     }
 }
 
-int value_chains(const dvc_forest* f) { return std::max(1, std::min({kMaxChains, f->chains, f->n / 128})); }
+int value_chains(const dvc_forest* f) { return std::max(1, std::min({kValueChains, f->chains, f->n / 128})); }
 
 // One value-mode iteration of chain k: (pending backprop +) select, the
 // network over the chain's leaves, credit.
@@ -1264,7 +1265,7 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     if (engine < 0 || engine > 2 || trees_per_cta < 0 || trees_per_cta > 64 || warps_per_cta < 0 ||
         warps_per_cta > 32 || chains < 0 || chains > kMaxChains)
         return fail(f->ctx, DVC_E_INVALID,
-                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..16");
+                    "dvc_forest_tune: engine 0..2, trees_per_cta 0..64, warps_per_cta 0..32, chains 0..32");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, f->ctx->device);
     const int eng = engine ? engine : f->engine;
