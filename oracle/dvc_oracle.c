@@ -33,11 +33,13 @@
  * a closed-form 1/k endgame; exact win probabilities of tiny endgames by an
  * independent exhaustive enumerator; determinizer counts against brute-force
  * enumeration plus a chi-square test; UCB1 selection on a forced-win toy tree;
- * visit-count invariants.  The value-network functions are pinned by finite
- * differences and by a closed-form single-layer case.
+ * visit-count invariants; the full game tree's STOP action and kept turn; the
+ * ordering-aware policy against the enumerator; vanilla MCTS-dvc's set layer
+ * against the determinizer's samples.  The value-network functions are pinned
+ * by finite differences and by a closed-form single-layer case.
  *
- * Readings of points the paper leaves open are listed in the design doc; the ones
- * that shape code are repeated beside that code.
+ * Where the paper leaves a point open, the reading taken is stated beside the
+ * code it shapes.
  */
 #include <math.h>
 #include <stdint.h>
