@@ -259,9 +259,10 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
  * separate streams so that one chain's tree walks run beside another chain's
  * playouts.  The determinizations of the graph's 64 iterations are sampled
  * up front, one thread per tree and iteration.  engine 0 keeps the current
- * engine (the default is 2 for forests of at least two trees per SM, else 1).
+ * engine (the default is 2 for forests of more than four trees per SM, else 1).
  * trees_per_cta, warps_per_cta, chains 0 = the engine's defaults (fused:
- * ceil(n_trees / SMs) trees, at most 32, and one warp per tree up to 16;
+ * ceil(n_trees / SMs) trees, at most 32, and a warp per tree or one playout
+ * per thread, whichever is more, up to 16 warps;
  * pipeline: round(n_trees / (1.12 SMs)) chains, at most 24; at least 2 trees,
  * ceil(n_trees / (0.85 chains SMs)), at most 64; warps for one playout per
  * thread, 4 to 16).  Changing

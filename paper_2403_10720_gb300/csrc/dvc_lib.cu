@@ -35,8 +35,9 @@ void default_shape(int n, int sms, int engine, int P, int& T, int& W, int& chain
         T = std::max(2, std::min(64, (int)std::ceil(n / (chains * 0.85 * S))));
         W = std::max(4, std::min(16, (T * std::max(P, 1) + 31) / 32));
     } else {
+        // a warp per tree, and enough warps for one playout per thread (16 at most)
         T = std::max(1, std::min(32, (n + S - 1) / S));
-        W = std::min(T, 16);
+        W = std::min(16, std::max(T, (T * std::max(P, 1) + 31) / 32));
         chains = 1;
     }
 }
@@ -836,7 +837,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     // enough trees to fill the GPU: the pipeline; small forests: the fused
     // lockstep kernel
-    f->engine = n >= 2 * std::max(sms, 1) ? 2 : 1;
+    f->engine = n > 4 * std::max(sms, 1) ? 2 : 1;
     default_shape(n, sms, f->engine, c->cfg.playouts, f->trees_per_cta, f->warps_per_cta, f->chains);
     std::vector<int32_t> order(n);
     {
