@@ -24,8 +24,9 @@ Pin status per function:
                       elimination, empty pool, the draw that follows; STOP and
                       a kept turn in the full game of Fig. 2a)
   mcts, vanilla ..... pinned (plausible-set nodes against the determinizer's
-                      samples: count, creation order, visits; the decision
-                      summed over sets)
+                      samples: count, creation order, visits, the observer's
+                      wins; joker places separate sets; a new set is a leaf;
+                      the decision summed over sets)
   mcts, full tree ... pinned (a correct in-tree guess keeps the turn: STOP nodes
                       below it; visit-count invariants; the playout coin at a
                       may-stop leaf against exact enumeration)

@@ -21,6 +21,8 @@
  *   plausible numbers sampled .... Sec. III-A (determinization per simulation)
  *   stop after a correct guess ... Sec. III-A, simplification 2 (inside the tree)
  *   expansion depth limit ........ Sec. III-A, simplification 3
+ *   plausible-set nodes (vanilla)  Sec. III-A, the tree simplification 1 removes
+ *   continue / stop nodes ........ Fig. 2a, the tree simplification 2 removes
  *   root-parallel merge .......... Sec. III-B
  *   Philox-4x32-10 ............... Salmon, Moraes, Dror, Shaw, "Parallel Random
  *                                  Numbers: As Easy as 1, 2, 3", SC'11
