@@ -1,5 +1,6 @@
 """Pins for the oracle's Philox-4x32-10 and its ln (no GPU)."""
 import math
+import os
 import struct
 
 import numpy as np
@@ -8,16 +9,19 @@ import pytest
 import oracle
 
 
-# Known-answer vectors published with Philox (Salmon et al., SC'11, Random123
-# distribution, kat_vectors: philox4x32 with 10 rounds).
-KAT = [
-    ([0x00000000, 0x00000000, 0x00000000, 0x00000000], [0x00000000, 0x00000000],
-     [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
-    ([0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF], [0xFFFFFFFF, 0xFFFFFFFF],
-     [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
-    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
-     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
-]
+def _kat():
+    # known-answer vectors published with Philox (fixture cites the source)
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    out = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out.append((w[0:4], w[4:6], w[6:10]))
+    return out
+
+
+KAT = _kat()
 
 
 @pytest.mark.parametrize("ctr,key,want", KAT)

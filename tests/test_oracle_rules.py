@@ -5,6 +5,7 @@ Sec. III-A, the closed-form 1/k endgame, and exact win probabilities of tiny
 endgames from the independent enumerator in bruteforce.py.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -136,8 +137,13 @@ def _hands_pre_draw(T):
 
 def test_root_guess_count_matches_paper():
     # Sec. III-A: with position + number as the node key the root has 88
-    # children (26 tiles, opponent holding four tiles): 4 slots x (26 - 4).
-    assert oracle.legal_count(_hands_pre_draw(26)) == 88
+    # children (26 tiles, opponent holding four tiles): 4 slots x (26 - 4);
+    # the value is read from the fixture that cites it
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_root_guesses.txt")
+    rows = [list(map(int, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
+    for tiles, face_down, held, children in rows:
+        assert face_down == 4 and held == 4
+        assert oracle.legal_count(_hands_pre_draw(tiles)) == children
     assert oracle.legal_count(_hands_pre_draw(24)) == 80
 
 
