@@ -791,7 +791,7 @@ def main():
     ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
     ap.add_argument("--move-budget", type=int, default=256, help="selfplay: UCT iterations per move")
     ap.add_argument("--queries", type=int, default=2000, help="serve: number of move queries")
-    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (queries/s)")
+    ap.add_argument("--rate", type=float, default=400.0, help="serve: Poisson arrival rate (queries/s)")
     ap.add_argument("--max-budget", type=int, default=100000, help="serve: largest query budget")
     ap.add_argument("--hbm-gb", type=float, default=64.0, help="serve: HBM budget for resident searches")
     ap.add_argument("--poll-iters", type=int, default=256, help="serve: iterations per poll")
