@@ -82,7 +82,7 @@ struct dvc_forest {
     cudaGraphExec_t chunk_exec;  // pipeline graph of kChunkIters iterations (captured on first use)
     cudaGraphExec_t value_exec;  // the same for value mode
     dvc_value_rows vrows;        // value mode: network activations, one slice per chain
-    int chains;               // independent chains in the pipeline graph (1..16)
+    int chains;               // independent chains in the pipeline graph (1..32)
     float* probs;             // value mode: win probabilities per tree
     int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
 };
