@@ -81,3 +81,33 @@ def test_forest_agents_route_and_count(monkeypatch):
         winner = (g % 2) ^ ((moves - 1) % 2)
         assert out["winners"][g] == winner
     assert out["a_wins"] == sum(int(out["winners"][g] == a_seat[g]) for g in range(n))
+
+
+class _Server:
+    def __init__(self):
+        self.queue, self.submitted = [], []
+
+    def dvc_server_submit(self, root, budget, mode, qid):
+        self.submitted.append((int(root[23]), budget, mode, qid))
+        self.queue.append(qid)
+
+    def dvc_server_poll(self, iters):
+        out = [{"query_id": q, "best_action": q} for q in self.queue[:3]]   # a few results per poll
+        self.queue = self.queue[3:]
+        return out
+
+
+def test_server_agents_route_and_count():
+    game = _Game()
+    sa, sb = _Server(), _Server()
+    n = 8
+    out = selfplay.play_agents(game, (sa, dvc.DVC_MODE_VALUE, 5), (sb, dvc.DVC_MODE_ROLLOUT, 7), n, root_seed=1,
+                               seed=9)
+    a_seat = np.arange(n) % 2
+    for srv, mode, budget, seat_of in ((sa, dvc.DVC_MODE_VALUE, 5, lambda g: a_seat[g]),
+                                       (sb, dvc.DVC_MODE_ROLLOUT, 7, lambda g: 1 - a_seat[g])):
+        assert srv.submitted
+        for mover, b, m, qid in srv.submitted:
+            assert m == mode and b == budget and mover == seat_of(qid % n)
+    assert out["decisions_a"] == len(sa.submitted) and out["decisions_b"] == len(sb.submitted)
+    assert out["games_finished"] == n and out["turns"] == 6
