@@ -17,7 +17,14 @@ Pin status per function:
                       under both playout policies)
   det_count ......... pinned (brute-force enumeration of consistent deals)
   determinize ....... pinned (chi-square against uniform over those deals)
-  mcts .............. pinned (UCB1 forced-win toy sequence, count invariants)
+  mcts .............. pinned (UCB1 forced-win toy sequence, count invariants;
+                      whole node tables of hand-solved 2- and 3-player
+                      endgames, which fix the seat each node credits at
+                      depths 1 to 3)
+  mcts, value mode .. pinned (the same hand-solved endgames with a network
+                      whose hidden weights are zero: each fresh leaf credits
+                      round(p * playouts) per seat, p = softmax of the output
+                      bias over the seats in play, relative to the mover)
   legal_actions ..... pinned (88 root guesses, canonical order written out;
                       ordering-aware policy: hand-made rows written out)
   play_move ......... pinned (hand-made positions: correct and wrong guesses,
@@ -120,6 +127,9 @@ def lib():
         L.or_mcts.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i32p,
                               ctypes.POINTER(ctypes.c_int), i32p]
         L.or_mcts.restype = ctypes.c_int
+        L.or_mcts_value.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_float), i32p, ctypes.POINTER(ctypes.c_int), i32p]
+        L.or_mcts_value.restype = ctypes.c_int
         f32p = ctypes.POINTER(ctypes.c_float)
         f64p = ctypes.POINTER(ctypes.c_double)
         L.or_value_nparams.argtypes = []
@@ -269,15 +279,25 @@ def value_loss_grad(params, states, labels):
     return loss, g
 
 
-def mcts(cfg: OracleConfig, root, seed: int, tree: int, budget: int):
+def mcts(cfg: OracleConfig, root, seed: int, tree: int, budget: int, value_params=None):
     """Returns (nodes (n, 4) int32 [action, parent, visits, wins] in creation
-    order, best (4,) int32 [action, visits, wins, root visits])."""
+    order, best (4,) int32 [action, visits, wins, root visits]).  With
+    value_params (the network's parameters, value_nparams() floats) the search
+    runs in value mode: a fresh leaf that did not end in the tree credits each
+    seat round(p * playouts) from the network instead of playing out."""
     s = _state(root)
     nodes = np.zeros((budget + 1, 4), dtype=np.int32)
     n = ctypes.c_int(0)
     best = np.zeros(4, dtype=np.int32)
     c = cfg.c()
-    rc = lib().or_mcts(ctypes.byref(c), _u8(s), seed, tree, budget, _i32(nodes), ctypes.byref(n), _i32(best))
+    if value_params is None:
+        rc = lib().or_mcts(ctypes.byref(c), _u8(s), seed, tree, budget, _i32(nodes), ctypes.byref(n), _i32(best))
+    else:
+        prm = np.ascontiguousarray(value_params, dtype=np.float32)
+        assert prm.size == value_nparams()
+        rc = lib().or_mcts_value(ctypes.byref(c), _u8(s), seed, tree, budget,
+                                 prm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _i32(nodes),
+                                 ctypes.byref(n), _i32(best))
     if rc:
         raise ValueError(f"or_mcts rc={rc}")
     return nodes[: n.value].copy(), best

@@ -978,13 +978,22 @@ static int tree_new_node(otree* t, int parent, int code) {
     return id;
 }
 
+int or_value_forward(const float* prm, const uint8_t* packed, double* probs);
+
 /* One search of `budget` iterations from `root` (observer = player to move):
  * determinize, descend by UCT among children legal in this determinization,
  * expand the first legal action without a child (canonical order) while the
- * depth is below d_max, run `playouts` random playouts from the leaf, and add
- * the playout count to every visit and the wins of each node's mover. */
-int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
-            int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
+ * depth is below d_max, score the leaf, and add the playout count to every
+ * visit and the leaf's credit for each node's mover to its wins (a node's
+ * wins are those of the seat that moved into it; the root's are the
+ * observer's).  The leaf's credit per seat: a leaf that ended inside the tree
+ * gives all `playouts` to its winner; otherwise, with value_prm NULL, the
+ * wins of `playouts` random playouts (Sec. II-B); with value_prm set (value
+ * mode, no counterpart in the paper: the learned evaluator stands in for the
+ * playouts), round(p_s * playouts) = floor(p_s * playouts + 0.5) for each
+ * seat s, p the network's win probabilities of the leaf. */
+static int mcts_run(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
+                    const float* value_prm, int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
     ost root;
     unpack(root_packed, &root);
     int obs = root.cur;
@@ -1068,6 +1077,12 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
         int32_t wins[4] = {0, 0, 0, 0};
         if (s.winner >= 0) {
             wins[s.winner] = P;
+        } else if (value_prm) {
+            uint8_t leaf[32];
+            double p[4];
+            pack(&s, leaf);
+            if (or_value_forward(value_prm, leaf, p)) { rc = -1; break; }
+            for (int q = 0; q < 4; q++) wins[q] = (int32_t)floor(p[q] * (double)P + 0.5);
         } else {
             uint8_t leaf[32];
             pack(&s, leaf);
@@ -1127,6 +1142,20 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
     free(mem);
     free(t.key);
     return rc;
+}
+
+int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
+            int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
+    return mcts_run(cfg, root_packed, seed, tree_id, budget, NULL, nodes_out, n_nodes_out, best_out);
+}
+
+/* The same search in value mode: every fresh leaf that did not end inside the
+ * tree is credited from the value network (parameters `prm`, layout below)
+ * instead of playouts. */
+int or_mcts_value(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
+                  const float* prm, int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
+    if (!prm) return -1;
+    return mcts_run(cfg, root_packed, seed, tree_id, budget, prm, nodes_out, n_nodes_out, best_out);
 }
 
 /* ------------------------------------------------------------- value net */
