@@ -21,8 +21,10 @@
  *   - returns 0 on success or a negative DVC_E_* code; dvc_last_error() gives
  *     a message.  No C++ exception crosses this boundary.
  *   - pointers named d_* are DEVICE memory owned by the caller (for example
- *     PyTorch tensors passed as raw pointers); h_* are host memory owned by
- *     the caller.  The library owns only its context, forests and workspace.
+ *     PyTorch tensors passed as raw pointers), of the context's device (or
+ *     managed memory): a pointer into another GPU's memory is DVC_E_INVALID;
+ *     h_* are host memory owned by the caller.  The library owns only its
+ *     context, forests and workspace.
  *   - work is enqueued on the given CUDA stream (cudaStream_t passed as void*;
  *     NULL = legacy default stream); outputs are valid after that stream is
  *     synchronised.  Arguments are validated on the host before anything is
@@ -313,18 +315,25 @@ int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream);
  * cudaMalloc: a process whose device memory is fully reserved by another
  * framework's caching allocator, or one that may not allocate after start-up.
  * The paper has no counterpart; this is a deployment variant of
- * dvc_determinize and returns the same records for the same arguments.
- * It needs no context: it runs on the calling thread's current device.  Its
- * scratch is a fixed 8 MiB device array inside the library (64 roots x
- * 16,384 table cells), held by every GPU that loads the library until exit.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (nothing in
- * it needs to start at zero); calls that overlap on the GPU race on it, so
- * issue them on one stream.  n > 64 returns DVC_E_UNSUPPORTED and enqueues
- * nothing.  d_status (optional, n int32): 0, or DVC_E_UNSUPPORTED for a view
- * whose table needs more than 16,384 cells (that output is the root).  Calls
- * no cudaMalloc or cudaFree.
+ * dvc_determinize.  For views whose counting table fits 16,384 cells and an
+ * observer below each root's player count (or -1, the seat to move) it
+ * returns the same records as dvc_determinize for the same arguments.
+ * It needs no context: it runs on the calling thread's current device, and
+ * every pointer must be memory of that device (or managed memory); any other
+ * pointer, or d_out overlapping d_roots, returns DVC_E_INVALID and enqueues
+ * nothing.  Its scratch is a fixed 8 MiB device array inside the library
+ * (64 roots x 16,384 table cells), held by every GPU that loads the library
+ * until exit.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (nothing in it needs to start at zero); calls that overlap on the GPU race
+ * on it, so issue them on one stream.  n > 64 returns DVC_E_UNSUPPORTED and
+ * enqueues nothing.  d_status (optional, n int32) per root: 0; DVC_E_INVALID
+ * when observer >= that root's player count (dvc_determinize refuses such a
+ * call on the host); DVC_E_UNSUPPORTED for a view whose table needs more
+ * than 16,384 cells (dvc_determinize handles up to 32,768).  In both error
+ * cases that output record is the root itself.  Calls no cudaMalloc or
+ * cudaFree.
  */
 int dvc_determinize_noalloc(const dvc_state* d_roots, int n, int observer, uint64_t seed,
                             const uint32_t* d_tree_ids, const uint32_t* d_iter_ids, dvc_state* d_out,

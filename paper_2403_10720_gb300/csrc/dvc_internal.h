@@ -54,14 +54,24 @@ inline int cuda_fail(dvc_ctx* c, cudaError_t e, const char* where) {
     return fail(c, DVC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-inline bool is_device_ptr(const void* p) {
+// Device memory of device `dev` (the context's), or managed memory.  A pointer
+// into another GPU's memory is refused: kernels run on the context's device
+// and would fault on a peer's memory without peer access.
+inline bool is_device_ptr(const void* p, int dev) {
     if (!p) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// [a, a + bytes) and [b, b + bytes) share a byte.
+inline bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + bytes && b0 < a0 + bytes;
 }
 
 

@@ -682,7 +682,7 @@ int dvc_philox(dvc_ctx* c, int n, const uint32_t* d_ctr, const uint32_t* d_key, 
     if (!c) return DVC_E_INVALID;
     if (n < 0) return fail(c, DVC_E_INVALID, "dvc_philox: n < 0");
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_ctr) || !is_device_ptr(d_key) || !is_device_ptr(d_out))
+    if (!is_device_ptr(d_ctr, c->device) || !is_device_ptr(d_key, c->device) || !is_device_ptr(d_out, c->device))
         return fail(c, DVC_E_INVALID, "dvc_philox: pointers must be device memory");
     if (int rc = set_device(c)) return rc;
     philox_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, d_ctr, d_key, d_out, use_reference);
@@ -693,7 +693,7 @@ int dvc_init_states(dvc_ctx* c, uint64_t seed, int n, dvc_state* d_states, void*
     if (!c) return DVC_E_INVALID;
     if (n < 0) return fail(c, DVC_E_INVALID, "dvc_init_states: n < 0");
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_states)) return fail(c, DVC_E_INVALID, "dvc_init_states: d_states must be device memory");
+    if (!is_device_ptr(d_states, c->device)) return fail(c, DVC_E_INVALID, "dvc_init_states: d_states must be device memory");
     if (int rc = set_device(c)) return rc;
     init_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(c->cfg, seed, n, d_states);
     return check_launch(c, "init_kernel");
@@ -704,10 +704,11 @@ int dvc_determinize(dvc_ctx* c, const dvc_state* d_roots, int n, int observer, u
     if (!c) return DVC_E_INVALID;
     if (n < 0 || observer >= c->cfg.nplayers) return fail(c, DVC_E_INVALID, "dvc_determinize: bad n or observer");
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_roots) || !is_device_ptr(d_tree_ids) || !is_device_ptr(d_iter_ids) ||
-        !is_device_ptr(d_out))
+    if (!is_device_ptr(d_roots, c->device) || !is_device_ptr(d_tree_ids, c->device) || !is_device_ptr(d_iter_ids, c->device) ||
+        !is_device_ptr(d_out, c->device))
         return fail(c, DVC_E_INVALID, "dvc_determinize: pointers must be device memory");
-    if (d_roots == d_out) return fail(c, DVC_E_INVALID, "dvc_determinize: d_out may not alias d_roots");
+    if (ranges_overlap(d_roots, d_out, sizeof(dvc_state) * (size_t)n))
+        return fail(c, DVC_E_INVALID, "dvc_determinize: d_out may not overlap d_roots");
     if (int rc = set_device(c)) return rc;
     if (!c->d_ws) {
         const size_t cells = (size_t)kDetChunk * kDetMaxCells;
@@ -734,8 +735,8 @@ int dvc_rollout_batch(dvc_ctx* c, const dvc_state* d_leaves, int n_leaves, int p
     if (!c) return DVC_E_INVALID;
     if (n_leaves < 0 || playouts_per_leaf < 1) return fail(c, DVC_E_INVALID, "dvc_rollout_batch: bad sizes");
     if (n_leaves == 0) return DVC_OK;
-    if (!is_device_ptr(d_leaves) || !is_device_ptr(d_tree_ids) || !is_device_ptr(d_leaf_ids) ||
-        !is_device_ptr(d_wins) || (d_words && !is_device_ptr(d_words)))
+    if (!is_device_ptr(d_leaves, c->device) || !is_device_ptr(d_tree_ids, c->device) || !is_device_ptr(d_leaf_ids, c->device) ||
+        !is_device_ptr(d_wins, c->device) || (d_words && !is_device_ptr(d_words, c->device)))
         return fail(c, DVC_E_INVALID, "dvc_rollout_batch: pointers must be device memory");
     if (int rc = set_device(c)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -764,7 +765,7 @@ int dvc_play_move(dvc_ctx* c, dvc_state* d_states, int n, const int32_t* d_actio
     if (!c) return DVC_E_INVALID;
     if (n < 0) return fail(c, DVC_E_INVALID, "dvc_play_move: n < 0");
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_states) || !is_device_ptr(d_actions) || (d_game_ids && !is_device_ptr(d_game_ids)))
+    if (!is_device_ptr(d_states, c->device) || !is_device_ptr(d_actions, c->device) || (d_game_ids && !is_device_ptr(d_game_ids, c->device)))
         return fail(c, DVC_E_INVALID, "dvc_play_move: pointers must be device memory");
     if (int rc = set_device(c)) return rc;
     play_move_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_states, n, d_actions, seed, d_game_ids, turn,
@@ -800,7 +801,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     if (!c) return DVC_E_INVALID;
     if (!out || n < 1 || !h_budgets) return fail(c, DVC_E_INVALID, "dvc_forest_create: bad arguments");
     *out = nullptr;
-    if (!is_device_ptr(d_roots)) return fail(c, DVC_E_INVALID, "dvc_forest_create: d_roots must be device memory");
+    if (!is_device_ptr(d_roots, c->device)) return fail(c, DVC_E_INVALID, "dvc_forest_create: d_roots must be device memory");
     for (int i = 0; i < n; ++i)
         if (h_budgets[i] < 0 || h_budgets[i] > (1 << 24))
             return fail(c, DVC_E_INVALID, "dvc_forest_create: budgets must be in 0..2^24");
@@ -935,7 +936,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
 
 int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream) {
     if (!f) return DVC_E_INVALID;
-    if (d_roots && !is_device_ptr(d_roots))
+    if (d_roots && !is_device_ptr(d_roots, f->ctx->device))
         return fail(f->ctx, DVC_E_INVALID, "dvc_forest_reset: d_roots must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
     forest_init_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
@@ -1342,7 +1343,7 @@ int dvc_mcts_expand(dvc_forest* f, void* stream) {
 
 int dvc_mcts_backprop(dvc_forest* f, const int32_t* d_wins, void* stream) {
     if (!f) return DVC_E_INVALID;
-    if (!is_device_ptr(d_wins)) return fail(f->ctx, DVC_E_INVALID, "dvc_mcts_backprop: d_wins must be device memory");
+    if (!is_device_ptr(d_wins, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_mcts_backprop: d_wins must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
     mcts_backprop_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
         dev_of(f), params_of(f), f->n, f->work, f->paths, f->movers, d_wins);
@@ -1351,7 +1352,7 @@ int dvc_mcts_backprop(dvc_forest* f, const int32_t* d_wins, void* stream) {
 
 int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream) {
     if (!f) return DVC_E_INVALID;
-    if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_counters: d_out must be device memory");
+    if (!is_device_ptr(d_out, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_counters: d_out must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(d_out, f->d_words, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
@@ -1370,7 +1371,7 @@ int dvc_forest_leaves(dvc_forest* f, dvc_state** d_leaves, uint32_t** d_tree_ids
 
 int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream) {
     if (!f) return DVC_E_INVALID;
-    if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_root_stats: d_out must be device memory");
+    if (!is_device_ptr(d_out, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_root_stats: d_out must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
     if (f->ctx->cfg.vanilla) {
         root_stats_vanilla_kernel<<<f->n, 256, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_out);
@@ -1383,7 +1384,7 @@ int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream) {
 int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream) {
     if (!f) return DVC_E_INVALID;
     if (tree < 0 || tree >= f->n) return fail(f->ctx, DVC_E_INVALID, "dvc_tree_export: tree out of range");
-    if (!is_device_ptr(d_out)) return fail(f->ctx, DVC_E_INVALID, "dvc_tree_export: d_out must be device memory");
+    if (!is_device_ptr(d_out, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_tree_export: d_out must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
     const int32_t budget = f->h_budgets[tree];
     if (budget > f->export_cap) {

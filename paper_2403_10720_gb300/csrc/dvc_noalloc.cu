@@ -33,14 +33,24 @@ __device__ __align__(256) unsigned long long g_det_scratch[(size_t)kNoAllocRoots
 void* g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mutex;
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (the one the kernel will run on), or managed
+// memory.  A pointer into another GPU's memory is refused: the kernel would
+// read and write a peer's memory, which faults without peer access.
+bool on_device(const void* p, int dev) {
     if (!p) return false;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// [a, a + n) and [b, b + n) records share a byte.
+bool overlaps(const dvc_state* a, const dvc_state* b, int n) {
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b, len = sizeof(dvc_state) * (uintptr_t)n;
+    return a0 < b0 + len && b0 < a0 + len;
 }
 
 __global__ void determinize_noalloc_kernel(const dvc_state* roots, int n, int observer, uint64_t seed,
@@ -49,6 +59,11 @@ __global__ void determinize_noalloc_kernel(const dvc_state* roots, int n, int ob
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     const G g = load_state(roots[idx]);
+    if (observer >= (int)g.np) {  // no such seat in this root's game
+        out[idx] = roots[idx];
+        if (status) status[idx] = DVC_E_INVALID;
+        return;
+    }
     const uint32_t obs = observer < 0 ? g.cur : (uint32_t)observer;
     DetPlan pl;
     det_plan(g, obs, pl);
@@ -75,15 +90,15 @@ extern "C" int dvc_determinize_noalloc(const dvc_state* d_roots, int n, int obse
     if (n < 0 || observer >= 4) return DVC_E_INVALID;
     if (n > kNoAllocRoots) return DVC_E_UNSUPPORTED;
     if (n == 0) return DVC_OK;
-    if (!on_device(d_roots) || !on_device(d_tree_ids) || !on_device(d_iter_ids) || !on_device(d_out) ||
-        (d_status && !on_device(d_status)))
-        return DVC_E_INVALID;
-    if (d_roots == d_out) return DVC_E_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return DVC_E_CUDA;
     }
+    if (!on_device(d_roots, dev) || !on_device(d_tree_ids, dev) || !on_device(d_iter_ids, dev) ||
+        !on_device(d_out, dev) || (d_status && !on_device(d_status, dev)))
+        return DVC_E_INVALID;
+    if (overlaps(d_roots, d_out, n)) return DVC_E_INVALID;
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mutex);

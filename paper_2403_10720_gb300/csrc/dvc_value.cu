@@ -519,7 +519,7 @@ int colsum(dvc_ctx* c, const float* A, int R, int C, float* out, int cols_out, c
 int check_states_args(dvc_ctx* c, const void* d_states, int n) {
     if (n < 0) return fail(c, DVC_E_INVALID, "value network: n < 0");
     if (n > (1 << 24)) return fail(c, DVC_E_UNSUPPORTED, "value network: more than 2^24 rows");
-    if (n > 0 && !is_device_ptr(d_states)) return fail(c, DVC_E_INVALID, "value network: states must be device memory");
+    if (n > 0 && !is_device_ptr(d_states, c->device)) return fail(c, DVC_E_INVALID, "value network: states must be device memory");
     return DVC_OK;
 }
 
@@ -544,7 +544,7 @@ int dvc_value_init(dvc_ctx* c, uint64_t seed, void* stream) {
 
 int dvc_value_params(dvc_ctx* c, float* d_params, int direction, void* stream) {
     if (!c) return DVC_E_INVALID;
-    if (!is_device_ptr(d_params) || (direction != 0 && direction != 1))
+    if (!is_device_ptr(d_params, c->device) || (direction != 0 && direction != 1))
         return fail(c, DVC_E_INVALID, "dvc_value_params: device pointer and direction 0 (out) or 1 (in)");
     if (int rc = set_device(c)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -563,7 +563,7 @@ int dvc_value_features(dvc_ctx* c, const dvc_state* d_states, int n, float* d_ou
     if (!c) return DVC_E_INVALID;
     if (int rc = check_states_args(c, d_states, n)) return rc;
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_out)) return fail(c, DVC_E_INVALID, "dvc_value_features: d_out must be device memory");
+    if (!is_device_ptr(d_out, c->device)) return fail(c, DVC_E_INVALID, "dvc_value_features: d_out must be device memory");
     if (int rc = set_device(c)) return rc;
     features_kernel<<<(n * 32 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_states, n, n, nullptr, d_out);
     return check_launch(c, "features_kernel");
@@ -573,7 +573,7 @@ int dvc_value_eval(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_winpro
     if (!c) return DVC_E_INVALID;
     if (int rc = check_states_args(c, d_leaves, n)) return rc;
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_winprob)) return fail(c, DVC_E_INVALID, "dvc_value_eval: d_winprob must be device memory");
+    if (!is_device_ptr(d_winprob, c->device)) return fail(c, DVC_E_INVALID, "dvc_value_eval: d_winprob must be device memory");
     if (int rc = set_device(c)) return rc;
     if (int rc = need_net(c)) return rc;
     const int npad = (n + 127) / 128 * 128;
@@ -589,7 +589,7 @@ int dvc_value_train_step(dvc_ctx* c, const dvc_state* d_states, const float* d_l
     if (!c) return DVC_E_INVALID;
     if (int rc = check_states_args(c, d_states, n)) return rc;
     if (n == 0) return DVC_OK;
-    if (!is_device_ptr(d_labels) || (d_loss && !is_device_ptr(d_loss)) || !(lr >= 0.0f))
+    if (!is_device_ptr(d_labels, c->device) || (d_loss && !is_device_ptr(d_loss, c->device)) || !(lr >= 0.0f))
         return fail(c, DVC_E_INVALID, "dvc_value_train_step: device labels/loss, lr >= 0");
     if (int rc = set_device(c)) return rc;
     if (int rc = need_net(c)) return rc;
@@ -647,7 +647,7 @@ int dvc_value_train_step(dvc_ctx* c, const dvc_state* d_states, const float* d_l
 
 int dvc_value_grads(dvc_ctx* c, float* d_out, void* stream) {
     if (!c) return DVC_E_INVALID;
-    if (!is_device_ptr(d_out)) return fail(c, DVC_E_INVALID, "dvc_value_grads: d_out must be device memory");
+    if (!is_device_ptr(d_out, c->device)) return fail(c, DVC_E_INVALID, "dvc_value_grads: d_out must be device memory");
     if (int rc = need_net(c)) return rc;
     if (int rc = set_device(c)) return rc;
     const cudaError_t e =
@@ -711,8 +711,8 @@ int dvc_gemm_bf16(dvc_ctx* c, const void* d_A, const void* d_B, const float* d_b
     if (!c) return DVC_E_INVALID;
     if (M < 1 || N < 16 || N % 16 || K < 64 || K % 64 || (act != kActNone && act != kActGelu))
         return fail(c, DVC_E_INVALID, "dvc_gemm_bf16: M >= 1, N % 16 == 0, K % 64 == 0, act 0 or 1");
-    if (!is_device_ptr(d_A) || !is_device_ptr(d_B) || (d_bias && !is_device_ptr(d_bias)) ||
-        (d_C && !is_device_ptr(d_C)) || (d_Cf && !is_device_ptr(d_Cf)) || (!d_C && !d_Cf))
+    if (!is_device_ptr(d_A, c->device) || !is_device_ptr(d_B, c->device) || (d_bias && !is_device_ptr(d_bias, c->device)) ||
+        (d_C && !is_device_ptr(d_C, c->device)) || (d_Cf && !is_device_ptr(d_Cf, c->device)) || (!d_C && !d_Cf))
         return fail(c, DVC_E_INVALID, "dvc_gemm_bf16: device pointers, at least one output");
     if (int rc = set_device(c)) return rc;
     const cudaError_t e = gemm((const __nv_bfloat16*)d_A, (const __nv_bfloat16*)d_B, d_bias, (__nv_bfloat16*)d_C, d_Cf,
