@@ -62,6 +62,9 @@ extern "C" {
 #define DVC_E_CUDA (-3)        /* a CUDA runtime call failed */
 #define DVC_E_TIMEOUT (-4)     /* a bounded device wait gave up */
 #define DVC_E_UNSUPPORTED (-5) /* a size beyond a documented capacity */
+#define DVC_E_INTERNAL (-6)    /* a device-side invariant failed: a playout still running after 128 guesses
+                                  (a game has at most |T| guesses, each turning one tile face up); that
+                                  playout credits nobody */
 
 #define DVC_MODE_ROLLOUT 0 /* leaves are scored by random playouts (Sec. II-B) */
 #define DVC_MODE_VALUE 1   /* leaves are scored by the value network */

@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libdvc.so")
 DVC_OK = 0
 DVC_MODE_ROLLOUT = 0
 DVC_MODE_VALUE = 1
-ERRORS = {-1: "DVC_E_INVALID", -2: "DVC_E_OOM", -3: "DVC_E_CUDA", -4: "DVC_E_TIMEOUT", -5: "DVC_E_UNSUPPORTED"}
+ERRORS = {-1: "DVC_E_INVALID", -2: "DVC_E_OOM", -3: "DVC_E_CUDA", -4: "DVC_E_TIMEOUT", -5: "DVC_E_UNSUPPORTED",
+          -6: "DVC_E_INTERNAL"}
 
 
 class DvcError(RuntimeError):

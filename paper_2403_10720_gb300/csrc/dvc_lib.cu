@@ -215,7 +215,7 @@ __global__ void play_move_kernel(dvc_state* states, int n, const int32_t* action
 template <bool ORD>
 __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uint64_t seed,
                                const uint32_t* tree_ids, const uint32_t* leaf_ids, uint32_t cont_thr, int32_t* wins,
-                               unsigned long long* words) {
+                               unsigned long long* words, int32_t* flags) {
     __shared__ uint32_t s_magic[32];
     fill_magic(s_magic, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -248,6 +248,8 @@ __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uin
                 }
                 if (res == kTurnOver) next_turn(g, r);
             }
+            // at most |T| guesses per game: no winner after 128 is a broken invariant
+            if (winner == kNone) latch_error(flags, DVC_E_INTERNAL);
             my_words += r.used();
         }
         if (winner < 4u) atomicAdd(&wins[4 * l + (int)winner], 1);
@@ -752,11 +754,11 @@ int dvc_rollout_batch(dvc_ctx* c, const dvc_state* d_leaves, int n_leaves, int p
     if (c->cfg.policy)
         rollout_kernel<true><<<(unsigned)blocks, block, 0, st>>>(d_leaves, n_leaves, playouts_per_leaf, seed,
                                                                  d_tree_ids, d_leaf_ids, c->cfg.cont_thr, d_wins,
-                                                                 (unsigned long long*)d_words);
+                                                                 (unsigned long long*)d_words, c->d_flags);
     else
         rollout_kernel<false><<<(unsigned)blocks, block, 0, st>>>(d_leaves, n_leaves, playouts_per_leaf, seed,
                                                                   d_tree_ids, d_leaf_ids, c->cfg.cont_thr, d_wins,
-                                                                  (unsigned long long*)d_words);
+                                                                  (unsigned long long*)d_words, c->d_flags);
     return check_launch(c, "rollout_kernel");
 }
 
@@ -910,6 +912,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->pipe.det_base, 0xC0, sizeof(int32_t) * n, st);  // none ahead
+    f->pipe.flags = c->d_flags;
     if (e != cudaSuccess) {
         dvc_forest_destroy(f);
         return cuda_fail(c, e, "dvc_forest_create copy");

@@ -25,6 +25,7 @@ struct PipeBufs {
     dvc_state* det;     // per tree, kDetAhead determinized roots: iterations det_base .. det_base + kDetAhead - 1
     uint4* tree0;       // per tree, kDetAhead first blocks of the iterations' tree streams (tag 3)
     int32_t* det_base;  // per tree; far below zero (bytes 0xC0) when nothing is sampled ahead
+    int32_t* flags;     // the context's latched error
 };
 
 __global__ void pipe_begin_kernel(ForestDev F, int n, int n_iter, int32_t* step_end) {
@@ -264,6 +265,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
             }
             ++steps;
             if (res == kGameOver || steps >= 128u) {
+                // a game has at most |T| guesses (each turns one tile face up),
+                // so 128 steps means a broken invariant: latch it, credit nobody
+                if (res != kGameOver) latch_error(P.flags, DVC_E_INTERNAL);
                 const uint32_t w = res == kGameOver ? winner : kNone;
                 if (w < 4u) atomicAdd(&s_wins[4 * k + w], 1);
                 words += r.used();

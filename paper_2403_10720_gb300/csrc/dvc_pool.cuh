@@ -253,6 +253,8 @@ __global__ void __launch_bounds__(MAXT, 1)
                     }
                     ++steps;
                     if (res == kGameOver || steps >= 128) {
+                        // at most |T| guesses per game: 128 steps is a broken invariant
+                        if (res != kGameOver) latch_error(F.flags, DVC_E_INTERNAL);
                         const uint32_t w = res == kGameOver ? winner : kNone;
                         if (w < 4u) atomicAdd(&s_wins[4 * slot + (int)w], 1);
                         words += r.used();

@@ -294,7 +294,7 @@ def test_uneven_workload_sampled(dvc):
     # two players, 24 tiles: the playout fast path with its shared-memory word rings
     ("2p24", (2, 3, 16, 4)), ("2p24", (2, 7, 16, 2)), ("2p24", (2, 2, 8, 3)), ("2p24", (2, 11, 32, 1)),
     ("2p24", (1, 4, 16, 0)),
-    # several playouts per thread: pool refills, then lane compaction once the pool is empty
+    # several playouts per thread: each lane refills from its CTA's pool of playouts as games end
     ("2p24", (2, 11, 4, 1)), ("2p24", (2, 6, 2, 2)),
 ])
 def test_mcts_launch_shapes_agree(dvc, variant, shape):
