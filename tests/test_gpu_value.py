@@ -105,6 +105,52 @@ def test_gradient_matches_oracle(dvc):
         assert rel < 5e-2, (a, b, rel)
 
 
+def _read_checkpoint(path):
+    """Version-1 value-network file: 'DVCV', u32 version, u64 count, i64 Adam
+    step, then FP32 master weights, first and second moments."""
+    raw = open(path, "rb").read()
+    assert raw[:4] == b"DVCV"
+    n = int(np.frombuffer(raw[8:16], dtype=np.uint64)[0])
+    step = int(np.frombuffer(raw[16:24], dtype=np.int64)[0])
+    body = np.frombuffer(raw[24:], dtype=np.float32).reshape(3, n)
+    return step, body[0].astype(np.float64), body[1].astype(np.float64), body[2].astype(np.float64)
+
+
+def test_adamw_update_matches_oracle(dvc, tmp_path):
+    """One GPU training step's optimizer update against the oracle's AdamW in
+    double, given the GPU's own gradient of that step: new master weights and
+    both moments, element by element.  The GPU computes in FP32 with its
+    constants rounded to FP32: 1 - b2 is then 1.3e-5 (relative) below 0.001,
+    and 1 - b2^t as far off, so the second moment agrees to 5e-5 relative, the
+    first to 1e-5, and the weights to 2^-22 of |w| plus 1e-4 of the step."""
+    kw = VARIANTS["3p24"]
+    ctx, _ = _net(dvc, kw, seed=5)
+    states = torch.from_numpy(oracle.init_states(oracle.OracleConfig(**kw), 51, 256)).cuda()
+    rng = np.random.default_rng(3)
+    lab = np.zeros((256, 4), dtype=np.float32)
+    lab[:, :3] = rng.dirichlet(np.ones(3), size=256)
+    labels = torch.from_numpy(lab).cuda()
+    lr = 2e-3
+    for _ in range(4):                       # non-trivial moments first
+        ctx.dvc_value_train_step(states, labels, lr)
+    a, b = tmp_path / "a.dvcv", tmp_path / "b.dvcv"
+    ctx.dvc_value_save(a)
+    ctx.dvc_value_train_step(states, labels, lr)
+    g = ctx.dvc_value_grads().cpu().numpy().astype(np.float64)
+    ctx.dvc_value_save(b)
+    ctx.dvc_check()
+    t0, w0, m0, v0 = _read_checkpoint(a)
+    t1, w1, m1, v1 = _read_checkpoint(b)
+    assert t1 == t0 + 1 == 5
+    ww, wm, wv = oracle.adamw_step(w0, m0, v0, g, t1, lr)
+    assert np.abs(m1 - wm).max() <= 1e-5 * np.abs(wm).max()
+    assert (np.abs(m1 - wm) <= 1e-5 * np.abs(wm) + 1e-12 * np.abs(wm).max()).all()
+    assert (np.abs(v1 - wv) <= 5e-5 * np.abs(wv) + 1e-12 * np.abs(wv).max()).all()
+    step = np.abs(w0 - ww)
+    assert (np.abs(w1 - ww) <= 2.0 ** -22 * np.abs(ww) + 1e-4 * step + 1e-12).all()
+    assert (step > 0).mean() > 0.5           # the update moved most parameters
+
+
 def test_training_reduces_loss_and_resumes_exactly(dvc, tmp_path):
     kw = VARIANTS["2p24"]
     ctx, _ = _net(dvc, kw, seed=3)
@@ -160,6 +206,63 @@ def test_value_mode_search(dvc):
     assert len(nodes) <= budget + 1
     for a, par, vis, w in nodes[1:]:
         assert 0 <= w <= vis and vis % 64 == 0
+
+
+def _zero_hidden_params(b4):
+    """Every weight matrix zero: the logits are the output bias b4, so the win
+    probabilities are softmax(b4) over the seats in play (relative to the
+    seat to move) in closed form, the same in FP32 and in double."""
+    prm = np.zeros(oracle.value_nparams(), dtype=np.float32)
+    prm[-4:] = b4
+    return prm
+
+
+@pytest.mark.parametrize("variant,P,budgets,chains", [
+    ("2p24", 32, [150, 57, 1, 0, 120, 96], 0),
+    ("3p24", 16, [130, 90, 3, 64], 0),
+    ("4p26j", 32, [120, 64, 100, 17, 1], 0),
+    ("2p24", 8, [100] * 300, 3),
+])
+def test_value_mode_bit_exact(dvc, variant, P, budgets, chains):
+    """Value-mode search (the network's probabilities stand in for a fresh
+    leaf's playouts, each seat credited round(p * P)) against the oracle's
+    value-mode search, node table for node table.  The network's hidden
+    weights are zero so that p is a closed form on both sides, and b4 keeps
+    every p * P at least 0.18 from a rounding tie, so FP32 on the GPU and
+    double in the oracle round alike."""
+    kw = dict(VARIANTS[variant], playouts=P)
+    nseat = kw["nplayers"]
+    b4 = np.array([0.4, -0.5, 0.0, 1.1], dtype=np.float32)
+    e = np.exp(b4[:nseat].astype(np.float64))
+    frac = (e / e.sum()) * P % 1.0
+    assert (np.abs(frac - 0.5) > 0.18).all()
+    prm = _zero_hidden_params(b4)
+    ocfg = oracle.OracleConfig(**kw)
+    n = len(budgets)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(1)
+    ctx.dvc_value_params(torch.from_numpy(prm).cuda())
+    roots = ctx.dvc_init_states(21, n)
+    oroots = oracle.init_states(ocfg, 21, n)
+    assert (roots.cpu().numpy() == oroots).all()
+    tree_ids = np.arange(n, dtype=np.uint32) * 5 + 9
+    f = dvc.Forest(ctx, roots, budgets, 8, tree_ids=tree_ids)
+    if chains:
+        f.dvc_forest_tune(0, 0, 0, chains)
+    f.dvc_mcts_step(max(budgets), dvc.DVC_MODE_VALUE)
+    stats = f.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    assert (stats[:, 6] == np.asarray(budgets)).all()
+    trees = range(n) if n <= 8 else (0, 1, 149, 298, 299)
+    for t in trees:
+        nodes, best = oracle.mcts(ocfg, oroots[t], 8, int(tree_ids[t]), int(budgets[t]), value_params=prm)
+        exp = f.dvc_tree_export(t).cpu().numpy()
+        assert (exp[: len(nodes)] == nodes).all(), t
+        assert (exp[len(nodes):] == -1).all(), t
+        assert stats[t][0] == best[0] and stats[t][1] == best[1] and stats[t][2] == best[2], t
+        assert stats[t][3] == best[3] and stats[t][5] == len(nodes), t
+    f.close()
+    ctx.close()
 
 
 def test_value_mode_chains_agree(dvc):
