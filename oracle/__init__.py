@@ -40,6 +40,9 @@ Pin status per function:
   value_features .... pinned (hand-made positions with features written out)
   value_forward ..... pinned (closed form with zero hidden weights)
   value_loss_grad ... pinned (central finite differences in double)
+  adamw_step ........ pinned (closed forms of the definition: the first step
+                      from zero moments, a constant gradient over many steps,
+                      weight decay on matrices only)
 """
 import ctypes
 import os
@@ -140,6 +143,9 @@ def lib():
         L.or_value_forward.restype = ctypes.c_int
         L.or_value_loss_grad.argtypes = [f32p, u8p, f32p, ctypes.c_int, f64p]
         L.or_value_loss_grad.restype = ctypes.c_double
+        L.or_adamw_step.argtypes = [f64p, f64p, f64p, f64p, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_adamw_step.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -301,3 +307,19 @@ def mcts(cfg: OracleConfig, root, seed: int, tree: int, budget: int, value_param
     if rc:
         raise ValueError(f"or_mcts rc={rc}")
     return nodes[: n.value].copy(), best
+
+
+ADAMW = dict(b1=0.9, b2=0.999, eps=1e-8, wd=1e-4)
+
+
+def adamw_step(w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=1e-4):
+    """One AdamW step in double on copies of (w, m, v) with gradient g; t is
+    the step number after the update.  Returns (w, m, v)."""
+    n = value_nparams()
+    arrs = [np.array(a, dtype=np.float64).reshape(n).copy() for a in (w, m, v)]
+    gg = np.ascontiguousarray(np.asarray(g, dtype=np.float64).reshape(n))
+    p = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs + [gg]]
+    rc = lib().or_adamw_step(p[0], p[1], p[2], p[3], int(t), lr, b1, b2, eps, wd)
+    if rc:
+        raise ValueError("or_adamw_step")
+    return tuple(arrs)

@@ -1349,3 +1349,30 @@ double or_value_loss_grad(const float* prm, const uint8_t* states, const float* 
     free(d);
     return loss / n;
 }
+
+/* One AdamW step (Loshchilov and Hutter, "Decoupled Weight Decay
+ * Regularization", ICLR 2019; Adam of Kingma and Ba, ICLR 2015), in double,
+ * over the value network's parameters in the layout above:
+ *   m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+ *   mhat = m / (1 - b1^t);  vhat = v / (1 - b2^t);
+ *   w <- w - lr (mhat / (sqrt(vhat) + eps) + wd w)
+ * with t the step number after this update (1 for the first) and the weight
+ * decay applied to the weight matrices only, not to the biases. */
+int or_adamw_step(double* w, double* m, double* v, const double* g, long long t, double lr, double b1, double b2,
+                  double eps, double wd) {
+    if (t < 1) return -1;
+    const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    const long long b1o = (long long)VH * VF, b2o = b1o + VH + (long long)VH * VH, b3o = b2o + VH + (long long)VH * VH,
+                    b4o = b3o + VH + 4LL * VH;
+    for (long long i = 0; i < VP; i++) {
+        const int is_bias = (i >= b1o && i < b1o + VH) || (i >= b2o && i < b2o + VH) || (i >= b3o && i < b3o + VH) ||
+                            i >= b4o;
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        const double mhat = m[i] / c1, vhat = v[i] / c2;
+        double upd = mhat / (sqrt(vhat) + eps);
+        if (!is_bias) upd += wd * w[i];
+        w[i] -= lr * upd;
+    }
+    return 0;
+}

@@ -110,3 +110,61 @@ def test_gradient_matches_finite_differences():
         lm, _ = oracle.value_loss_grad(q, states, labels)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(g[i])) + 1e-7, (i, fd, g[i])
+
+
+# ---- AdamW (Loshchilov and Hutter; Kingma and Ba) -------------------------
+
+VH, VF = 512, 640
+BIAS_RANGES = [(VH * VF, VH * VF + VH), (VH * VF + VH + VH * VH, VH * VF + 2 * VH + VH * VH),
+               (VH * VF + 2 * VH + 2 * VH * VH, VH * VF + 3 * VH + 2 * VH * VH),
+               (VH * VF + 3 * VH + 2 * VH * VH + 4 * VH, VH * VF + 3 * VH + 2 * VH * VH + 4 * VH + 4)]
+
+
+def _is_bias():
+    n = oracle.value_nparams()
+    b = np.zeros(n, dtype=bool)
+    for a, z in BIAS_RANGES:
+        b[a:z] = True
+    assert BIAS_RANGES[-1][1] == n
+    return b
+
+
+def test_adamw_first_step_is_sign_like():
+    # From zero moments the bias corrections make mhat = g and vhat = g^2
+    # exactly, so the step is g / (|g| + eps), plus wd * w on weight matrices.
+    n = oracle.value_nparams()
+    rng = np.random.default_rng(1)
+    w0 = rng.normal(size=n)
+    g = rng.normal(size=n) * 10.0 ** rng.integers(-6, 2, size=n)
+    g[::97] = 0.0
+    lr, wd, eps = 1e-3, 1e-4, 1e-8
+    w, m, v = oracle.adamw_step(w0, np.zeros(n), np.zeros(n), g, 1, lr)
+    dec = np.where(_is_bias(), 0.0, wd * w0)
+    want = w0 - lr * (g / (np.abs(g) + eps) + dec)
+    assert np.allclose(w, want, rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g, rtol=1e-15, atol=0) and np.allclose(v, 0.001 * g * g, rtol=1e-12, atol=0)
+    # a zero gradient moves a matrix entry by decay alone and leaves a bias entry
+    z = np.zeros(n)
+    w1, _, _ = oracle.adamw_step(w0, z, z, z, 1, lr)
+    bias = _is_bias()
+    assert (w1[bias] == w0[bias]).all()
+    assert np.allclose(w1[~bias], w0[~bias] * (1 - lr * wd), rtol=1e-15, atol=0)
+
+
+def test_adamw_constant_gradient_closed_form():
+    # A constant gradient keeps mhat = g and vhat = g^2 at every step (the
+    # bias corrections undo the zero start), so with a = 1 - lr wd:
+    #   w_k = a^k w_0 - lr s (1 - a^k) / (1 - a)   (matrices), w_0 - k lr s (biases),
+    # s = g / (|g| + eps).
+    n = oracle.value_nparams()
+    rng = np.random.default_rng(2)
+    w0 = rng.normal(size=n)
+    g = rng.normal(size=n)
+    lr, wd, eps, K = 1e-2, 1e-4, 1e-8, 25
+    w, m, v = w0.copy(), np.zeros(n), np.zeros(n)
+    for t in range(1, K + 1):
+        w, m, v = oracle.adamw_step(w, m, v, g, t, lr)
+    s = g / (np.abs(g) + eps)
+    a = 1 - lr * wd
+    want = np.where(_is_bias(), w0 - K * lr * s, a ** K * w0 - lr * s * (1 - a ** K) / (1 - a))
+    assert np.allclose(w, want, rtol=0, atol=1e-11)
