@@ -307,6 +307,13 @@ int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream);
  * the method: a draw, a joker position, a guess or a continue coin).  Copies
  * then zeroes the counter, on `stream`.  d_out: one uint64. */
 int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream);
+/* The forest's playout work since creation or the last call, two uint64:
+ * d_out[0] random words (as dvc_forest_counters), d_out[1] game steps -- one
+ * per guess of a playout (Sec. II-A: the guess with its resolution, any
+ * continue coin and the next seat's draw), plus one for the continue coin a
+ * playout from a may-stop leaf draws first.  Copies then zeroes both
+ * counters, on `stream`. */
+int dvc_forest_work(dvc_forest* f, uint64_t* d_out, void* stream);
 
 /* Nodes of tree t in creation order, 4 int32 each: action, parent (-1 for
  * the root), visits, wins.  d_out holds h_budgets[t] + 1 rows; rows past the
@@ -379,6 +386,14 @@ int dvc_value_load(dvc_ctx* ctx, const char* path);
  * act 0 none, 1 GELU. */
 int dvc_gemm_bf16(dvc_ctx* ctx, const void* d_A, const void* d_B, const float* d_bias, void* d_C, float* d_Cf, int M,
                   int N, int K, int act, void* stream);
+/* Test hook of the GEMM's failure path (not part of the method): the same
+ * kernel with its copy-issuing warp issuing nothing, so the tensor-core and
+ * epilogue warps' mbarrier waits run out after wait_ms (1..1000) with no copy
+ * or MMA in flight; the kernel frees its tensor memory, exits and latches
+ * DVC_E_TIMEOUT, which dvc_check reports.  d_Cf is not written.  Every
+ * mbarrier wait of the GEMM is bounded this way (2 s in normal calls). */
+int dvc_gemm_timeout_probe(dvc_ctx* ctx, const void* d_A, const void* d_B, float* d_Cf, int M, int N, int K,
+                           int wait_ms, void* stream);
 
 /*
  * Serving: a request loop that keeps many searches resident on the device.
@@ -388,11 +403,17 @@ int dvc_gemm_bf16(dvc_ctx* ctx, const void* d_A, const void* d_B, const float* d
  * runs `iterations` more iterations of every resident search together, and
  * returns the queries whose budget is complete.  Slots are sized for
  * max_budget iterations and their number is fixed at creation by the HBM
- * budget (value_share_pct of it for value-mode slots if the context has a
- * value network), so admission is by memory.  A query's search is keyed by
- * (seed, low 32 bits of its id) and runs exactly as it would alone: results do
- * not depend on what else is resident.  Host-side calls; poll synchronises
- * the server's own stream.  A vanilla context returns DVC_E_UNSUPPORTED.
+ * budget, so admission is by memory.  A query's search is keyed by (seed,
+ * low 32 bits of its id) and runs exactly as it would alone: results do not
+ * depend on what else is resident.  Host-side calls; poll synchronises the
+ * server's own streams.  A vanilla context returns DVC_E_UNSUPPORTED.
+ *
+ * A server may hold several game variants (player count and tile set), one
+ * context each: its slots are split into lanes, one per (context, leaf mode),
+ * each a forest of that variant with its own stream, so the searches of
+ * different variants and modes run side by side on the GPU.  A submitted
+ * root goes to the lane of its variant and mode.  The paper searches one
+ * game at a time; serving many games is not part of its method.
  */
 typedef struct dvc_server dvc_server;
 typedef struct dvc_result {
@@ -400,15 +421,32 @@ typedef struct dvc_result {
     int32_t best_action, best_visits, best_wins, root_visits, iterations, mode;
     double t_submit, t_done; /* host steady-clock seconds */
 } dvc_result;
+/* One context.  value_share_pct of the budget goes to value-mode slots if
+ * the context has a value network. */
 int dvc_server_create(dvc_ctx* ctx, size_t hbm_budget, int max_budget, int value_share_pct, uint64_t seed,
                       dvc_server** out);
+/* n_ctx (1..16) contexts of distinct game variants on one device.  Context i
+ * gets h_weights[i] / sum(h_weights) of hbm_budget (NULL: equal shares),
+ * value_share_pct of that for value-mode slots if it has a value network;
+ * its slot count is that share over its per-slot footprint (node arena for
+ * max_budget iterations, counting table, buffers).  Each context's value
+ * network serves its own variant's value-mode queries.  DVC_E_INVALID for
+ * two contexts of one variant or contexts on different devices; DVC_E_OOM if
+ * the budget holds no slot at all. */
+int dvc_server_create_multi(dvc_ctx* const* ctxs, int n_ctx, const int32_t* h_weights, size_t hbm_budget,
+                            int max_budget, int value_share_pct, uint64_t seed, dvc_server** out);
 void dvc_server_destroy(dvc_server* sv);
-/* Queue a query; h_root is a host record of the context's game variant. */
+/* Queue a query; h_root is a host record of one of the server's variants
+ * (DVC_E_INVALID otherwise; DVC_E_UNSUPPORTED if that variant has no slots
+ * of this mode). */
 int dvc_server_submit(dvc_server* sv, const dvc_state* h_root, int budget, int mode, uint64_t query_id);
 /* Admit, search `iterations` more, collect; returns the number of results written (<= max_results). */
 int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int max_results);
-/* h_out[5]: queued, resident, completed, rollout slots, value slots. */
+/* h_out[5]: queued, resident, completed, rollout slots, value slots (over all lanes). */
 int dvc_server_stats(dvc_server* sv, int64_t* h_out);
+/* Per lane, 6 int32: context index, players, tiles, mode, slots, resident.
+ * Writes min(lanes, max_lanes) rows; returns the number of lanes. */
+int dvc_server_lanes(dvc_server* sv, int max_lanes, int32_t* h_out);
 
 /* Test hook for the random-number generator: out[4k..4k+3] = Philox-4x32-10
  * of counter d_ctr[4k..], key d_key[2k..], by this library's generator

@@ -133,6 +133,8 @@ def lib():
         L.or_mcts_value.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_float), i32p, ctypes.POINTER(ctypes.c_int), i32p]
         L.or_mcts_value.restype = ctypes.c_int
+        L.or_mcts_work.argtypes = [cfgp, u8p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, i64p]
+        L.or_mcts_work.restype = ctypes.c_int
         f32p = ctypes.POINTER(ctypes.c_float)
         f64p = ctypes.POINTER(ctypes.c_double)
         L.or_value_nparams.argtypes = []
@@ -323,3 +325,16 @@ def adamw_step(w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=1e-4):
     if rc:
         raise ValueError("or_adamw_step")
     return tuple(arrs)
+
+
+def mcts_work(cfg: OracleConfig, root, seed: int, tree: int, budget: int):
+    """(random words, game steps) consumed by the playouts of or_mcts's search:
+    one game step per guess, plus one per continue coin a playout from a
+    may-stop leaf draws first."""
+    s = _state(root)
+    out = np.zeros(2, dtype=np.int64)
+    c = cfg.c()
+    rc = lib().or_mcts_work(ctypes.byref(c), _u8(s), seed, tree, budget, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc:
+        raise ValueError(f"or_mcts_work rc={rc}")
+    return int(out[0]), int(out[1])

@@ -437,16 +437,21 @@ static _Thread_local int legal_q[MAXLEGAL], legal_s[MAXLEGAL], legal_x[MAXLEGAL]
 
 /* One random playout from a state where the player to move is about to guess
  * (Sec. II-B): uniform guesses among the legal ones until one player is left. */
-static int playout(ost s, uint32_t cont_thr, int policy, stream* rng, uint8_t* trace, int* ntrace, int maxtrace) {
+/* *nsteps (if set) gains the playout's game steps: one per guess, plus one
+ * for the continue coin drawn first from a may-stop state. */
+static int playout(ost s, uint32_t cont_thr, int policy, stream* rng, uint8_t* trace, int* ntrace, int maxtrace,
+                   int64_t* nsteps) {
     if (s.winner >= 0) return s.winner;
     if (s.mstop) {
         /* after a correct guess a playout goes on iff the next word is below cont_thr */
+        if (nsteps) ++*nsteps;
         s.mstop = 0;
         if (!(cont_thr != 0u && next_word(rng) < cont_thr)) next_turn(&s, rng);
     }
     for (;;) {
         int n = legal_list_policy(&s, policy, legal_q, legal_s, legal_x);
         int k = pick(next_word(rng), n);
+        if (nsteps) ++*nsteps;
         int r = resolve(&s, legal_q[k], legal_s[k], legal_x[k], 0, cont_thr, rng);
         if (r == TURN_OVER) next_turn(&s, rng);
         if (trace && *ntrace < maxtrace) pack(&s, trace + 32 * (*ntrace)++);
@@ -826,8 +831,17 @@ int or_determinize(const or_config* cfg, const uint8_t* root, int observer, uint
 
 /* Per-leaf playouts (Sec. II-B; leaf parallelism): playout j of leaf i of
  * tree t runs on the stream keyed (seed, t) with counter (., j, i, ROLL). */
+static int rollout_counted(const or_config* cfg, const uint8_t* leaf, int P, uint64_t seed, uint32_t tree,
+                           uint32_t leaf_id, int32_t* wins, int64_t* words, int64_t* steps);
+
 int or_rollout(const or_config* cfg, const uint8_t* leaf, int P, uint64_t seed, uint32_t tree, uint32_t leaf_id,
                int32_t* wins, int64_t* words) {
+    return rollout_counted(cfg, leaf, P, seed, tree, leaf_id, wins, words, NULL);
+}
+
+/* or_rollout that also adds the playouts' game steps to *steps (if set). */
+static int rollout_counted(const or_config* cfg, const uint8_t* leaf, int P, uint64_t seed, uint32_t tree,
+                           uint32_t leaf_id, int32_t* wins, int64_t* words, int64_t* steps) {
     ost s;
     unpack(leaf, &s);
     for (int p = 0; p < 4; p++) wins[p] = 0;
@@ -840,7 +854,7 @@ int or_rollout(const or_config* cfg, const uint8_t* leaf, int P, uint64_t seed, 
     for (int j = 0; j < P; j++) {
         stream rng;
         stream_open(&rng, seed, tree, (uint32_t)j, leaf_id, TAG_ROLL);
-        int w = playout(s, cfg->cont_thr, cfg->policy, &rng, NULL, NULL, 0);
+        int w = playout(s, cfg->cont_thr, cfg->policy, &rng, NULL, NULL, 0, steps);
         wins[w]++;
         total += rng.words;
     }
@@ -855,7 +869,7 @@ int or_playout_trace(const or_config* cfg, const uint8_t* leaf, uint64_t seed, u
     stream rng;
     stream_open(&rng, seed, tree, j, leaf_id, TAG_ROLL);
     int n = 0;
-    playout(s, cfg->cont_thr, cfg->policy, &rng, trace, &n, maxtrace);
+    playout(s, cfg->cont_thr, cfg->policy, &rng, trace, &n, maxtrace, NULL);
     return n;
 }
 
@@ -993,7 +1007,7 @@ int or_value_forward(const float* prm, const uint8_t* packed, double* probs);
  * playouts), round(p_s * playouts) = floor(p_s * playouts + 0.5) for each
  * seat s, p the network's win probabilities of the leaf. */
 static int mcts_run(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
-                    const float* value_prm, int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
+                    const float* value_prm, int32_t* nodes_out, int* n_nodes_out, int32_t* best_out, int64_t* work) {
     ost root;
     unpack(root_packed, &root);
     int obs = root.cur;
@@ -1086,7 +1100,9 @@ static int mcts_run(const or_config* cfg, const uint8_t* root_packed, uint64_t s
         } else {
             uint8_t leaf[32];
             pack(&s, leaf);
-            or_rollout(cfg, leaf, P, seed, tree_id, (uint32_t)it, wins, NULL);
+            int64_t nw = 0;
+            rollout_counted(cfg, leaf, P, seed, tree_id, (uint32_t)it, wins, &nw, work ? work + 1 : NULL);
+            if (work) work[0] += nw;
         }
         for (int k = 0; k < np; k++) {
             t.visits[path[k]] += P;
@@ -1146,7 +1162,15 @@ static int mcts_run(const or_config* cfg, const uint8_t* root_packed, uint64_t s
 
 int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
             int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
-    return mcts_run(cfg, root_packed, seed, tree_id, budget, NULL, nodes_out, n_nodes_out, best_out);
+    return mcts_run(cfg, root_packed, seed, tree_id, budget, NULL, nodes_out, n_nodes_out, best_out, NULL);
+}
+
+/* The search's playout work: work[0] random words, work[1] game steps (one
+ * per guess, plus one per continue coin drawn first from a may-stop leaf). */
+int or_mcts_work(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
+                 int64_t* work) {
+    work[0] = work[1] = 0;
+    return mcts_run(cfg, root_packed, seed, tree_id, budget, NULL, NULL, NULL, NULL, work);
 }
 
 /* The same search in value mode: every fresh leaf that did not end inside the
@@ -1155,7 +1179,7 @@ int or_mcts(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uin
 int or_mcts_value(const or_config* cfg, const uint8_t* root_packed, uint64_t seed, uint32_t tree_id, int budget,
                   const float* prm, int32_t* nodes_out, int* n_nodes_out, int32_t* best_out) {
     if (!prm) return -1;
-    return mcts_run(cfg, root_packed, seed, tree_id, budget, prm, nodes_out, n_nodes_out, best_out);
+    return mcts_run(cfg, root_packed, seed, tree_id, budget, prm, nodes_out, n_nodes_out, best_out, NULL);
 }
 
 /* ------------------------------------------------------------- value net */

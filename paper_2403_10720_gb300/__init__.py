@@ -118,6 +118,7 @@ def lib():
             "dvc_forest_leaves": ([vp, pp, pp, pp], i),
             "dvc_root_stats": ([vp, vp, vp], i),
             "dvc_forest_counters": ([vp, vp, vp], i),
+            "dvc_forest_work": ([vp, vp, vp], i),
             "dvc_tree_export": ([vp, i, vp, vp], i),
             "dvc_philox": ([vp, i, vp, vp, vp, i, vp], i),
             "dvc_determinize_noalloc": ([vp, i, i, u64, vp, vp, vp, vp, vp], i),
@@ -130,11 +131,15 @@ def lib():
             "dvc_value_save": ([vp, ctypes.c_char_p], i),
             "dvc_value_load": ([vp, ctypes.c_char_p], i),
             "dvc_gemm_bf16": ([vp, vp, vp, vp, vp, vp, i, i, i, i, vp], i),
+            "dvc_gemm_timeout_probe": ([vp, vp, vp, vp, i, i, i, i, vp], i),
             "dvc_server_create": ([vp, ctypes.c_size_t, i, i, u64, ctypes.POINTER(vp)], i),
             "dvc_server_destroy": ([vp], None),
             "dvc_server_submit": ([vp, vp, i, i, u64], i),
             "dvc_server_poll": ([vp, i, ctypes.POINTER(dvc_result), i], i),
             "dvc_server_stats": ([vp, ctypes.POINTER(ctypes.c_int64)], i),
+            "dvc_server_create_multi": ([ctypes.POINTER(vp), i, vp, ctypes.c_size_t, i, i, u64,
+                                         ctypes.POINTER(vp)], i),
+            "dvc_server_lanes": ([vp, i, ctypes.POINTER(ctypes.c_int32)], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -346,6 +351,12 @@ class Forest:
         self.ctx._rc(lib().dvc_forest_counters(self.h, _ptr(out), _stream(stream)), "dvc_forest_counters")
         return out
 
+    def dvc_forest_work(self, out=None, stream=None):
+        """(random words, game steps) of the forest's playouts since the last call."""
+        out = torch.zeros(2, dtype=torch.int64, device=self.ctx.dev()) if out is None else out
+        self.ctx._rc(lib().dvc_forest_work(self.h, _ptr(out), _stream(stream)), "dvc_forest_work")
+        return out
+
     def dvc_root_stats(self, out=None, stream=None):
         out = torch.empty((self.n, 8), dtype=torch.int32, device=self.ctx.dev()) if out is None else out
         self.ctx._rc(lib().dvc_root_stats(self.h, _ptr(out), _stream(stream)), "dvc_root_stats")
@@ -359,13 +370,27 @@ class Forest:
 
 
 class Server:
-    """Owns a dvc_server: continuous batching of move queries (see include/dvc.h)."""
+    """Owns a dvc_server: continuous batching of move queries (see include/dvc.h).
+    `ctx` is one Context, or a list of Contexts of distinct game variants that
+    share the HBM budget (by `weights`, equal if None)."""
 
-    def __init__(self, ctx: Context, hbm_budget: int, max_budget: int, value_share_pct: int = 0, seed: int = 1):
-        self.ctx = ctx
+    def __init__(self, ctx, hbm_budget: int, max_budget: int, value_share_pct: int = 0, seed: int = 1,
+                 weights=None):
+        ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+        self.ctxs = ctxs
+        self.ctx = ctxs[0]
         h = ctypes.c_void_p()
-        ctx._rc(lib().dvc_server_create(ctx.h, hbm_budget, max_budget, value_share_pct, seed, ctypes.byref(h)),
-                "dvc_server_create")
+        if len(ctxs) == 1 and weights is None:
+            rc = lib().dvc_server_create(self.ctx.h, hbm_budget, max_budget, value_share_pct, seed, ctypes.byref(h))
+        else:
+            arr = (ctypes.c_void_p * len(ctxs))(*[c.h.value for c in ctxs])
+            w = None
+            if weights is not None:
+                self._w = (ctypes.c_int32 * len(ctxs))(*[int(x) for x in weights])
+                w = ctypes.cast(self._w, ctypes.c_void_p)
+            rc = lib().dvc_server_create_multi(arr, len(ctxs), w, hbm_budget, max_budget, value_share_pct, seed,
+                                               ctypes.byref(h))
+        self.ctx._rc(rc, "dvc_server_create")
         self.h = h
         self._buf = (dvc_result * 65536)()
 
@@ -399,4 +424,13 @@ class Server:
         a = (ctypes.c_int64 * 5)()
         self.ctx._rc(lib().dvc_server_stats(self.h, a), "dvc_server_stats")
         return dict(queued=a[0], resident=a[1], completed=a[2], rollout_slots=a[3], value_slots=a[4])
+
+    def dvc_server_lanes(self):
+        """Per lane: dict(context, players, tiles, mode, slots, resident)."""
+        a = (ctypes.c_int32 * (6 * 64))()
+        n = lib().dvc_server_lanes(self.h, 64, a)
+        if n < 0:
+            self.ctx._rc(n, "dvc_server_lanes")
+        keys = ("context", "players", "tiles", "mode", "slots", "resident")
+        return [dict(zip(keys, a[6 * i:6 * i + 6])) for i in range(min(n, 64))]
 

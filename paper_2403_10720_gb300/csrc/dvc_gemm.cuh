@@ -63,10 +63,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Bounded wait; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false once limit_ns of global time have passed (checked every
+// 64 polls) or after kWaitLimit polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(bar, phase)) return true;
+        if ((i & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 
@@ -139,6 +149,8 @@ struct GemmArgs {
     int M, N, K;             // K % 64 == 0, N % BN == 0
     int act;
     int32_t* flags;
+    uint64_t wait_ns;  // limit of every mbarrier wait (global time)
+    int starve;        // test hook: the producer issues no copy, so every consumer wait runs out
 };
 
 // Stage geometry for a BN-column tile: A 128 x 64 and B BN x 64 BF16 per
@@ -205,7 +217,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const int m0 = (t / ntn) * kGemmBM, n0 = (t % ntn) * BN;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % S, r = it / S;
-                    if ((it >= S && !mbar_wait(&s_empty[s], (uint32_t)(r - 1) & 1u)) || *fail) {
+                    if (a.starve || (it >= S && !mbar_wait(&s_empty[s], (uint32_t)(r - 1) & 1u, a.wait_ns)) ||
+                        *fail) {
                         *fail = 1;
                         stop = true;
                         break;
@@ -227,7 +240,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             bool stop = false;
             for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++j) {
                 const int b = j & 1, u = j >> 1;
-                if (u > 0 && !mbar_wait(&s_acce[b], (uint32_t)(u - 1) & 1u)) {
+                if (u > 0 && !mbar_wait(&s_acce[b], (uint32_t)(u - 1) & 1u, a.wait_ns)) {
                     *fail = 1;
                     break;
                 }
@@ -235,7 +248,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint32_t acc = tmem + (uint32_t)b * Cfg::kAccCols;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int s = it % S, r = it / S;
-                    if (!mbar_wait(&s_full[s], (uint32_t)r & 1u) || *fail) {
+                    if (!mbar_wait(&s_full[s], (uint32_t)r & 1u, a.wait_ns) || *fail) {
                         *fail = 1;
                         stop = true;
                         break;
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         int j = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int b = j & 1, u = j >> 1;
-            const bool got = mbar_wait(&s_accf[b], (uint32_t)u & 1u);
+            const bool got = mbar_wait(&s_accf[b], (uint32_t)u & 1u, a.wait_ns);
             if (!__all_sync(0xFFFFFFFFu, got) || *fail) {
                 if (lane == 0) *fail = 1;
                 break;
@@ -313,9 +326,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __syncthreads();
     // every MMA has completed before tensor memory is freed; on failure the
     // copies still in flight land first
-    const bool ok = __syncthreads_and(mbar_wait(&s_done, 0) && !*fail) != 0;
+    const bool ok = __syncthreads_and(mbar_wait(&s_done, 0, a.wait_ns) && !*fail) != 0;
     if (!ok && tid == 0) {
-        for (int it = s_consumed; it < s_issued; ++it) mbar_wait(&s_full[it % S], (uint32_t)(it / S) & 1u);
+        for (int it = s_consumed; it < s_issued; ++it) mbar_wait(&s_full[it % S], (uint32_t)(it / S) & 1u, a.wait_ns);
         if (a.flags) atomicCAS(a.flags, 0, -4);  // DVC_E_TIMEOUT
     }
     tc_fence_before();

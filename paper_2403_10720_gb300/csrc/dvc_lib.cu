@@ -520,8 +520,9 @@ __device__ void init_tree(ForestDev& F, int t, DetPlan* plans, unsigned long lon
         const dvc_state& rs = roots[t];
         const bool variant = rs.nplayers == nplayers && rs.ntiles == ntiles;  // the context's game
         const bool usable = pl.ok && pl.total != 0ull && variant;
-        if (!pl.ok) latch(F.flags, DVC_E_UNSUPPORTED);
-        else if (!pl.total || !variant) latch(F.flags, DVC_E_INVALID);
+        if (!variant) latch(F.flags, DVC_E_INVALID);  // a root of another game than the context's
+        else if (!pl.ok) latch(F.flags, DVC_E_UNSUPPORTED);
+        else if (!pl.total) latch(F.flags, DVC_E_INVALID);
         const uint32_t U = g.tmask & ~g.hand(g.cur) & ~g.rev;
         uint32_t slots = 0;
         for (uint32_t q = 0; q < g.np; ++q)
@@ -889,7 +890,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         alloc((void**)&f->plans, sizeof(DetPlan) * n) && alloc((void**)&f->work, sizeof(Descent) * n) &&
         alloc((void**)&f->paths, sizeof(int32_t) * kPathMax * n) && alloc((void**)&f->movers, kPathMax * (size_t)n) &&
         alloc((void**)&f->leaves, sizeof(dvc_state) * n) && alloc((void**)&f->leaf_tree, sizeof(uint32_t) * n) &&
-        alloc((void**)&f->leaf_iter, sizeof(uint32_t) * n) && alloc((void**)&f->d_words, sizeof(unsigned long long)) &&
+        alloc((void**)&f->leaf_iter, sizeof(uint32_t) * n) && alloc((void**)&f->d_words, 2 * sizeof(unsigned long long)) &&
         alloc((void**)&f->tables, sizeof(unsigned long long) * (size_t)f->table_cap * n) &&
         alloc((void**)&f->nodes, sizeof(Node) * (size_t)slots) && alloc((void**)&f->link, sizeof(int32_t) * (size_t)slots) &&
         alloc((void**)&f->created, sizeof(int32_t) * (size_t)slots) && alloc((void**)&f->order, sizeof(int32_t) * n) &&
@@ -909,7 +910,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
     // pageable source: the copy is staged before cudaMemcpyAsync returns
     cudaError_t e = cudaMemcpyAsync(f->meta, hm.data(), sizeof(TreeMeta) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->roots, d_roots, sizeof(dvc_state) * n, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->pipe.det_base, 0xC0, sizeof(int32_t) * n, st);  // none ahead
     f->pipe.flags = c->d_flags;
@@ -1364,6 +1365,17 @@ int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream) {
     return DVC_OK;
 }
 
+int dvc_forest_work(dvc_forest* f, uint64_t* d_out, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (!is_device_ptr(d_out, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_work: d_out must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_out, f->d_words, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_words, 0, 2 * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_work");
+    return DVC_OK;
+}
+
 int dvc_forest_leaves(dvc_forest* f, dvc_state** d_leaves, uint32_t** d_tree_ids, uint32_t** d_leaf_ids) {
     if (!f || !d_leaves || !d_tree_ids || !d_leaf_ids) return DVC_E_INVALID;
     *d_leaves = f->leaves;
@@ -1427,7 +1439,7 @@ double now_s() {
 struct ServerQuery {
     dvc_state root;
     int32_t budget;
-    int32_t mode;
+    int32_t lane;  // the (context, mode) lane that searches it
     uint64_t id;
     double t_submit;
 };
@@ -1437,45 +1449,115 @@ struct ServerSlot {
     ServerQuery q;
 };
 
-}  // namespace
-
-struct dvc_server {
-    dvc_ctx* ctx;
-    int max_budget;
-    dvc_forest* f[2] = {nullptr, nullptr};  // rollout, value
-    std::vector<ServerSlot> slots[2];
-    std::deque<ServerQuery> queue;
+// One game variant (a context) in one leaf mode: a forest whose trees are
+// the search slots, its own stream (so the lanes' searches overlap on the
+// device), admission staging buffers and a pinned copy of the root stats.
+struct ServerLane {
+    dvc_ctx* ctx = nullptr;
+    int mode = DVC_MODE_ROLLOUT;
+    int ctx_index = 0;
+    dvc_forest* f = nullptr;
+    std::vector<ServerSlot> slots;
     cudaStream_t st = nullptr;
-    // admission staging (device) and statistics (host, pinned)
     int32_t* d_slot = nullptr;
     dvc_state* d_root = nullptr;
     int32_t* d_budget = nullptr;
     uint32_t* d_tid = nullptr;
     int32_t* d_stats = nullptr;
     int32_t* h_stats = nullptr;
+    int resident = 0;
+    bool stepped = false;
+};
+
+// Device bytes of one search slot of context c sized for max_budget
+// iterations: node arena (48 B per slot: node, UCB terms, link, creation
+// stamp), counting table, plan, meta and pipeline buffers (determinizations
+// sampled ahead included), plus the lane's staging per slot.
+size_t server_slot_bytes(const dvc_ctx* c, int max_budget) {
+    const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 48;
+    const size_t table = (size_t)(c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells) * 8;
+    return arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) +
+           (sizeof(dvc_state) + sizeof(uint4)) * kDetAhead + 256;
+}
+
+}  // namespace
+
+struct dvc_server {
+    dvc_ctx* ctx;  // the first context: error messages
+    int max_budget;
+    std::vector<ServerLane> lanes;
+    std::deque<ServerQuery> queue;
     long long completed = 0;
 };
 
 namespace {
 
-int server_admit(dvc_server* sv, int m) {
-    dvc_forest* f = sv->f[m];
-    if (!f) return DVC_OK;
+void lane_free(ServerLane& L) {
+    if (L.st) cudaStreamSynchronize(L.st);
+    dvc_forest_destroy(L.f);
+    L.f = nullptr;
+    void* ptrs[] = {L.d_slot, L.d_budget, L.d_tid, L.d_root, L.d_stats};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (L.h_stats) cudaFreeHost(L.h_stats);
+    if (L.st) cudaStreamDestroy(L.st);
+    L = ServerLane();
+}
+
+// A lane of n slots: staging buffers, idle roots, the forest (budget 0 until
+// a query is admitted), and the engine shape for resident searches.
+int lane_create(ServerLane& L, dvc_ctx* c, int ctx_index, int mode, int n, int max_budget, uint64_t seed) {
+    L.ctx = c;
+    L.mode = mode;
+    L.ctx_index = ctx_index;
+    if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&L.d_slot, 4 * (size_t)n) != cudaSuccess || cudaMalloc(&L.d_budget, 4 * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&L.d_tid, 4 * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&L.d_root, sizeof(dvc_state) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&L.d_stats, 32 * (size_t)n) != cudaSuccess ||
+        cudaMallocHost(&L.h_stats, 32 * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DVC_E_OOM, "dvc_server_create: staging buffers");
+    }
+    // any valid roots: the slots start idle (budget 0) and take real roots on admission
+    int rc = dvc_init_states(c, seed, n, L.d_root, L.st);
+    if (rc == DVC_OK) {
+        std::vector<int32_t> budgets(n, max_budget);
+        rc = dvc_forest_create(c, n, L.d_root, budgets.data(), nullptr, seed, &L.f, L.st);
+    }
+    if (rc == DVC_OK) {
+        forest_set_budget_kernel<<<(n + 127) / 128, 128, 0, L.st>>>(L.f->meta, n, 0);
+        rc = check_launch(c, "forest_set_budget_kernel");
+    }
+    // resident searches start and end at any time: the fused engine, one
+    // launch per poll over the CTAs that hold resident slots only; four
+    // slots per CTA, so a search waits on three others per iteration
+    if (rc == DVC_OK && mode == DVC_MODE_ROLLOUT) rc = dvc_forest_tune(L.f, 1, 4, 4, 0);
+    if (rc == DVC_OK) L.slots.assign(n, ServerSlot());
+    return rc;
+}
+
+// Move queued queries of this lane into its free slots (FIFO within the
+// lane; a full lane does not hold up the others) and plan their views on
+// the device.  Enqueued on the lane's stream; the staging buffers are free
+// again once the poll has synchronised that stream.
+int lane_admit(dvc_server* sv, int li) {
+    ServerLane& L = sv->lanes[li];
     std::vector<int32_t> slot, budget;
     std::vector<dvc_state> root;
     std::vector<uint32_t> tid;
     std::vector<int> freeidx;
-    for (int s = 0; s < f->n; ++s)
-        if (!sv->slots[m][s].busy) freeidx.push_back(s);
+    for (int s = 0; s < L.f->n; ++s)
+        if (!L.slots[s].busy) freeidx.push_back(s);
     size_t next = 0;
     for (auto it = sv->queue.begin(); it != sv->queue.end() && next < freeidx.size();) {
-        if (it->mode != m) {
+        if (it->lane != li) {
             ++it;
             continue;
         }
         const int s = freeidx[next++];
-        sv->slots[m][s].busy = true;
-        sv->slots[m][s].q = *it;
+        L.slots[s].busy = true;
+        L.slots[s].q = *it;
         slot.push_back(s);
         budget.push_back(it->budget);
         root.push_back(it->root);
@@ -1483,83 +1565,80 @@ int server_admit(dvc_server* sv, int m) {
         it = sv->queue.erase(it);
     }
     const int k = (int)slot.size();
+    L.resident += k;
     if (k == 0) return DVC_OK;
-    dvc_ctx* c = sv->ctx;
-    cudaError_t e = cudaMemcpyAsync(sv->d_slot, slot.data(), 4 * k, cudaMemcpyHostToDevice, sv->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_budget, budget.data(), 4 * k, cudaMemcpyHostToDevice, sv->st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sv->d_tid, tid.data(), 4 * k, cudaMemcpyHostToDevice, sv->st);
+    dvc_ctx* c = L.ctx;
+    // pageable sources: each copy is staged before cudaMemcpyAsync returns
+    cudaError_t e = cudaMemcpyAsync(L.d_slot, slot.data(), 4 * k, cudaMemcpyHostToDevice, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_budget, budget.data(), 4 * k, cudaMemcpyHostToDevice, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_tid, tid.data(), 4 * k, cudaMemcpyHostToDevice, L.st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(sv->d_root, root.data(), sizeof(dvc_state) * k, cudaMemcpyHostToDevice, sv->st);
+        e = cudaMemcpyAsync(L.d_root, root.data(), sizeof(dvc_state) * k, cudaMemcpyHostToDevice, L.st);
     if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server admit");
-    forest_admit_kernel<<<(k * 32 + 127) / 128, 128, 0, sv->st>>>(dev_of(f), k, sv->d_slot, sv->d_root, sv->d_budget,
-                                                                  sv->d_tid, f->plans, f->tables, f->table_cap,
-                                                                  c->cfg.nplayers, c->cfg.ntiles, f->pipe.np);
-    if (int rc = check_launch(c, "forest_admit_kernel")) return rc;
-    // the staging buffers are reused by the next admission: wait for the copies
-    e = cudaStreamSynchronize(sv->st);
-    return e == cudaSuccess ? DVC_OK : cuda_fail(c, e, "dvc_server admit sync");
+    forest_admit_kernel<<<(k * 32 + 127) / 128, 128, 0, L.st>>>(dev_of(L.f), k, L.d_slot, L.d_root, L.d_budget,
+                                                                L.d_tid, L.f->plans, L.f->tables, L.f->table_cap,
+                                                                c->cfg.nplayers, c->cfg.ntiles, L.f->pipe.np);
+    return check_launch(c, "forest_admit_kernel");
 }
 
 }  // namespace
 
 extern "C" {
 
-int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_share_pct, uint64_t seed,
-                      dvc_server** out) {
-    if (!c) return DVC_E_INVALID;
+int dvc_server_create_multi(dvc_ctx* const* ctxs, int n_ctx, const int32_t* h_weights, size_t hbm_budget,
+                            int max_budget, int value_share_pct, uint64_t seed, dvc_server** out) {
+    if (!ctxs || n_ctx < 1 || n_ctx > 16 || !ctxs[0]) return DVC_E_INVALID;
+    dvc_ctx* c0 = ctxs[0];
     if (!out || max_budget < 1 || max_budget > (1 << 24) || value_share_pct < 0 || value_share_pct > 100)
-        return fail(c, DVC_E_INVALID, "dvc_server_create: max_budget 1..2^24, value_share_pct 0..100");
+        return fail(c0, DVC_E_INVALID, "dvc_server_create: max_budget 1..2^24, value_share_pct 0..100");
     *out = nullptr;
-    if (c->cfg.vanilla) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_create: vanilla trees are searched by forests only");
-    if (int rc = set_device(c)) return rc;
-    // device bytes per search slot: node arena (48 B per slot: node, UCB terms,
-    // link, creation stamp), counting table, plan, meta and pipeline buffers
-    // (determinizations sampled ahead included)
-    const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 48;
-    const size_t table = (size_t)(c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells) * 8;
-    const size_t per_slot = arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) +
-                            (sizeof(dvc_state) + sizeof(uint4)) * kDetAhead + 256;
-    const long long total = (long long)(hbm_budget / per_slot);
-    const long long nv = c->vnet ? total * value_share_pct / 100 : 0;
-    const long long nr = total - nv;
-    if (nr < 1 && nv < 1) return fail(c, DVC_E_OOM, "dvc_server_create: HBM budget below one search slot");
-    if (nr > (1 << 20) || nv > (1 << 20)) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_create: over 2^20 slots");
+    long long wsum = 0;
+    for (int i = 0; i < n_ctx; ++i) {
+        dvc_ctx* c = ctxs[i];
+        if (!c) return fail(c0, DVC_E_INVALID, "dvc_server_create: null context");
+        if (c->device != c0->device) return fail(c0, DVC_E_INVALID, "dvc_server_create: contexts on different devices");
+        if (c->cfg.vanilla)
+            return fail(c0, DVC_E_UNSUPPORTED, "dvc_server_create: vanilla trees are searched by forests only");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j]->cfg.nplayers == c->cfg.nplayers && ctxs[j]->cfg.ntiles == c->cfg.ntiles)
+                return fail(c0, DVC_E_INVALID, "dvc_server_create: two contexts of one game variant");
+        const long long w = h_weights ? h_weights[i] : 1;
+        if (w < 0) return fail(c0, DVC_E_INVALID, "dvc_server_create: negative weight");
+        wsum += w;
+    }
+    if (wsum <= 0) return fail(c0, DVC_E_INVALID, "dvc_server_create: weights sum to zero");
+    if (int rc = set_device(c0)) return rc;
+    // slots per (context, mode): the context's share of the HBM budget over
+    // its per-slot footprint, value_share_pct of it for value mode
+    std::vector<long long> counts(2 * n_ctx, 0);
+    long long total_slots = 0;
+    for (int i = 0; i < n_ctx; ++i) {
+        const long long w = h_weights ? h_weights[i] : 1;
+        const double share = (double)hbm_budget * (double)w / (double)wsum;
+        const long long n = (long long)(share / (double)server_slot_bytes(ctxs[i], max_budget));
+        const long long nv = ctxs[i]->vnet ? n * value_share_pct / 100 : 0;
+        counts[2 * i] = n - nv;
+        counts[2 * i + 1] = nv;
+        if (n - nv > (1 << 20) || nv > (1 << 20))
+            return fail(c0, DVC_E_UNSUPPORTED, "dvc_server_create: over 2^20 slots per lane");
+        total_slots += n;
+    }
+    if (total_slots < 1) return fail(c0, DVC_E_OOM, "dvc_server_create: HBM budget below one search slot");
     dvc_server* sv = new (std::nothrow) dvc_server();
-    if (!sv) return fail(c, DVC_E_OOM, "dvc_server_create: host allocation");
-    sv->ctx = c;
+    if (!sv) return fail(c0, DVC_E_OOM, "dvc_server_create: host allocation");
+    sv->ctx = c0;
     sv->max_budget = max_budget;
     int rc = DVC_OK;
-    const int nmax = (int)std::max(nr, nv);
-    if (cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc(&sv->d_slot, 4 * (size_t)nmax) != cudaSuccess || cudaMalloc(&sv->d_budget, 4 * (size_t)nmax) != cudaSuccess ||
-        cudaMalloc(&sv->d_tid, 4 * (size_t)nmax) != cudaSuccess ||
-        cudaMalloc(&sv->d_root, sizeof(dvc_state) * (size_t)nmax) != cudaSuccess ||
-        cudaMalloc(&sv->d_stats, 32 * (size_t)nmax) != cudaSuccess ||
-        cudaMallocHost(&sv->h_stats, 32 * (size_t)nmax) != cudaSuccess) {
-        cudaGetLastError();
-        rc = fail(c, DVC_E_OOM, "dvc_server_create: staging buffers");
-    }
-    const long long counts[2] = {nr, nv};
-    for (int m = 0; m < 2 && rc == DVC_OK; ++m) {
-        const int n = (int)counts[m];
-        if (n < 1) continue;
-        // any valid roots: the slots start idle (budget 0) and take real roots on admission
-        rc = dvc_init_states(c, seed, n, sv->d_root, sv->st);
-        if (rc == DVC_OK) {
-            std::vector<int32_t> budgets(n, max_budget);
-            rc = dvc_forest_create(c, n, sv->d_root, budgets.data(), nullptr, seed, &sv->f[m], sv->st);
+    for (int i = 0; i < n_ctx && rc == DVC_OK; ++i)
+        for (int m = 0; m < 2 && rc == DVC_OK; ++m) {
+            const int n = (int)counts[2 * i + m];
+            if (n < 1) continue;
+            sv->lanes.emplace_back();
+            rc = lane_create(sv->lanes.back(), ctxs[i], i, m, n, max_budget, seed);
         }
-        if (rc == DVC_OK) {
-            forest_set_budget_kernel<<<(n + 127) / 128, 128, 0, sv->st>>>(sv->f[m]->meta, n, 0);
-            rc = check_launch(c, "forest_set_budget_kernel");
-        }
-        // resident searches start and end at any time: the fused engine, one
-        // launch per poll over the CTAs that hold resident slots only; four
-        // slots per CTA, so a search waits on three others per iteration
-        if (rc == DVC_OK && m == 0) rc = dvc_forest_tune(sv->f[m], 1, 4, 4, 0);
-        if (rc == DVC_OK) sv->slots[m].assign(n, ServerSlot());
-    }
-    if (rc == DVC_OK && cudaStreamSynchronize(sv->st) != cudaSuccess) rc = fail(c, DVC_E_CUDA, "dvc_server_create sync");
+    for (ServerLane& L : sv->lanes)
+        if (rc == DVC_OK && L.st && cudaStreamSynchronize(L.st) != cudaSuccess)
+            rc = fail(c0, DVC_E_CUDA, "dvc_server_create sync");
     if (rc != DVC_OK) {
         dvc_server_destroy(sv);
         return rc;
@@ -1568,16 +1647,16 @@ int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_s
     return DVC_OK;
 }
 
+int dvc_server_create(dvc_ctx* c, size_t hbm_budget, int max_budget, int value_share_pct, uint64_t seed,
+                      dvc_server** out) {
+    if (!c) return DVC_E_INVALID;
+    return dvc_server_create_multi(&c, 1, nullptr, hbm_budget, max_budget, value_share_pct, seed, out);
+}
+
 void dvc_server_destroy(dvc_server* sv) {
     if (!sv) return;
     cudaSetDevice(sv->ctx->device);
-    if (sv->st) cudaStreamSynchronize(sv->st);
-    for (int m = 0; m < 2; ++m) dvc_forest_destroy(sv->f[m]);
-    void* ptrs[] = {sv->d_slot, sv->d_budget, sv->d_tid, sv->d_root, sv->d_stats};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    if (sv->h_stats) cudaFreeHost(sv->h_stats);
-    if (sv->st) cudaStreamDestroy(sv->st);
+    for (ServerLane& L : sv->lanes) lane_free(L);
     delete sv;
 }
 
@@ -1586,13 +1665,20 @@ int dvc_server_submit(dvc_server* sv, const dvc_state* h_root, int budget, int m
     dvc_ctx* c = sv->ctx;
     if (!h_root || budget < 1 || budget > sv->max_budget || (mode != DVC_MODE_ROLLOUT && mode != DVC_MODE_VALUE))
         return fail(c, DVC_E_INVALID, "dvc_server_submit: root, budget 1..max_budget, mode");
-    if (!sv->f[mode]) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_submit: no slots for this mode");
-    if (h_root->nplayers != c->cfg.nplayers || h_root->ntiles != c->cfg.ntiles)
-        return fail(c, DVC_E_INVALID, "dvc_server_submit: root of another game variant");
+    int lane = -1;
+    bool variant = false;
+    for (int i = 0; i < (int)sv->lanes.size(); ++i) {
+        const ServerLane& L = sv->lanes[i];
+        if (L.ctx->cfg.nplayers != h_root->nplayers || L.ctx->cfg.ntiles != h_root->ntiles) continue;
+        variant = true;
+        if (L.mode == mode) lane = i;
+    }
+    if (!variant) return fail(c, DVC_E_INVALID, "dvc_server_submit: no context of this root's game variant");
+    if (lane < 0) return fail(c, DVC_E_UNSUPPORTED, "dvc_server_submit: no slots for this mode and variant");
     ServerQuery q;
     q.root = *h_root;
     q.budget = budget;
-    q.mode = mode;
+    q.lane = lane;
     q.id = query_id;
     q.t_submit = now_s();
     sv->queue.push_back(q);
@@ -1605,26 +1691,36 @@ int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int m
     if (iterations < 0 || max_results < 0 || (max_results > 0 && !h_results))
         return fail(c, DVC_E_INVALID, "dvc_server_poll: iterations >= 0, results buffer");
     if (int rc = set_device(c)) return rc;
-    int written = 0;
-    for (int m = 0; m < 2; ++m) {
-        dvc_forest* f = sv->f[m];
-        if (!f) continue;
-        if (int rc = server_admit(sv, m)) return rc;
+    // 1. admission, then `iterations` more of every lane's resident searches
+    //    and its root statistics, each lane on its own stream
+    for (int li = 0; li < (int)sv->lanes.size(); ++li) {
+        ServerLane& L = sv->lanes[li];
+        L.stepped = false;
+        if (int rc = lane_admit(sv, li)) return rc;
+        if (L.resident == 0) continue;
         int top = -1;
-        for (int s = 0; s < f->n; ++s)
-            if (sv->slots[m][s].busy) top = s;
-        if (top < 0) continue;
-        f->active_prefix = top + 1;
+        for (int s = 0; s < L.f->n; ++s)
+            if (L.slots[s].busy) top = s;
+        L.f->active_prefix = top + 1;
         if (iterations > 0)
-            if (int rc = dvc_mcts_step(f, iterations, m, sv->st)) return rc;
-        if (int rc = dvc_root_stats(f, sv->d_stats, sv->st)) return rc;
-        cudaError_t e = cudaMemcpyAsync(sv->h_stats, sv->d_stats, 32 * (size_t)f->n, cudaMemcpyDeviceToHost, sv->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(sv->st);
+            if (int rc = dvc_mcts_step(L.f, iterations, L.mode, L.st)) return rc;
+        if (int rc = dvc_root_stats(L.f, L.d_stats, L.st)) return rc;
+        const cudaError_t e = cudaMemcpyAsync(L.h_stats, L.d_stats, 32 * (size_t)L.f->n, cudaMemcpyDeviceToHost, L.st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll copy");
+        L.stepped = true;
+    }
+    // 2. wait for every lane, then collect the finished queries
+    for (ServerLane& L : sv->lanes) {
+        const cudaError_t e = cudaStreamSynchronize(L.st);
         if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll");
-        const double t = now_s();
-        for (int s = 0; s < f->n && written < max_results; ++s) {
-            ServerSlot& sl = sv->slots[m][s];
-            const int32_t* st = sv->h_stats + 8 * s;
+    }
+    const double t = now_s();
+    int written = 0;
+    for (ServerLane& L : sv->lanes) {
+        if (!L.stepped) continue;
+        for (int s = 0; s < L.f->n && written < max_results; ++s) {
+            ServerSlot& sl = L.slots[s];
+            const int32_t* st = L.h_stats + 8 * s;
             if (!sl.busy || st[6] < sl.q.budget) continue;
             dvc_result& r = h_results[written++];
             r.query_id = sl.q.id;
@@ -1633,10 +1729,11 @@ int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int m
             r.best_wins = st[2];
             r.root_visits = st[3];
             r.iterations = st[6];
-            r.mode = m;
+            r.mode = L.mode;
             r.t_submit = sl.q.t_submit;
             r.t_done = t;
             sl.busy = false;
+            L.resident--;
             sv->completed++;
         }
     }
@@ -1645,18 +1742,33 @@ int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int m
 
 int dvc_server_stats(dvc_server* sv, int64_t* h_out) {
     if (!sv || !h_out) return DVC_E_INVALID;
-    long long active = 0, slots = 0;
-    for (int m = 0; m < 2; ++m) {
-        slots += (long long)sv->slots[m].size();
-        for (const ServerSlot& s : sv->slots[m]) active += s.busy;
+    long long active = 0, rollout = 0, value = 0;
+    for (const ServerLane& L : sv->lanes) {
+        (L.mode == DVC_MODE_VALUE ? value : rollout) += (long long)L.slots.size();
+        active += L.resident;
     }
     h_out[0] = (int64_t)sv->queue.size();
     h_out[1] = active;
     h_out[2] = sv->completed;
-    h_out[3] = (int64_t)sv->slots[0].size();
-    h_out[4] = (int64_t)sv->slots[1].size();
-    (void)slots;
+    h_out[3] = rollout;
+    h_out[4] = value;
     return DVC_OK;
+}
+
+int dvc_server_lanes(dvc_server* sv, int max_lanes, int32_t* h_out) {
+    if (!sv || max_lanes < 0 || (max_lanes > 0 && !h_out)) return DVC_E_INVALID;
+    const int n = (int)sv->lanes.size();
+    for (int i = 0; i < n && i < max_lanes; ++i) {
+        const ServerLane& L = sv->lanes[i];
+        int32_t* o = h_out + 6 * i;
+        o[0] = L.ctx_index;
+        o[1] = L.ctx->cfg.nplayers;
+        o[2] = L.ctx->cfg.ntiles;
+        o[3] = L.mode;
+        o[4] = (int32_t)L.slots.size();
+        o[5] = L.resident;
+    }
+    return n;
 }
 
 }  // extern "C"

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     // playout p belongs to leaf p / Pp: multiply-high by ceil(2^32 / Pp) gives
     // the quotient or one more (p < 2^32), fixed by one comparison
     const uint32_t mP = Pp > 1u ? 0xFFFFFFFFu / Pp + 1u : 0u;
-    unsigned long long words = 0ull;
+    unsigned long long words = 0ull, nsteps = 0ull;
     uint32_t k = 0, steps = 0;
     RingQueue r;
     r.ring = s_ring + tid;
@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
             g = load_state(ls);
             playout_begin(g, r, sp.cont_thr);
         }
-        steps = 0;
+        // a may-stop leaf's first continue coin is a game step of its own
+        // (the fast path counts it as an iteration of its loop)
+        steps = (!FAST2 && (ls.flags & 2u)) ? 1u : 0u;
     };
     // the lanes in `want` take consecutive playout indices (all lanes call)
     auto take = [&](bool want) -> uint32_t {
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
                 const uint32_t w = res == kGameOver ? winner : kNone;
                 if (w < 4u) atomicAdd(&s_wins[4 * k + w], 1);
                 words += r.used();
+                nsteps += steps;
                 ended = true;
             }
         }
@@ -290,9 +293,11 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         w[2] = s_wins[4 * e + 2];
         w[3] = s_wins[4 * e + 3];
     }
-    if (words_out) {
+    if (words_out) {  // words_out[0]: random words, words_out[1]: game steps (guesses)
         const unsigned long long sum = warp_sum_u64(words);
+        const unsigned long long st = warp_sum_u64(nsteps);
         if (lane == 0 && sum) atomicAdd(words_out, sum);
+        if (lane == 0 && st) atomicAdd(words_out + 1, st);
     }
 }
 

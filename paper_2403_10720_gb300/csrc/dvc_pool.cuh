@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     if constexpr (FAST2) fill_select12(s_lut12, tid, blockDim.x);
     __syncthreads();
 
-    unsigned long long words = 0ull;
+    unsigned long long words = 0ull, nsteps = 0ull;
     for (int iter = 0;; ++iter) {
         int32_t* cnt = s_cnt + 4 * (iter & 1);
         if (iter % kDetAhead == 0) {
@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(MAXT, 1)
                     g = load_state(ls);
                     playout_begin(g, r, sp.cont_thr);
                 }
-                steps = 0;
+                // a may-stop leaf's first continue coin is a game step of its
+                // own (the fast path counts it as an iteration of its loop)
+                steps = (!FAST2 && (ls.flags & 2u)) ? 1 : 0;
             };
             int p = atomicAdd(&cnt[1], 1);
             bool busy = p < total;
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                         const uint32_t w = res == kGameOver ? winner : kNone;
                         if (w < 4u) atomicAdd(&s_wins[4 * slot + (int)w], 1);
                         words += r.used();
+                        nsteps += steps;
                         p = atomicAdd(&cnt[1], 1);
                         busy = p < total;
                         if (busy) start(p);
@@ -287,9 +290,11 @@ __global__ void __launch_bounds__(MAXT, 1)
             dst.failed = s_tm[s].failed;
         }
     }
-    if (F.words) {
+    if (F.words) {  // F.words[0]: random words, F.words[1]: game steps (guesses)
         const unsigned long long sum = warp_sum_u64(words);
+        const unsigned long long st = warp_sum_u64(nsteps);
         if (lane == 0 && sum) atomicAdd(F.words, sum);
+        if (lane == 0 && st) atomicAdd(F.words + 1, st);
     }
 }
 

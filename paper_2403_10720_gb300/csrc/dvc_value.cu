@@ -402,9 +402,11 @@ cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+constexpr uint64_t kGemmWaitNs = 2000000000ull;  // 2 s: far beyond any wait of a working GEMM
+
 cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, __nv_bfloat16* C, float* Cf, int M,
                  int N, int K, int act, int32_t* flags, cudaStream_t st) {
-    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags};
+    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0};
     if (N % 256 == 0) return launch_gemm<256>(a, st);
     if (N % 128 == 0) return launch_gemm<128>(a, st);
     if (N % 64 == 0) return launch_gemm<64>(a, st);
@@ -704,6 +706,25 @@ int dvc_value_load(dvc_ctx* c, const char* path) {
     v->step = step;
     if (int rc = refresh(c, nullptr)) return rc;
     return cudaDeviceSynchronize() == cudaSuccess ? DVC_OK : fail(c, DVC_E_CUDA, "dvc_value_load: sync");
+}
+
+int dvc_gemm_timeout_probe(dvc_ctx* c, const void* d_A, const void* d_B, float* d_Cf, int M, int N, int K,
+                           int wait_ms, void* stream) {
+    if (!c) return DVC_E_INVALID;
+    if (M < 1 || N < 16 || N % 16 || K < 64 || K % 64 || wait_ms < 1 || wait_ms > 1000)
+        return fail(c, DVC_E_INVALID, "dvc_gemm_timeout_probe: M >= 1, N % 16 == 0, K % 64 == 0, wait 1..1000 ms");
+    if (!is_device_ptr(d_A, c->device) || !is_device_ptr(d_B, c->device) || !is_device_ptr(d_Cf, c->device))
+        return fail(c, DVC_E_INVALID, "dvc_gemm_timeout_probe: device pointers");
+    if (int rc = set_device(c)) return rc;
+    GemmArgs a{(const __nv_bfloat16*)d_A, (const __nv_bfloat16*)d_B, nullptr, nullptr, d_Cf, M, N, K, kActNone,
+               c->d_flags, (uint64_t)wait_ms * 1000000ull, 1};
+    cudaError_t e;
+    if (N % 256 == 0) e = launch_gemm<256>(a, (cudaStream_t)stream);
+    else if (N % 128 == 0) e = launch_gemm<128>(a, (cudaStream_t)stream);
+    else if (N % 64 == 0) e = launch_gemm<64>(a, (cudaStream_t)stream);
+    else if (N % 32 == 0) e = launch_gemm<32>(a, (cudaStream_t)stream);
+    else e = launch_gemm<16>(a, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVC_OK : cuda_fail(c, e, "dvc_gemm_timeout_probe");
 }
 
 int dvc_gemm_bf16(dvc_ctx* c, const void* d_A, const void* d_B, const float* d_bias, void* d_C, float* d_Cf, int M,

@@ -38,3 +38,111 @@ def poisson_run(server, roots, budgets, modes, rate, iterations_per_poll=128, se
         "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "rate": rate,
     }
+
+
+def _pct(a, q):
+    return float(np.percentile(np.asarray(a), q) * 1e3) if len(a) else None
+
+
+def game_serving_run(server, ctxs, n_games, rate, duration_s, budget_lo=1000, budget_hi=100000, value_frac=0.5,
+                     seed=0, iterations_per_poll=256, move_seed=77, max_seconds=900.0, device="cuda"):
+    """Serve move queries from n_games concurrent games of the variants of
+    `ctxs` (one context per variant, game g of variant g mod len(ctxs)).
+
+    Queries arrive at seeded exponential gaps (rate per second, real time)
+    for duration_s seconds; each arrival is the next move of a game picked
+    uniformly among those with no query outstanding, its root that game's
+    current position, its budget log-uniform in [budget_lo, budget_hi], its
+    mode value with probability value_frac.  When an answer returns, the
+    chosen guess is played on the game (dvc_play_move of its variant; the next
+    seat draws) and a finished game is dealt afresh.  After the arrival window
+    the outstanding queries are drained.  Returns decisions per second over
+    the whole run, latency percentiles overall, per mode and per variant, and
+    the counts."""
+    import torch
+    nv = len(ctxs)
+    rng = np.random.default_rng(seed)
+    variant = np.arange(n_games) % nv
+    states = np.zeros((n_games, 32), dtype=np.uint8)
+    fresh = [0] * nv
+    for v, c in enumerate(ctxs):
+        idx = np.nonzero(variant == v)[0]
+        states[idx] = c.dvc_init_states(1000 + v, len(idx)).cpu().numpy()
+    names = [f"{c.cfg.nplayers}p{c.cfg.ntiles}" for c in ctxs]
+    waiting = np.zeros(n_games, dtype=bool)
+    idle = list(range(n_games))
+    info = {}
+    lat = []
+    t0 = time.perf_counter()
+    next_arrival = rng.exponential(1.0 / rate)
+    qid = 0
+    polls = 0
+    moves = 0
+    while True:
+        now = time.perf_counter() - t0
+        if now > max_seconds:
+            raise TimeoutError(f"{len(lat)} queries done after {max_seconds} s")
+        while next_arrival <= min(now, duration_s) and idle:
+            k = int(rng.integers(0, len(idle)))
+            g = idle[k]
+            idle[k] = idle[-1]
+            idle.pop()
+            budget = int(np.exp(rng.uniform(np.log(budget_lo), np.log(budget_hi))))
+            mode = 1 if rng.random() < value_frac else 0
+            server.dvc_server_submit(states[g], budget, mode, qid)
+            info[qid] = (g, mode, budget)
+            waiting[g] = True
+            qid += 1
+            next_arrival += rng.exponential(1.0 / rate)
+        if now >= duration_s and not waiting.any():
+            break
+        done = server.dvc_server_poll(iterations_per_poll)
+        polls += 1
+        by_variant = {}
+        for r in done:
+            g, mode, budget = info.pop(r["query_id"])
+            lat.append((r["t_done"] - r["t_submit"], mode, int(variant[g])))
+            by_variant.setdefault(int(variant[g]), []).append((g, int(r["best_action"])))
+        for v, lst in by_variant.items():
+            gs = np.array([g for g, _ in lst], dtype=np.int64)
+            acts = torch.tensor([a for _, a in lst], dtype=torch.int32, device=device)
+            st = torch.from_numpy(states[gs]).to(device)
+            ids = torch.from_numpy(gs.astype(np.int32)).to(device)
+            ctxs[v].dvc_play_move(st, acts, move_seed, polls, ids)
+            out = st.cpu().numpy()
+            over = np.nonzero(out[:, 28] != 0xFF)[0]
+            if len(over):   # a finished game is dealt afresh
+                fresh[v] += 1
+                out[over] = ctxs[v].dvc_init_states(5000 + 7919 * fresh[v] + v, len(over)).cpu().numpy()
+            states[gs] = out
+            moves += len(lst)
+            waiting[gs] = False
+            idle.extend(int(g) for g in gs)
+        if not done and not server.dvc_server_stats()["resident"] and now < duration_s:
+            time.sleep(max(0.0, min(next_arrival - (time.perf_counter() - t0), 0.01)))
+    wall = time.perf_counter() - t0
+    lat_s = np.array([x[0] for x in lat])
+    modes = np.array([x[1] for x in lat])
+    vars_ = np.array([x[2] for x in lat])
+    out = {
+        "games": n_games,
+        "variants": names,
+        "rate": rate,
+        "arrival_window_s": duration_s,
+        "queries": len(lat),
+        "wall_s": wall,
+        "decisions_per_s": len(lat) / wall,
+        "moves_played": moves,
+        "polls": polls,
+        "p50_ms": _pct(lat_s, 50),
+        "p99_ms": _pct(lat_s, 99),
+        "by_mode": {},
+        "by_variant": {},
+    }
+    for m, nm in ((0, "rollout"), (1, "value")):
+        sel = lat_s[modes == m]
+        out["by_mode"][nm] = {"queries": int(len(sel)), "p50_ms": _pct(sel, 50), "p99_ms": _pct(sel, 99)}
+    for v, nm in enumerate(names):
+        sel = lat_s[vars_ == v]
+        out["by_variant"][nm] = {"queries": int(len(sel)), "p50_ms": _pct(sel, 50), "p99_ms": _pct(sel, 99)}
+    return out

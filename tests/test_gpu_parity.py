@@ -407,3 +407,41 @@ def test_rollout_from_may_stop_leaves_bit_exact(dvc, variant):
         assert (wins[i] == w).all(), i
         total += wd
     assert int(words.item()) == total
+
+
+@pytest.mark.parametrize("variant,P,budgets,extra,engine", [
+    ("2p24", 32, [150, 57, 1, 120], {}, 1),
+    ("2p24", 32, [150, 57, 1, 120] * 40, {}, 2),
+    ("4p26j", 16, [120, 64, 30], {}, 1),
+    ("4p26j", 16, [120, 64, 30] * 60, {}, 2),
+    ("2p24", 16, [90, 40, 77], dict(tree_continue=1), 1),
+    ("3p24", 16, [90, 40, 77] * 60, dict(tree_continue=1), 2),
+])
+def test_forest_work_counters_match_oracle(dvc, variant, P, budgets, extra, engine):
+    """Random words and game steps (one per playout guess, plus a may-stop
+    leaf's first coin) counted by the GPU's playout kernels equal the
+    oracle's counts for the same searches, in both engines."""
+    kw = dict(VARIANTS[variant], playouts=P, **extra)
+    ocfg = oracle.OracleConfig(**kw)
+    n = len(budgets)
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(31, n)
+    oroots = oracle.init_states(ocfg, 31, n)
+    forest = dvc.Forest(ctx, roots, budgets, 6)
+    forest.dvc_forest_tune(engine)
+    forest.dvc_mcts_step(max(budgets))
+    work = forest.dvc_forest_work().cpu().numpy()
+    ctx.dvc_check()
+    out = {}
+
+    def run(t):
+        out[t] = oracle.mcts_work(ocfg, oroots[t], 6, t, int(budgets[t]))
+
+    ths = [threading.Thread(target=run, args=(t,)) for t in range(n)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert int(work[0]) == sum(w for w, _ in out.values())
+    assert int(work[1]) == sum(s for _, s in out.values())
+    assert (forest.dvc_forest_work().cpu().numpy() == 0).all()   # read-and-zero

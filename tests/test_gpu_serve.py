@@ -106,3 +106,68 @@ def test_poisson_driver_reports_latency(dvc):
     out = serving.poisson_run(sv, roots, budgets, np.zeros(200, dtype=int), rate=2000.0, iterations_per_poll=64)
     assert out["queries"] == 200 and out["p99_ms"] >= out["p50_ms"] > 0
     assert all(out["results"][i]["iterations"] == budgets[i] for i in range(200))
+
+
+MULTI = {
+    "2p24": dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5, playouts=32),
+    "3p24": dict(nplayers=3, ntiles=24, deal=4, max_predraw=6, max_revealed=3, playouts=32),
+    "2p26": dict(nplayers=2, ntiles=26, deal=4, max_predraw=10, max_revealed=5, playouts=32),
+    "4p26": dict(nplayers=4, ntiles=26, deal=3, max_predraw=8, max_revealed=3, playouts=32),
+}
+
+
+def test_multi_variant_mix_same_as_alone(dvc):
+    """One server over four game variants, rollout and value queries mixed:
+    every sampled result equals the same search run alone (its own forest of
+    one tree), and a query alone in a fresh server gives the same result."""
+    names = sorted(MULTI)
+    ctxs = []
+    for i, nm in enumerate(names):
+        c = dvc.Context(dvc.Config(**MULTI[nm]), 0)
+        c.dvc_value_init(40 + i)
+        ctxs.append(c)
+    seed = 13
+    per = 24
+    rng = np.random.default_rng(7)
+    queries = []   # (qid, variant index, root, budget, mode)
+    for vi, c in enumerate(ctxs):
+        roots = c.dvc_init_states(90 + vi, per).cpu().numpy()
+        for k in range(per):
+            queries.append((1000 * vi + k, vi, roots[k], int(rng.integers(20, 260)), int(rng.integers(0, 2))))
+    order = rng.permutation(len(queries))
+    sv = dvc.Server(ctxs, 512 << 20, 512, value_share_pct=40, seed=seed)
+    lanes = sv.dvc_server_lanes()
+    assert len(lanes) == 2 * len(names)
+    assert {(l["players"], l["tiles"], l["mode"]) for l in lanes} == {
+        (MULTI[n]["nplayers"], MULTI[n]["ntiles"], m) for n in names for m in (0, 1)}
+    got = {}
+    for step in range(2000):
+        for j in order[step * 9:(step + 1) * 9]:
+            qid, vi, root, b, mode = queries[j]
+            sv.dvc_server_submit(root, b, mode, qid)
+        for r in sv.dvc_server_poll(41):
+            got[r["query_id"]] = r
+        if len(got) == len(queries):
+            break
+    assert len(got) == len(queries)
+    for c in ctxs:
+        c.dvc_check()
+    for qid, vi, root, b, mode in queries[::5]:
+        r = got[qid]
+        assert r["mode"] == mode and r["iterations"] == b
+        assert _key(r) == _direct(dvc, ctxs[vi], root, b, qid, seed, mode=mode), (qid, vi, mode)
+    # alone in a fresh single-variant server
+    qid, vi, root, b, mode = next(q for q in queries if q[1] == 3 and q[4] == 1)
+    alone = dvc.Server(ctxs[vi], 64 << 20, 512, value_share_pct=50, seed=seed)
+    alone.dvc_server_submit(root, b, mode, qid)
+    res = []
+    while not res:
+        res = alone.dvc_server_poll(64)
+    assert _key(res[0]) == _key(got[qid])
+    # a root of a variant the server does not hold is refused on the host
+    other = dvc.Context(dvc.Config(nplayers=4, ntiles=24, deal=3, playouts=32), 0)
+    r4 = other.dvc_init_states(1, 1).cpu().numpy()[0]
+    with pytest.raises(dvc.DvcError):
+        sv.dvc_server_submit(r4, 100, 0, 99999)
+    sv.close()
+    alone.close()

@@ -185,3 +185,29 @@ def test_mcts_decision_prefers_winning_guess():
         cfg = oracle.OracleConfig(playouts=P)
         _, best = oracle.mcts(cfg, root, seed=3, tree=1, budget=64)
         assert best[0] == (1 << 10) | (5 << 5) | 5
+
+
+def test_mcts_work_counts_one_step_per_guess():
+    # With d_max = 0 every iteration's leaf is the determinized root, so the
+    # search's game steps are the traced playouts' lengths (one record per
+    # guess), plus one per playout for the continue coin a may-stop leaf
+    # draws first.
+    P, budget, seed, tree = 3, 5, 4, 2
+    cfg = oracle.OracleConfig(playouts=P, d_max=0, max_predraw=6)
+    root = oracle.init_states(cfg, 9, 1)[0]
+    want = 0
+    for it in range(budget):
+        leaf = oracle.determinize(cfg, root, int(root[23]), seed, tree, it)
+        want += sum(len(oracle.playout_trace(cfg, leaf, seed, tree, j, it)) for j in range(P))
+    words, steps = oracle.mcts_work(cfg, root, seed, tree, budget)
+    assert steps == want and words >= steps
+    # a may-stop root: the coin first
+    ms = root.copy()
+    ms[22] |= 2
+    cfg_c = oracle.OracleConfig(playouts=P, d_max=0, tree_continue=1)
+    want = budget * P
+    for it in range(budget):
+        leaf = oracle.determinize(cfg_c, ms, int(ms[23]), seed, tree, it)
+        assert leaf[22] & 2
+        want += sum(len(oracle.playout_trace(cfg_c, leaf, seed, tree, j, it)) for j in range(P))
+    assert oracle.mcts_work(cfg_c, ms, seed, tree, budget)[1] == want

@@ -45,3 +45,45 @@ def test_poisson_run_submits_every_query_once_in_order():
     lat = sorted(float(b) for b in budgets)           # a query takes exactly its budget in polls
     assert abs(out["p50_ms"] - 1e3 * np.percentile(lat, 50)) < 1e-6
     assert abs(out["p99_ms"] - 1e3 * np.percentile(lat, 99)) < 1e-6
+
+
+class _Ctx:
+    """A variant's context: roots tagged with the variant and a deal number;
+    a move bumps byte 30 (a move counter) and ends the game at 3 moves."""
+
+    def __init__(self, v, nplayers, ntiles):
+        import types
+        self.v = v
+        self.cfg = types.SimpleNamespace(nplayers=nplayers, ntiles=ntiles)
+        self.deals = 0
+
+    def dvc_init_states(self, seed, n):
+        import torch
+        s = torch.zeros((n, 32), dtype=torch.uint8)
+        s[:, 26] = self.cfg.nplayers
+        s[:, 27] = self.cfg.ntiles
+        s[:, 28] = 0xFF
+        s[:, 29] = self.v
+        self.deals += n
+        return s
+
+    def dvc_play_move(self, st, acts, seed, turn, ids):
+        assert (st[:, 29] == self.v).all()           # each game's moves go to its own variant
+        st[:, 30] += 1
+        st[st[:, 30] >= 3, 28] = 0
+        return st
+
+
+def test_game_serving_run_routes_moves_and_redeals():
+    srv = _Server()
+    ctxs = [_Ctx(0, 2, 24), _Ctx(1, 4, 26), _Ctx(2, 3, 24)]
+    out = serving.game_serving_run(srv, ctxs, n_games=30, rate=1e5, duration_s=0.05, budget_lo=1, budget_hi=4,
+                                   value_frac=0.5, seed=2, device="cpu")
+    assert out["queries"] == len(srv.order) and out["queries"] > 0
+    assert out["moves_played"] == out["queries"]
+    assert sorted(out["by_variant"]) == ["2p24", "3p24", "4p26"]
+    assert sum(v["queries"] for v in out["by_variant"].values()) == out["queries"]
+    assert sum(v["queries"] for v in out["by_mode"].values()) == out["queries"]
+    # a game finishes after three moves and is dealt afresh
+    if out["queries"] >= 90:
+        assert sum(c.deals for c in ctxs) > 30
