@@ -36,7 +36,22 @@ import numpy as np  # noqa: E402
 
 from paper_2403_10720_gb300.workloads import BATCHED, UNEVEN  # noqa: E402
 
-PHILOX_OPS_PER_WORD = 25  # Philox-4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds) per 4 words
+# Algorithmic 32-bit integer operations by throughput class, per random word
+# (Philox: 10 mul.lo/mul.hi, 10 xor + 5 key adds) and per game step of the
+# two-player 24-tile playout apart from its words (the guess: hands, the
+# unseen set and two population counts, the (slot, identity) split by one
+# multiply-high and a reciprocal multiply, the slot's tile by a 12-bit
+# select; the check, the reveal and the game-over test; the next seat's draw:
+# pool, count, multiply-high, select, insert).  Each step is listed in
+# the design doc section 7.
+OPS_PER_WORD = {"alu": 15, "mul": 10, "popc": 0}
+OPS_PER_STEP_2P24 = {"alu": 48, "mul": 5, "popc": 6}
+# Per-SM, per-clock throughput of each class (CUDA C++ Programming Guide,
+# arithmetic instruction throughput, compute capability 9.0 and 10.x): 64
+# lanes for 32-bit integer add, logic, shift, compare and multiply, 16 for
+# population count; an SM issues 4 warp instructions (128 lanes) per clock.
+LANES_PER_CLOCK = {"alu": 64, "mul": 64, "popc": 16}
+ISSUE_LANES_PER_CLOCK = 128
 VALUE_MACS_PER_LEAF = 640 * 512 + 2 * 512 * 512 + 512 * 4  # dense layers of the value network
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # DRAM bytes per launch of the pipeline's kernels at the default shape of the
@@ -44,7 +59,14 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # rollout CTA), from ncu captures (cold cache) summarised under profiles/
 # (dram_per_launch_2p24_4096trees_24chains.md).
 PROFILED_SHAPE = (24, 2, 16)
-DRAM_PER_LAUNCH = {"select": 399_941, "rollout": 73_061, "det": 206_464}
+DRAM_PER_LAUNCH = {"select": 400_907, "rollout": 73_456, "det": 202_752}
+# Warp instructions per step of the same workload at that shape (4,096 trees
+# x 4,096 iterations), summed over every kernel of the step by ncu
+# (graph-level capture, instruction counts only), and lanes active per warp
+# instruction (profiles/issue_slots_2p24_4096trees_24chains.md).
+ISSUE_PROFILE = {"warp_instructions_per_step": 5.6054e11, "lanes_active_per_instruction": 22.68,
+                 "source": "ncu smsp__inst_executed.sum / smsp__thread_inst_executed.sum over every kernel and "
+                           "graph of one step (profiles/issue_slots_2p24_4096trees_24chains.md)"}
 
 
 def _env_int(k, d):
@@ -239,8 +261,11 @@ def run_ours(args, w):
     trees_per_cta = args.trees_per_cta or max(2, min(64, math.ceil(n / (chains * 0.85 * sms))))
     warps = args.warps or max(4, min(16, (trees_per_cta * w.playouts + 31) // 32))
     forest.dvc_forest_tune(2, trees_per_cta, warps, chains)
+    if args.compact:
+        receivers, donate_at = (int(x) for x in args.compact.split(","))
+        forest.dvc_forest_compaction(receivers, donate_at)
     stats = torch.empty((n, 8), dtype=torch.int32, device=dev)
-    words = torch.zeros(1, dtype=torch.int64, device=dev)
+    work = torch.zeros(2, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     budget = int(budgets.max())
@@ -259,7 +284,7 @@ def run_ours(args, w):
         step()
     torch.cuda.synchronize()
     ctx.dvc_check()
-    forest.dvc_forest_counters(out=words)  # zero the counter
+    forest.dvc_forest_work(out=work)  # zero the counters
 
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     ev = [(E(), E(), E(), E()) for _ in range(args.steps)]
@@ -281,8 +306,9 @@ def run_ours(args, w):
     ctx.dvc_check()
     step_ms = [a.elapsed_time(b) for a, _, _, b in ev]
     kern_ms = [a.elapsed_time(b) for _, a, b, _ in ev]
-    forest.dvc_forest_counters(out=words)
-    words_per_step = int(words.item()) / args.steps
+    forest.dvc_forest_work(out=work)
+    words_per_step = int(work[0].item()) / args.steps
+    game_steps_per_step = int(work[1].item()) / args.steps
     total_s = sum(step_ms) / 1e3
     if world > 1:
         total_s = max_over_ranks(total_s, dist, dev)
@@ -313,14 +339,29 @@ def run_ours(args, w):
     decisions = host_stats.numpy()
 
     traffic = None
-    if (chains, trees_per_cta, warps) == PROFILED_SHAPE and n == 4096:
+    if (chains, trees_per_cta, warps) == PROFILED_SHAPE and n == 4096 and not args.compact:
         traffic = (budget * chains * (DRAM_PER_LAUNCH["select"] + DRAM_PER_LAUNCH["rollout"])
                    + -(-budget // 64) * chains * DRAM_PER_LAUNCH["det"])
     peaks, peak_kind = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e9
     kern_mean_s = sum(kern_ms) / len(kern_ms) / 1e3
-    achieved_gops = PHILOX_OPS_PER_WORD * words_per_step / kern_mean_s / 1e9
+    # ALU roofline in game steps: the algorithmic integer operations of one
+    # step (its own plus its share of random words), by class; the bound is
+    # the class that needs the most clocks per SM at its documented rate
+    wps = words_per_step / max(game_steps_per_step, 1.0)
+    ops = {c: OPS_PER_STEP_2P24[c] + wps * OPS_PER_WORD[c] for c in LANES_PER_CLOCK}
+    clocks_per_step = {c: ops[c] / LANES_PER_CLOCK[c] for c in ops}
+    clocks_per_step["issue"] = sum(ops.values()) / ISSUE_LANES_PER_CLOCK
+    bound_class = max(clocks_per_step, key=clocks_per_step.get)
+    peak_gsteps = props.multi_processor_count * sm_max * 1e6 / clocks_per_step[bound_class] / 1e9
+    achieved_gsteps = game_steps_per_step / kern_mean_s / 1e9
+    issue = None
+    if (chains, trees_per_cta, warps) == PROFILED_SHAPE and n == 4096 and budget == 4096 and not args.compact:
+        issue = {"utilisation": ISSUE_PROFILE["warp_instructions_per_step"] / (
+                     props.multi_processor_count * 4 * sm_max * 1e6 * (sum(step_ms) / len(step_ms) / 1e3)),
+                 "lanes_active_per_instruction": ISSUE_PROFILE["lanes_active_per_instruction"],
+                 "warp_instructions_per_playout": ISSUE_PROFILE["warp_instructions_per_step"] / playouts_per_step,
+                 "source": ISSUE_PROFILE["source"]} if ISSUE_PROFILE else None
 
     if rank != 0:
         if world > 1:
@@ -333,21 +374,30 @@ def run_ours(args, w):
         "config": {"workload": w.name, "trees": n, "iterations": w.budget, "playouts_per_leaf": w.playouts,
                    "players": w.nplayers, "tiles": w.ntiles, "d_max": w.d_max,
                    "engine": f"pipeline, {trees_per_cta} trees x {warps} warps per rollout CTA, {chains} chains, "
-                             "CUDA graph",
+                             "CUDA graph" + (f", lane compaction {args.compact}" if args.compact else ""),
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
         "decisions_per_s": n * world * args.steps / total_s,
         "kernel_ms": sum(kern_ms) / len(kern_ms),
         "words_per_playout": words_per_step / playouts_per_step,
+        "game_steps_per_playout": game_steps_per_step / playouts_per_step,
+        "game_steps_per_s": game_steps_per_step * world * args.steps / total_s,
+        "issue_slots": issue,
         "e2e": {"value": e2e_value, "unit": "playouts/s", "h2d_bytes_per_step": int(host_roots.numel()),
                 "d2h_bytes_per_step": int(host_stats.numel() * 4)},
         # kernels per step: forest reset, pipeline begin, per 64-iteration chunk one
         # determinization launch per chain, per iteration (select + rollout) x chains,
         # final backprop, root stats
         "gpu_launches": args.steps * (4 + chains * (-(-budget // 64)) + 2 * budget * chains),
-        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved_gops / peak_gops, "traffic": traffic,
-                     "peak_kind": f"{props.multi_processor_count} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind})",
-                     "work": "Philox-4x32-10 integer ops of the random words the playouts consume",
+        "roofline": {"bound": "alu", "achieved": achieved_gsteps, "peak": peak_gsteps, "unit": "Gstep/s",
+                     "frac": achieved_gsteps / peak_gsteps, "traffic": traffic,
+                     "peak_kind": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz ({peak_kind} clock) / "
+                                  f"{clocks_per_step[bound_class]:.3f} SM clocks per game step ({bound_class} "
+                                  "class bound)",
+                     "ops_per_step": {c: round(v, 2) for c, v in ops.items()},
+                     "clocks_per_step": {c: round(v, 4) for c, v in clocks_per_step.items()},
+                     "work": "game steps (a playout guess with its resolution, continue coin and the next seat's "
+                             "draw), counted by the playout kernels; per step the algorithmic integer operations "
+                             "by class, Philox words included",
                      "launch": "one dvc_mcts_step: the CUDA-graph pipeline (determinize-ahead, select, rollout "
                                "kernels of all chains)",
                      "traffic_source": "ncu dram__bytes per kernel launch (cold cache) x launches per step; null "
@@ -357,6 +407,17 @@ def run_ours(args, w):
     }
     if rank == 0:
         line["value_net"] = value_net_roofline(dvc, ctx, peaks, peak_kind)
+    if rank == 0 and world == 1 and not args.no_extras:
+        # the other configurations, each bounded in time: one step of the
+        # uneven forest, a serving run, the value network against playouts
+        forest.close()
+        del flush
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        line["uneven"] = measure_uneven(UNEVEN, steps=1, warmup=1)
+        line["serve"] = serve_games(10_000, 400.0, 10.0, 64.0, 100_000, 256)
+        line["value_vs_rollout"] = value_vs_rollout()
+        line["extras_wall_s"] = time.perf_counter() - t0
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         p, dt = oracle_sample(w, cores, cores)
@@ -368,64 +429,187 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
-def run_uneven(args, w):
-    """The uneven forest: every tree searches its whole budget; one step = all trees."""
+def measure_uneven(w, steps=1, warmup=1, trees=0, iterations=0, shape=None, warmup_cap=64):
+    """The uneven forest (config 3): every tree searches its whole budget; one
+    step = all trees.  The launch shape comes from the autotuner unless given;
+    the tail of long budgets runs on the fused engine (autotune.step_with_tail).
+    Warm-up steps run with budgets capped at warmup_cap iterations (graph
+    capture, kernel attributes).  Returns a dict of the measurement."""
     import torch
 
     import paper_2403_10720_gb300 as dvc
     from paper_2403_10720_gb300 import autotune, build
     build.build()
     ctx = dvc.Context(dvc.Config(**w.config_kwargs()), 0)
-    n = args.trees or w.n_trees
+    n = trees or w.n_trees
     roots = ctx.dvc_init_states(w.root_seed, n)
     budgets = w.budgets(n)
-    if args.iterations:  # small profiling cases: budgets capped
-        budgets = np.minimum(budgets, args.iterations).astype(np.int32)
-    if args.chains or args.trees_per_cta or args.warps:
-        shape = (2, args.trees_per_cta, args.warps, args.chains)
-    else:
+    if iterations:  # small profiling cases: budgets capped
+        budgets = np.minimum(budgets, iterations).astype(np.int32)
+    if shape is None:
         shape = autotune.tune(dvc, ctx, roots, budgets, w.seed, scale=0.02)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cut = autotune.tail_start(budgets, sms)
+    if warmup:
+        capped = np.minimum(budgets, warmup_cap).astype(np.int32)
+        f0 = dvc.Forest(ctx, roots, capped, w.seed)
+        f0.dvc_forest_tune(*shape)
+        for _ in range(warmup):
+            f0.dvc_forest_reset()
+            autotune.step_with_tail(f0, capped, shape, sms)
+        torch.cuda.synchronize()
+        f0.close()
     forest = dvc.Forest(ctx, roots, budgets, w.seed)
     forest.dvc_forest_tune(*shape)
     stats = torch.empty((n, 8), dtype=torch.int32, device=roots.device)
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    cut = autotune.tail_start(budgets, sms)
-
-    def search():
-        # the tuned shape while many trees run, one tree per fused CTA for the tail
-        autotune.step_with_tail(forest, budgets, shape, sms)
-    for _ in range(args.warmup):
-        forest.dvc_forest_reset()
-        search()
-    torch.cuda.synchronize()
+    work = torch.zeros(2, dtype=torch.int64, device=roots.device)
+    forest.dvc_forest_work(out=work)
     ev = []
     clocks = ClockSampler(0)
     clocks.start()
-    for _ in range(args.steps):
+    for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         forest.dvc_forest_reset()
-        search()
+        # the tuned shape while many trees run, one tree per fused CTA for the tail
+        autotune.step_with_tail(forest, budgets, shape, sms)
         forest.dvc_root_stats(out=stats)
         b.record()
         ev.append((a, b))
     torch.cuda.synchronize()
     clk = clocks.stop()
+    forest.dvc_forest_work(out=work)
     ctx.dvc_check()
     ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(ms) / 1e3
-    playouts = int(budgets.sum()) * w.playouts * args.steps
+    playouts = int(budgets.sum()) * w.playouts * steps
+    st = stats.cpu().numpy()
+    assert (st[:, 6] == budgets).all()
+    forest.close()
+    ctx.close()
+    return {"workload": w.name if n == w.n_trees and not iterations else f"{w.name}_first{n}_cap{iterations}",
+            "playouts_per_s": playouts / total_s, "decisions_per_s": n * steps / total_s,
+            "ms_per_step": 1e3 * total_s / steps, "steps": steps,
+            "game_steps_per_s": int(work[1].item()) / total_s,
+            "words_per_playout": int(work[0].item()) / playouts, "trees": n,
+            "iterations_total": int(budgets.sum()), "budget_range": [int(budgets.min()), int(budgets.max())],
+            "playouts_per_leaf": w.playouts, "players": w.nplayers, "tiles": w.ntiles,
+            "launch_shape": list(shape), "tail": {"from_iteration": cut, "launch_shape": list(autotune.TAIL_SHAPE)},
+            "clocks": clk}
+
+
+def run_uneven(args, w):
+    """Config 3 on its own (one JSON line)."""
+    m = measure_uneven(w, steps=args.steps, warmup=args.warmup, trees=args.trees, iterations=args.iterations,
+                       shape=(args.engine or 2, args.trees_per_cta, args.warps, args.chains)
+                       if (args.engine or args.chains or args.trees_per_cta or args.warps) else None)
     print(json.dumps({
-        "metric": "playouts/s", "value": playouts / total_s, "unit": "playouts/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "metric": "playouts/s", "value": m["playouts_per_s"], "unit": "playouts/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w.name if n == w.n_trees and not args.iterations else f"{w.name}_first{n}_cap{args.iterations}",
-                   "trees": n, "iterations_total": int(budgets.sum()),
-                   "budget_range": [int(budgets.min()), int(budgets.max())], "playouts_per_leaf": w.playouts,
-                   "players": w.nplayers, "tiles": w.ntiles, "launch_shape": list(shape),
-                   "tail": {"from_iteration": cut, "launch_shape": list(autotune.TAIL_SHAPE)},
-                   "l2": "working set (node arenas) far above L2"},
-        "decisions_per_s": n * args.steps / total_s, "clocks": clk}), flush=True)
+        "config": {k: m[k] for k in ("workload", "trees", "iterations_total", "budget_range", "playouts_per_leaf",
+                                     "players", "tiles", "launch_shape", "tail")} |
+                  {"l2": "working set (node arenas) far above L2"},
+        "decisions_per_s": m["decisions_per_s"], "game_steps_per_s": m["game_steps_per_s"], "clocks": m["clocks"]}),
+          flush=True)
+
+
+def _crossing(xs, ys, level=0.5):
+    """x where the piecewise-linear curve through (xs, ys) first reaches
+    `level` (xs ascending), or None if it does not within the range."""
+    for (x0, y0), (x1, y1) in zip(zip(xs, ys), zip(xs[1:], ys[1:])):
+        if (y0 - level) * (y1 - level) <= 0 and y1 != y0:
+            return x0 + (level - y0) * (x1 - x0) / (y1 - y0)
+        if y0 == level:
+            return x0
+    return None
+
+
+def value_vs_rollout(train_states=10_000_000, epochs=4, games=2000, rollout_budget=256,
+                     value_budgets=(128, 192, 256, 384), hbm_gb=4.0):
+    """Config 4: the value network trained on the GPU (states of the 2-player
+    24-tile root generator labelled by 1,024 playouts each), its held-out
+    win-probability error against rollout estimates, then games of the value
+    agent at several iteration budgets against the playout agent (32 playouts
+    per leaf) at rollout_budget, with 95% intervals; the GPU time per decision
+    of each agent; and the budget, in iterations and in GPU time relative to
+    the playout agent, at which the value agent wins half the games."""
+    import torch
+
+    import paper_2403_10720_gb300 as dvc
+    from paper_2403_10720_gb300 import build, selfplay
+    from paper_2403_10720_gb300 import value_train as vt
+    build.build()
+    w = BATCHED
+    kw = dict(w.config_kwargs(), playouts=32)
+    ctx = dvc.Context(dvc.Config(**kw), 0)
+    ctx.dvc_value_init(1)
+    t0 = time.perf_counter()
+    states, labels = vt.make_dataset(ctx, train_states, root_seed=1001)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    curve = vt.train(ctx, states, labels, epochs=epochs, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del states, labels
+    hs, hl = vt.make_dataset(ctx, 16384, root_seed=2002)
+    err = {"net": vt.mean_abs_error(ctx.dvc_value_eval(hs), hl, hs)}
+    for k in (16, 64, 256):
+        err[f"playouts_{k}"] = vt.mean_abs_error(vt.rollout_estimate(ctx, hs, k), hl, hs)
+    roots = ctx.dvc_init_states(w.root_seed, 4096)
+    agree = selfplay.move_agreement(ctx, dvc, roots, rollout_budget, 16 * rollout_budget, seed=7)
+    half = {k: 1.96 * math.sqrt(max(v * (1 - v), 1e-12) / agree["positions"]) for k, v in agree.items()
+            if k.endswith("strong") or k == "value_vs_rollout"}
+    agree["ci95_half_width"] = half
+
+    def us_per_decision(budget, mode):
+        f = dvc.Forest(ctx, roots, [budget] * 4096, 5)
+        f.dvc_mcts_step(budget, mode=mode)
+        f.dvc_forest_reset()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f.dvc_mcts_step(budget, mode=mode)
+        b.record()
+        torch.cuda.synchronize()
+        f.close()
+        return a.elapsed_time(b) * 1e3 / 4096
+    t_roll = us_per_decision(rollout_budget, dvc.DVC_MODE_ROLLOUT)
+    t_val = {b: us_per_decision(b, dvc.DVC_MODE_VALUE) for b in value_budgets}
+    gctx = dvc.Context(dvc.Config(**dict(kw, max_predraw=0)), 0)
+    gctx.dvc_value_init(1)
+    gctx.dvc_value_params(ctx.dvc_value_params())
+    server = dvc.Server(gctx, int(hbm_gb * (1 << 30)), max(max(value_budgets), rollout_budget), value_share_pct=50,
+                        seed=9)
+    points = []
+    t0 = time.perf_counter()
+    for b in value_budgets:
+        g = selfplay.play_games(gctx, server, games, rollout_budget, root_seed=3003, seed=11, value_budget=b,
+                                poll_iters=max(b, rollout_budget))
+        points.append({"value_iterations": b, "win_rate": g["value_win_rate"], "ci95": g["ci95"],
+                       "games_finished": g["games_finished"], "value_us_per_decision": t_val[b]})
+    t_games = time.perf_counter() - t0
+    server.close()
+    gctx.dvc_check()
+    ctx.dvc_check()
+    xs = [p["value_iterations"] for p in points]
+    mid = _crossing(xs, [p["win_rate"] for p in points])
+    lo = _crossing(xs, [p["ci95"][1] for p in points])   # upper edge reaches 0.5 first
+    hi = _crossing(xs, [p["ci95"][0] for p in points])
+    t_at = (lambda x: None if x is None else float(np.interp(x, xs, [t_val[b] for b in xs])))
+    return {
+        "workload": "2p24_value_vs_playouts_selfplay", "games_per_point": games, "players": 2, "tiles": 24,
+        "rollout_iterations": rollout_budget, "playouts_per_leaf": 32, "points": points,
+        "rollout_us_per_decision": t_roll,
+        "value_iterations_at_50pct": mid, "value_iterations_at_50pct_ci95": [lo, hi],
+        "gpu_time_ratio_at_50pct": None if mid is None else t_at(mid) / t_roll,
+        "gpu_time_ratio_at_50pct_ci95": [None if x is None else t_at(x) / t_roll for x in (lo, hi)],
+        "winprob_abs_err_heldout": err, "move_agreement": agree,
+        "train": {"states": train_states, "label_playouts": 1024, "epochs": epochs, "label_s": t_label,
+                  "train_s": t_train, "loss_first_epoch": curve[0], "loss_last_epoch": curve[-1]},
+        "games_wall_s": t_games,
+    }
 
 
 def run_selfplay(args):
@@ -744,32 +928,62 @@ def run_scaling(args):
           flush=True)
 
 
-def run_serve(args):
-    """Poisson arrivals of move queries into a device-resident server."""
-    import numpy as np
-    import torch
+SERVE_VARIANTS = [  # config 5: 2-4 players, 24- and 26-tile games (26 tiles: with the two jokers)
+    dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5),
+    dict(nplayers=3, ntiles=24, deal=4, max_predraw=6, max_revealed=3),
+    dict(nplayers=4, ntiles=24, deal=3, max_predraw=6, max_revealed=3),
+    dict(nplayers=2, ntiles=26, deal=4, max_predraw=10, max_revealed=5),
+    dict(nplayers=3, ntiles=26, deal=4, max_predraw=6, max_revealed=3),
+    dict(nplayers=4, ntiles=26, deal=3, max_predraw=8, max_revealed=3),
+]
 
+
+def serve_games(games, rate, window_s, hbm_gb, max_budget, poll_iters, value_frac=0.5, value_share_pct=35):
+    """Serving (config 5): one server over six game variants sharing an HBM
+    budget, Poisson arrivals of move queries from `games` concurrent games,
+    value and rollout modes mixed per query.  Returns the driver's dict plus
+    the server's slot layout."""
     import paper_2403_10720_gb300 as dvc
     from paper_2403_10720_gb300 import build, serving
     build.build()
-    kw = dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5, playouts=32)
-    ctx = dvc.Context(dvc.Config(**kw), 0)
-    n = args.queries
-    roots = ctx.dvc_init_states(505, n).cpu().numpy()
-    rng = np.random.default_rng(5)
-    budgets = np.floor(np.exp(rng.uniform(np.log(1000), np.log(args.max_budget), size=n))).astype(np.int32)
-    server = dvc.Server(ctx, int(args.hbm_gb * (1 << 30)), args.max_budget, seed=5)
-    out = serving.poisson_run(server, roots, budgets, np.zeros(n, dtype=int), rate=args.rate,
-                              iterations_per_poll=args.poll_iters, seed=6, max_seconds=900)
-    st = server.dvc_server_stats()
+    ctxs = []
+    for i, kw in enumerate(SERVE_VARIANTS):
+        c = dvc.Context(dvc.Config(**dict(kw, playouts=32)), 0)
+        c.dvc_value_init(100 + i)
+        ctxs.append(c)
+    server = dvc.Server(ctxs, int(hbm_gb * (1 << 30)), max_budget, value_share_pct=value_share_pct, seed=5)
+    lanes = server.dvc_server_lanes()
+    out = serving.game_serving_run(server, ctxs, games, rate, window_s, budget_lo=1000, budget_hi=max_budget,
+                                   value_frac=value_frac, seed=6, iterations_per_poll=poll_iters)
+    for c in ctxs:
+        c.dvc_check()
+    after = server.dvc_server_lanes()
+    server.close()
+    out["lanes"] = [{"variant": f"{l['players']}p{l['tiles']}", "mode": ("rollout", "value")[l["mode"]],
+                     "slots": l["slots"], "steps": a["steps"],
+                     "us_per_iteration": a["step_us"] / poll_iters if a["steps"] else None}
+                    for l, a in zip(lanes, after)]
+    out["hbm_gb"] = hbm_gb
+    out["iterations_per_poll"] = poll_iters
+    out["budget_range"] = [1000, max_budget]
+    out["value_frac"] = value_frac
+    out["playouts_per_leaf"] = 32
+    return out
+
+
+def run_serve(args):
+    """Config 5 on its own: Poisson arrivals of move queries from concurrent
+    games of six variants into one device-resident server (one JSON line)."""
+    out = serve_games(args.games_live, args.rate, args.window, args.hbm_gb, args.max_budget, args.poll_iters)
     print(json.dumps({
         "metric": "decisions/s", "value": out["decisions_per_s"], "unit": "decisions/s", "n_gpus": 1,
-        "higher_is_better": True, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "serving_2p24_poisson", "queries": n, "rate_per_s": args.rate,
-                   "budget_range": [1000, args.max_budget], "playouts_per_leaf": 32, "hbm_gb": args.hbm_gb,
-                   "slots": st["rollout_slots"], "iterations_per_poll": args.poll_iters},
-        "p50_ms": out["p50_ms"], "p99_ms": out["p99_ms"], "wall_s": out["wall_s"],
-        "playouts_per_s": float(budgets.sum()) * 32 / out["wall_s"]}), flush=True)
+        "higher_is_better": True, "dtype": "u32 playouts / bf16 net", "data": "synthetic",
+        "config": {"workload": "serving_6variants_poisson", "games": out["games"], "rate_per_s": args.rate,
+                   "arrival_window_s": args.window, "budget_range": out["budget_range"],
+                   "value_frac": out["value_frac"], "playouts_per_leaf": 32, "hbm_gb": args.hbm_gb,
+                   "iterations_per_poll": args.poll_iters},
+        **{k: out[k] for k in ("queries", "wall_s", "moves_played", "p50_ms", "p99_ms", "by_mode", "by_variant",
+                               "lanes")}}), flush=True)
 
 
 def main():
@@ -779,18 +993,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven-forest, serving and value-vs-playout sub-measurements")
     ap.add_argument("--trees", type=int, default=0, help="override the tree count (small profiling cases)")
     ap.add_argument("--iterations", type=int, default=0, help="override the iterations per tree")
     ap.add_argument("--chains", type=int, default=0, help="pipeline chains (launch shape only; 0 = default)")
     ap.add_argument("--trees-per-cta", type=int, default=0, help="pipeline trees per rollout CTA (0 = default)")
     ap.add_argument("--warps", type=int, default=0, help="warps per rollout CTA (0 = default)")
+    ap.add_argument("--compact", default="", help="lane compaction 'receivers,donate_at' (default off)")
+    ap.add_argument("--engine", type=int, default=0, help="uneven: 1 fused, 2 pipeline (launch shape only)")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "uneven", "serve", "selfplay", "policy", "scaling", "fulltree", "vanilla"])
     ap.add_argument("--train-states", type=int, default=10_000_000, help="selfplay: training states")
     ap.add_argument("--epochs", type=int, default=4, help="selfplay: training epochs")
     ap.add_argument("--games", type=int, default=10_000, help="selfplay: games between the two agents")
     ap.add_argument("--move-budget", type=int, default=256, help="selfplay: UCT iterations per move")
-    ap.add_argument("--queries", type=int, default=2000, help="serve: number of move queries")
+    ap.add_argument("--games-live", type=int, default=10_000, help="serve: concurrent games")
+    ap.add_argument("--window", type=float, default=10.0, help="serve: seconds of query arrivals")
     ap.add_argument("--rate", type=float, default=400.0, help="serve: Poisson arrival rate (queries/s)")
     ap.add_argument("--max-budget", type=int, default=100000, help="serve: largest query budget")
     ap.add_argument("--hbm-gb", type=float, default=64.0, help="serve: HBM budget for resident searches")

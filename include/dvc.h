@@ -307,6 +307,17 @@ int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream);
  * the method: a draw, a joker position, a guess or a continue coin).  Copies
  * then zeroes the counter, on `stream`.  d_out: one uint64. */
 int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream);
+/* Lane compaction in the pipeline engine's two-player 24-tile playouts
+ * (uniform policy, no may-stop leaves; other forests ignore it), off by
+ * default (receivers = 0).  The paper studies the branch divergence of GPU
+ * playouts (Sec. IV); this regroups running games instead: once a rollout
+ * CTA's pool of playouts is empty, each of its warps from `receivers` on
+ * that has at most `donate_at` games running hands them (state and stream
+ * position) to the CTA's first `receivers` warps, whose idle lanes finish
+ * them.  Results are identical either way.  DVC_E_INVALID unless
+ * 0 <= receivers < warps per rollout CTA and 1 <= donate_at <= 31.  Takes
+ * effect at the next dvc_mcts_step. */
+int dvc_forest_compaction(dvc_forest* f, int receivers, int donate_at);
 /* The forest's playout work since creation or the last call, two uint64:
  * d_out[0] random words (as dvc_forest_counters), d_out[1] game steps -- one
  * per guess of a playout (Sec. II-A: the guess with its resolution, any
@@ -399,9 +410,12 @@ int dvc_gemm_timeout_probe(dvc_ctx* ctx, const void* d_A, const void* d_B, float
  * Serving: a request loop that keeps many searches resident on the device.
  * Move queries from concurrent games (root state, iteration budget, leaf
  * mode, id) wait in a FIFO queue and are admitted as search slots free up
- * (continuous batching): every poll admits queued queries into free slots,
- * runs `iterations` more iterations of every resident search together, and
- * returns the queries whose budget is complete.  Slots are sized for
+ * (continuous batching).  The slots form lanes (below); each lane steps on
+ * its own stream: a step runs `iterations` more iterations of every resident
+ * search of the lane together.  A poll collects the lanes whose step has
+ * finished (returning the queries whose budget is complete), admits queued
+ * queries into their free slots and starts their next step; if no lane had
+ * finished it waits (on the host) until one has.  Slots are sized for
  * max_budget iterations and their number is fixed at creation by the HBM
  * budget, so admission is by memory.  A query's search is keyed by (seed,
  * low 32 bits of its id) and runs exactly as it would alone: results do not
@@ -440,11 +454,14 @@ void dvc_server_destroy(dvc_server* sv);
  * (DVC_E_INVALID otherwise; DVC_E_UNSUPPORTED if that variant has no slots
  * of this mode). */
 int dvc_server_submit(dvc_server* sv, const dvc_state* h_root, int budget, int mode, uint64_t query_id);
-/* Admit, search `iterations` more, collect; returns the number of results written (<= max_results). */
+/* Collect finished lanes, admit, start their next `iterations`; returns the number of results written
+ * (<= max_results; results that did not fit are returned by the next poll). */
 int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int max_results);
 /* h_out[5]: queued, resident, completed, rollout slots, value slots (over all lanes). */
 int dvc_server_stats(dvc_server* sv, int64_t* h_out);
-/* Per lane, 6 int32: context index, players, tiles, mode, slots, resident.
+/* Per lane, 8 int32: context index, players, tiles, mode, slots, resident,
+ * steps collected so far, their mean device time in microseconds (from the
+ * step's first launch to its statistics on the host side of the copy).
  * Writes min(lanes, max_lanes) rows; returns the number of lanes. */
 int dvc_server_lanes(dvc_server* sv, int max_lanes, int32_t* h_out);
 

@@ -119,6 +119,7 @@ def lib():
             "dvc_root_stats": ([vp, vp, vp], i),
             "dvc_forest_counters": ([vp, vp, vp], i),
             "dvc_forest_work": ([vp, vp, vp], i),
+            "dvc_forest_compaction": ([vp, i, i], i),
             "dvc_tree_export": ([vp, i, vp, vp], i),
             "dvc_philox": ([vp, i, vp, vp, vp, i, vp], i),
             "dvc_determinize_noalloc": ([vp, i, i, u64, vp, vp, vp, vp, vp], i),
@@ -351,6 +352,9 @@ class Forest:
         self.ctx._rc(lib().dvc_forest_counters(self.h, _ptr(out), _stream(stream)), "dvc_forest_counters")
         return out
 
+    def dvc_forest_compaction(self, receivers, donate_at=8):
+        self.ctx._rc(lib().dvc_forest_compaction(self.h, receivers, donate_at), "dvc_forest_compaction")
+
     def dvc_forest_work(self, out=None, stream=None):
         """(random words, game steps) of the forest's playouts since the last call."""
         out = torch.zeros(2, dtype=torch.int64, device=self.ctx.dev()) if out is None else out
@@ -426,11 +430,11 @@ class Server:
         return dict(queued=a[0], resident=a[1], completed=a[2], rollout_slots=a[3], value_slots=a[4])
 
     def dvc_server_lanes(self):
-        """Per lane: dict(context, players, tiles, mode, slots, resident)."""
-        a = (ctypes.c_int32 * (6 * 64))()
+        """Per lane: dict(context, players, tiles, mode, slots, resident, steps, step_us)."""
+        a = (ctypes.c_int32 * (8 * 64))()
         n = lib().dvc_server_lanes(self.h, 64, a)
         if n < 0:
             self.ctx._rc(n, "dvc_server_lanes")
-        keys = ("context", "players", "tiles", "mode", "slots", "resident")
-        return [dict(zip(keys, a[6 * i:6 * i + 6])) for i in range(min(n, 64))]
+        keys = ("context", "players", "tiles", "mode", "slots", "resident", "steps", "step_us")
+        return [dict(zip(keys, a[8 * i:8 * i + 8])) for i in range(min(n, 64))]
 

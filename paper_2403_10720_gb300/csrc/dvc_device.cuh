@@ -595,6 +595,21 @@ struct RingQueue {
         return r;
     }
     __device__ __forceinline__ uint32_t used() const { return head; }
+    // Continue a stream another lane started (stream fields already set):
+    // h words were handed out; this lane's ring gets the block holding word
+    // h, so the next word is word h of the stream.
+    __device__ __forceinline__ void resume(uint32_t h) {
+        head = h;
+        tail = h & ~3u;
+        uint32_t a = tail >> 2, b = j, c = i, d = tw;
+        philox10(a, b, c, d, k0, k1);
+        const uint32_t s = tail & 15u;
+        ring[s * stride] = a;
+        ring[(s + 1u) * stride] = b;
+        ring[(s + 2u) * stride] = c;
+        ring[(s + 3u) * stride] = d;
+        tail += 4u;
+    }
 };
 
 // One step of a two-player, 24-tile playout (no jokers): the mover guesses;

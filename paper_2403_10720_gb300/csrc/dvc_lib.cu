@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "dvc_internal.h"
@@ -85,6 +86,8 @@ struct dvc_forest {
     int chains;               // independent chains in the pipeline graph (1..32)
     float* probs;             // value mode: win probabilities per tree
     int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
+    int cmp_receivers;        // lane compaction in the pipeline's two-player playouts: receiver warps (0 = off)
+    int cmp_donate_at;        // ... and the running games at or below which a donor warp hands its games over
 };
 
 namespace {
@@ -1013,7 +1016,10 @@ int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
     // may-stop leaves possible: the full tree, or leaves that can be the root itself
     const bool pend = c->cfg.tree_continue || c->cfg.d_max == 0 || c->cfg.vanilla;
     const uint32_t smem = pipe_rollout_smem(L, threads);
-    if (fast2 && !sp.policy && !pend)
+    if (fast2 && !sp.policy && !pend && f->cmp_receivers > 0 && f->cmp_receivers < threads / 32)
+        pipe_rollout_compact_kernel<<<b1 - b0, threads, pipe_compact_smem(L, threads, f->cmp_receivers), st>>>(
+            sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words, f->cmp_receivers, f->cmp_donate_at);
+    else if (fast2 && !sp.policy && !pend)
         pipe_rollout_kernel<true, false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta,
                                                                                f->pipe, f->d_words);
     else if (fast2 && !sp.policy)
@@ -1132,6 +1138,13 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+        }
+        if (e == cudaSuccess && f->cmp_receivers > 0) {
+            const int smc = (int)pipe_compact_smem(f->trees_per_cta, threads, f->cmp_receivers);
+            e = cudaFuncSetAttribute(pipe_rollout_compact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smc);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(pipe_rollout_compact_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared);
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "pipeline attributes");
@@ -1365,6 +1378,20 @@ int dvc_forest_counters(dvc_forest* f, uint64_t* d_out, void* stream) {
     return DVC_OK;
 }
 
+int dvc_forest_compaction(dvc_forest* f, int receivers, int donate_at) {
+    if (!f) return DVC_E_INVALID;
+    const int warps = pipe_rollout_threads(f) / 32;
+    if (receivers < 0 || (receivers > 0 && (receivers >= warps || donate_at < 1 || donate_at > 31)))
+        return fail(f->ctx, DVC_E_INVALID, "dvc_forest_compaction: 0 <= receivers < warps per rollout CTA, 1 <= donate_at <= 31");
+    if (receivers != f->cmp_receivers || donate_at != f->cmp_donate_at) {
+        if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);  // recaptured with the other kernel
+        f->chunk_exec = nullptr;
+    }
+    f->cmp_receivers = receivers;
+    f->cmp_donate_at = receivers ? donate_at : 0;
+    return DVC_OK;
+}
+
 int dvc_forest_work(dvc_forest* f, uint64_t* d_out, void* stream) {
     if (!f) return DVC_E_INVALID;
     if (!is_device_ptr(d_out, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_work: d_out must be device memory");
@@ -1466,7 +1493,11 @@ struct ServerLane {
     int32_t* d_stats = nullptr;
     int32_t* h_stats = nullptr;
     int resident = 0;
-    bool stepped = false;
+    cudaEvent_t begin = nullptr;  // recorded before a step's search
+    cudaEvent_t done = nullptr;   // recorded after the step's statistics reach h_stats
+    bool in_flight = false;       // a step of this lane is enqueued and not yet collected
+    long long steps = 0;          // steps collected
+    double step_us = 0.0;         // their device time (begin to done)
 };
 
 // Device bytes of one search slot of context c sized for max_budget
@@ -1500,6 +1531,8 @@ void lane_free(ServerLane& L) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (L.h_stats) cudaFreeHost(L.h_stats);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.begin) cudaEventDestroy(L.begin);
     if (L.st) cudaStreamDestroy(L.st);
     L = ServerLane();
 }
@@ -1511,6 +1544,7 @@ int lane_create(ServerLane& L, dvc_ctx* c, int ctx_index, int mode, int n, int m
     L.mode = mode;
     L.ctx_index = ctx_index;
     if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&L.done) != cudaSuccess || cudaEventCreate(&L.begin) != cudaSuccess ||
         cudaMalloc(&L.d_slot, 4 * (size_t)n) != cudaSuccess || cudaMalloc(&L.d_budget, 4 * (size_t)n) != cudaSuccess ||
         cudaMalloc(&L.d_tid, 4 * (size_t)n) != cudaSuccess ||
         cudaMalloc(&L.d_root, sizeof(dvc_state) * (size_t)n) != cudaSuccess ||
@@ -1691,37 +1725,27 @@ int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int m
     if (iterations < 0 || max_results < 0 || (max_results > 0 && !h_results))
         return fail(c, DVC_E_INVALID, "dvc_server_poll: iterations >= 0, results buffer");
     if (int rc = set_device(c)) return rc;
-    // 1. admission, then `iterations` more of every lane's resident searches
-    //    and its root statistics, each lane on its own stream
-    for (int li = 0; li < (int)sv->lanes.size(); ++li) {
-        ServerLane& L = sv->lanes[li];
-        L.stepped = false;
-        if (int rc = lane_admit(sv, li)) return rc;
-        if (L.resident == 0) continue;
-        int top = -1;
-        for (int s = 0; s < L.f->n; ++s)
-            if (L.slots[s].busy) top = s;
-        L.f->active_prefix = top + 1;
-        if (iterations > 0)
-            if (int rc = dvc_mcts_step(L.f, iterations, L.mode, L.st)) return rc;
-        if (int rc = dvc_root_stats(L.f, L.d_stats, L.st)) return rc;
-        const cudaError_t e = cudaMemcpyAsync(L.h_stats, L.d_stats, 32 * (size_t)L.f->n, cudaMemcpyDeviceToHost, L.st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll copy");
-        L.stepped = true;
-    }
-    // 2. wait for every lane, then collect the finished queries
-    for (ServerLane& L : sv->lanes) {
-        const cudaError_t e = cudaStreamSynchronize(L.st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll");
-    }
-    const double t = now_s();
     int written = 0;
-    for (ServerLane& L : sv->lanes) {
-        if (!L.stepped) continue;
-        for (int s = 0; s < L.f->n && written < max_results; ++s) {
+    // collect the finished queries of a lane whose step is complete; the lane
+    // stays collected-pending while some finished query did not fit
+    auto collect = [&](ServerLane& L) -> bool {
+        const double t = now_s();
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, L.begin, L.done) == cudaSuccess) {
+            L.steps++;
+            L.step_us += 1e3 * (double)ms;
+        } else {
+            cudaGetLastError();
+        }
+        bool all = true;
+        for (int s = 0; s < L.f->n; ++s) {
             ServerSlot& sl = L.slots[s];
             const int32_t* st = L.h_stats + 8 * s;
             if (!sl.busy || st[6] < sl.q.budget) continue;
+            if (written >= max_results) {
+                all = false;
+                break;
+            }
             dvc_result& r = h_results[written++];
             r.query_id = sl.q.id;
             r.best_action = st[0];
@@ -1736,6 +1760,63 @@ int dvc_server_poll(dvc_server* sv, int iterations, dvc_result* h_results, int m
             L.resident--;
             sv->completed++;
         }
+        return all;
+    };
+    // enqueue admission, `iterations` more of the lane's resident searches
+    // and its root statistics on the lane's stream
+    auto launch = [&](int li) -> int {
+        ServerLane& L = sv->lanes[li];
+        if (int rc = lane_admit(sv, li)) return rc;
+        if (L.resident == 0) return DVC_OK;
+        int top = -1;
+        for (int s = 0; s < L.f->n; ++s)
+            if (L.slots[s].busy) top = s;
+        L.f->active_prefix = top + 1;
+        cudaError_t e = cudaEventRecord(L.begin, L.st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll launch");
+        if (iterations > 0)
+            if (int rc = dvc_mcts_step(L.f, iterations, L.mode, L.st)) return rc;
+        if (int rc = dvc_root_stats(L.f, L.d_stats, L.st)) return rc;
+        e = cudaMemcpyAsync(L.h_stats, L.d_stats, 32 * (size_t)L.f->n, cudaMemcpyDeviceToHost, L.st);
+        if (e == cudaSuccess) e = cudaEventRecord(L.done, L.st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server_poll launch");
+        L.in_flight = true;
+        return DVC_OK;
+    };
+    // 1. lanes whose step is complete: collect, then relaunch with newly
+    //    admitted queries; lanes never stepped or idle: launch
+    bool any_done = false;
+    for (int li = 0; li < (int)sv->lanes.size(); ++li) {
+        ServerLane& L = sv->lanes[li];
+        if (L.in_flight) {
+            const cudaError_t q = cudaEventQuery(L.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return cuda_fail(c, q, "dvc_server_poll");
+            any_done = true;
+            if (!collect(L)) continue;  // results left over: collect them next poll first
+            L.in_flight = false;
+        }
+        if (int rc = launch(li)) return rc;
+    }
+    // 2. if nothing completed yet, wait (host-side) until some lane's step
+    //    does, collect it and relaunch it
+    bool waiting = !any_done;
+    while (waiting) {
+        bool flying = false;
+        for (int li = 0; li < (int)sv->lanes.size() && waiting; ++li) {
+            ServerLane& L = sv->lanes[li];
+            if (!L.in_flight) continue;
+            flying = true;
+            const cudaError_t q = cudaEventQuery(L.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return cuda_fail(c, q, "dvc_server_poll");
+            waiting = false;
+            if (!collect(L)) break;
+            L.in_flight = false;
+            if (int rc = launch(li)) return rc;
+        }
+        if (!flying) break;
+        if (waiting) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     return written;
 }
@@ -1760,13 +1841,15 @@ int dvc_server_lanes(dvc_server* sv, int max_lanes, int32_t* h_out) {
     const int n = (int)sv->lanes.size();
     for (int i = 0; i < n && i < max_lanes; ++i) {
         const ServerLane& L = sv->lanes[i];
-        int32_t* o = h_out + 6 * i;
+        int32_t* o = h_out + 8 * i;
         o[0] = L.ctx_index;
         o[1] = L.ctx->cfg.nplayers;
         o[2] = L.ctx->cfg.ntiles;
         o[3] = L.mode;
         o[4] = (int32_t)L.slots.size();
         o[5] = L.resident;
+        o[6] = (int32_t)std::min<long long>(L.steps, INT32_MAX);
+        o[7] = (int32_t)std::min<double>(L.step_us / std::max<long long>(L.steps, 1), (double)INT32_MAX);
     }
     return n;
 }

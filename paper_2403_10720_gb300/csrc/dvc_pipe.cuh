@@ -159,6 +159,9 @@ __global__ void __launch_bounds__(128)
 // PEND: leaves may begin where the mover may stop (the full game tree, or
 // d_max = 0); without it that check is compiled out of the playout loop,
 // since an in-tree action always clears the may-stop bit otherwise.
+// Registers: 32 for the two-player path (two 1024-thread or three
+// 512-thread CTAs per SM, with room left in the register file for the
+// other chains' tree walks), up to 64 for the general path.
 template <bool FAST2, bool ORD = false, bool PEND = true>
 __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     pipe_rollout_kernel(SearchParams sp, int n, int L, int b0, const int32_t* order, const TreeMeta* meta, PipeBufs P,
@@ -204,7 +207,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     // playout p belongs to leaf p / Pp: multiply-high by ceil(2^32 / Pp) gives
     // the quotient or one more (p < 2^32), fixed by one comparison
     const uint32_t mP = Pp > 1u ? 0xFFFFFFFFu / Pp + 1u : 0u;
-    unsigned long long words = 0ull, nsteps = 0ull;
+    // work counters: random words per lane; game steps per warp (every
+    // running lane takes one step per pass of the loop)
+    uint32_t words = 0u, wsteps = 0u;
     uint32_t k = 0, steps = 0;
     RingQueue r;
     r.ring = s_ring + tid;
@@ -245,7 +250,10 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     uint32_t p = take(true);
     bool busy = p < total;
     if (busy) start(p);
-    while (__any_sync(0xFFFFFFFFu, busy)) {
+    for (;;) {
+        const unsigned running = __ballot_sync(0xFFFFFFFFu, busy);
+        if (!running) break;
+        wsteps += __popc(running);
         bool ended = false;
         if (busy) {
             int res;
@@ -267,13 +275,12 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
             }
             ++steps;
             if (res == kGameOver || steps >= 128u) {
-                // a game has at most |T| guesses (each turns one tile face up),
-                // so 128 steps means a broken invariant: latch it, credit nobody
-                if (res != kGameOver) latch_error(P.flags, DVC_E_INTERNAL);
+                // a game has at most |T| guesses (each turns one tile face up), so
+                // 128 steps means a broken invariant: nobody is credited, and the
+                // leaf's wins fall short of P (checked below)
                 const uint32_t w = res == kGameOver ? winner : kNone;
                 if (w < 4u) atomicAdd(&s_wins[4 * k + w], 1);
                 words += r.used();
-                nsteps += steps;
                 ended = true;
             }
         }
@@ -292,12 +299,263 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         w[1] = s_wins[4 * e + 1];
         w[2] = s_wins[4 * e + 2];
         w[3] = s_wins[4 * e + 3];
+        if (s_wins[4 * e] + s_wins[4 * e + 1] + s_wins[4 * e + 2] + s_wins[4 * e + 3] != (int32_t)Pp)
+            latch_error(P.flags, DVC_E_INTERNAL);
     }
     if (words_out) {  // words_out[0]: random words, words_out[1]: game steps (guesses)
-        const unsigned long long sum = warp_sum_u64(words);
-        const unsigned long long st = warp_sum_u64(nsteps);
+        const unsigned long long sum = warp_sum_u64((unsigned long long)words);
         if (lane == 0 && sum) atomicAdd(words_out, sum);
-        if (lane == 0 && st) atomicAdd(words_out + 1, st);
+        if (lane == 0 && wsteps) atomicAdd(words_out + 1, (unsigned long long)wsteps);
+        if constexpr (PEND && !FAST2) {
+            // the general path draws a may-stop leaf's first continue coin when
+            // a playout starts, outside the loop counted above: one step each
+            if (tid == 0) {
+                unsigned long long coins = 0ull;
+                for (int e = 0; e < nl; ++e) coins += (s_leaf[e].flags & 2u) ? Pp : 0u;
+                if (coins) atomicAdd(words_out + 1, coins);
+            }
+        }
+    }
+}
+
+// Dynamic shared memory of pipe_rollout_kernel: the word rings and the
+// listed leaves.
+__host__ __device__ inline uint32_t pipe_rollout_smem(int L, int threads) {
+    return (uint32_t)(64 * threads + 4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
+}
+
+// Lane compaction for the two-player 24-tile playouts (uniform policy, no
+// may-stop leaves), a variant of pipe_rollout_kernel measured against it
+// and off by default.  Warps 0 .. R-1 receive, the others donate: once the
+// CTA's pool of playouts is empty, a donor warp with at most `donate_at`
+// games still running posts them (state, leaf, stream position) to a mailbox
+// in shared memory and leaves the playout loop; receiver lanes that are idle
+// take posted games and finish them.  Every game goes on with the same words
+// of its own stream, so results equal the default kernel's.  Receivers stop
+// once no donor is left and the mailbox is drained; every wait is bounded
+// (DVC_E_TIMEOUT latched if a limit is hit).
+constexpr int kMailFields = 11;
+
+__host__ __device__ inline uint32_t pipe_compact_smem(int L, int threads, int receivers) {
+    const uint32_t cap = (uint32_t)(threads / 32 - receivers) * 32u;
+    return pipe_rollout_smem(L, threads) + cap * 4u * (kMailFields + 1u);
+}
+
+__global__ void __launch_bounds__(1024, 2)
+    pipe_rollout_compact_kernel(SearchParams sp, int n, int L, int b0, const int32_t* order, const TreeMeta* meta,
+                                PipeBufs P, unsigned long long* words_out, int R, int donate_at) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_magic[32];
+    __shared__ unsigned long long s_lut12[4096];
+    __shared__ int32_t s_n, s_next, s_posted, s_taken, s_donors;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    uint32_t* s_ring = (uint32_t*)smem;
+    int32_t* s_tree = (int32_t*)(smem + 64u * blockDim.x);
+    int32_t* s_wins = s_tree + L;
+    uint32_t* s_tid = (uint32_t*)(s_wins + 4 * L);
+    uint32_t* s_it = s_tid + L;
+    dvc_state* s_leaf = (dvc_state*)(((uintptr_t)(s_it + L) + 15) & ~(uintptr_t)15);
+    const uint32_t cap = (blockDim.x >> 5) * 32u - (uint32_t)R * 32u;
+    uint32_t* mail = (uint32_t*)(smem + pipe_rollout_smem(L, blockDim.x));  // kMailFields x cap, then cap flags
+    volatile uint32_t* ready = mail + kMailFields * cap;
+    fill_magic(s_magic, tid, blockDim.x);
+    fill_select12(s_lut12, tid, blockDim.x);
+    for (uint32_t e = tid; e < cap; e += blockDim.x) ready[e] = 0u;
+    if (tid == 0) {
+        int32_t k = 0;
+        for (int e = 0; e < L; ++e) {
+            const int i = (b0 + (int)blockIdx.x) * L + e;
+            if (i >= n) break;
+            const int t = order[i];
+            if (P.np[t] < 0 || P.leaf[t].winner != kNone) continue;
+            s_tree[k] = t;
+            k++;
+        }
+        s_n = k;
+        s_next = 0;
+        s_posted = 0;
+        s_taken = 0;
+        s_donors = (int)(blockDim.x >> 5) - R;
+    }
+    __syncthreads();
+    const int nl = s_n;
+    for (int k = (int)tid; k < nl; k += (int)blockDim.x) {
+        const int t = s_tree[k];
+        s_leaf[k] = P.leaf[t];
+        s_tid[k] = meta[t].tree_id;
+        s_it[k] = (uint32_t)meta[t].done;
+        s_wins[4 * k] = s_wins[4 * k + 1] = s_wins[4 * k + 2] = s_wins[4 * k + 3] = 0;
+    }
+    __syncthreads();
+    const uint32_t Pp = (uint32_t)sp.playouts;
+    const uint32_t total = (uint32_t)nl * Pp;
+    const uint32_t mP = Pp > 1u ? 0xFFFFFFFFu / Pp + 1u : 0u;
+    const bool receiver = (int)warp < R;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t words = 0u, wsteps = 0u;  // random words per lane, game steps per warp
+    uint32_t k = 0, steps = 0;
+    RingQueue r;
+    r.ring = s_ring + tid;
+    r.stride = blockDim.x;
+    uint32_t h0 = 0, h1 = 0, rev = 0, cur = 0, drawn = kNone, winner = kNone;
+    auto start = [&](uint32_t p) {
+        k = Pp > 1u ? __umulhi(p, mP) : p;
+        if (k * Pp > p) --k;
+        const dvc_state& ls = s_leaf[k];
+        r.open(sp.seed, s_tid[k], p - k * Pp, s_it[k], kTagRoll);
+        h0 = ls.hand[0];
+        h1 = ls.hand[1];
+        rev = ls.revealed;
+        cur = ls.cur;
+        drawn = ls.drawn;
+        winner = kNone;
+        steps = 0;
+    };
+    auto take = [&](bool want) -> uint32_t {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+        uint32_t base = 0;
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) base = (uint32_t)atomicAdd(&s_next, __popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        }
+        return base + (uint32_t)__popc(m & lt);
+    };
+    uint32_t p = take(true);
+    bool busy = p < total;
+    if (busy) start(p);
+    bool timed_out = false;
+    for (uint32_t guard = 0;; ++guard) {
+        if (guard > (1u << 24)) {  // far beyond any CTA's playouts: give up, report
+            timed_out = true;
+            break;
+        }
+        wsteps += __popc(__ballot_sync(0xFFFFFFFFu, busy));
+        bool ended = false;
+        if (busy) {
+            const int res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
+            ++steps;
+            if (res == kGameOver || steps >= 128u) {  // 128 steps: a broken invariant, checked below
+                const uint32_t w = res == kGameOver ? winner : kNone;
+                if (w < 4u) atomicAdd(&s_wins[4 * k + w], 1);
+                words += r.used();
+                ended = true;
+            }
+        }
+        if (__any_sync(0xFFFFFFFFu, ended)) {
+            const uint32_t q = take(ended);
+            if (ended) {
+                busy = q < total;
+                if (busy) start(q);
+            }
+        }
+        // shared counters are read by lane 0 and broadcast: every branch
+        // below is taken by the whole warp
+        int32_t next = 0, posted = 0, taken = 0, donors = 0;
+        if (lane == 0) {
+            // donors first: once it reads 0 every post is made, so the posted
+            // count read after it is final
+            donors = *(volatile int32_t*)&s_donors;
+            __threadfence_block();
+            next = *(volatile int32_t*)&s_next;
+            posted = *(volatile int32_t*)&s_posted;
+            taken = *(volatile int32_t*)&s_taken;
+        }
+        next = __shfl_sync(0xFFFFFFFFu, next, 0);
+        posted = __shfl_sync(0xFFFFFFFFu, posted, 0);
+        taken = __shfl_sync(0xFFFFFFFFu, taken, 0);
+        donors = __shfl_sync(0xFFFFFFFFu, donors, 0);
+        const bool pool_empty = next >= (int32_t)total;
+        const unsigned running = __ballot_sync(0xFFFFFFFFu, busy);
+        if (!receiver) {
+            if (!pool_empty) continue;
+            if (running == 0u) break;
+            if (__popc(running) > donate_at) continue;
+            // donate the running games and leave
+            const int leader = __ffs(running) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = (uint32_t)atomicAdd(&s_posted, __popc(running));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (busy) {
+                const uint32_t e = base + (uint32_t)__popc(running & lt);
+                const uint32_t v[kMailFields] = {h0, h1, rev, cur, drawn, k, steps, r.k1, r.j, r.i, r.head};
+#pragma unroll
+                for (int f = 0; f < kMailFields; ++f) mail[f * cap + e] = v[f];
+                __threadfence_block();
+                ready[e] = 1u;
+            }
+            busy = false;
+            break;
+        }
+        // receiver: idle lanes take posted games
+        if (!pool_empty) continue;
+        const unsigned idle = ~running;
+        if (posted > taken && idle) {
+            const int leader = __ffs(idle) - 1;
+            int32_t base = 0, cnt = 0;
+            if ((int)lane == leader) {
+                cnt = min(__popc(idle), posted - taken);
+                if (atomicCAS(&s_taken, taken, taken + cnt) != taken) cnt = 0;  // another warp took first
+                base = taken;
+            }
+            cnt = __shfl_sync(0xFFFFFFFFu, cnt, leader);
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            const int rank = __popc(idle & lt);
+            if (!busy && rank < cnt) {
+                const uint32_t e = (uint32_t)(base + rank);
+                uint32_t spin = 0;
+                while (ready[e] == 0u && spin < (1u << 22)) ++spin;  // the donor sets it right after writing
+                if (ready[e] == 0u) {
+                    timed_out = true;
+                } else {
+                    __threadfence_block();
+                    h0 = mail[0 * cap + e];
+                    h1 = mail[1 * cap + e];
+                    rev = mail[2 * cap + e];
+                    cur = mail[3 * cap + e];
+                    drawn = mail[4 * cap + e];
+                    k = mail[5 * cap + e];
+                    steps = mail[6 * cap + e];
+                    r.k0 = (uint32_t)sp.seed;
+                    r.tw = kTagRoll + 16u * (uint32_t)(sp.seed >> 32);
+                    r.k1 = mail[7 * cap + e];
+                    r.j = mail[8 * cap + e];
+                    r.i = mail[9 * cap + e];
+                    r.resume(mail[10 * cap + e]);
+                    winner = kNone;
+                    busy = true;
+                }
+            }
+            if (__any_sync(0xFFFFFFFFu, timed_out)) break;
+            continue;
+        }
+        if (running != 0u) continue;
+        // nothing running here: done once no donor can still post and every post is taken
+        if (donors == 0 && posted == taken) break;
+        __nanosleep(64);
+    }
+    if (timed_out && lane == 0) latch_error(P.flags, DVC_E_TIMEOUT);
+    if (!receiver) {
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            atomicSub(&s_donors, 1);
+        }
+    }
+    __syncthreads();
+    for (int e = (int)tid; e < nl; e += (int)blockDim.x) {
+        int32_t* w = P.wins + 4 * s_tree[e];
+        w[0] = s_wins[4 * e];
+        w[1] = s_wins[4 * e + 1];
+        w[2] = s_wins[4 * e + 2];
+        w[3] = s_wins[4 * e + 3];
+        if (s_wins[4 * e] + s_wins[4 * e + 1] + s_wins[4 * e + 2] + s_wins[4 * e + 3] != (int32_t)Pp)
+            latch_error(P.flags, DVC_E_INTERNAL);
+    }
+    if (words_out) {  // words_out[0]: random words, words_out[1]: game steps (guesses)
+        const unsigned long long sum = warp_sum_u64((unsigned long long)words);
+        if (lane == 0 && sum) atomicAdd(words_out, sum);
+        if (lane == 0 && wsteps) atomicAdd(words_out + 1, (unsigned long long)wsteps);
     }
 }
 
@@ -318,12 +576,6 @@ __global__ void pipe_value_wins_kernel(int t0, int t1, PipeBufs P, const float* 
     if (P.np[t] < 0 || P.leaf[t].winner != kNone) return;
     int32_t* w = P.wins + 4 * t;
     for (int s = 0; s < 4; ++s) w[s] = (int32_t)(probs[4 * t + s] * (float)playouts + 0.5f);
-}
-
-// Dynamic shared memory of pipe_rollout_kernel: the word rings and the
-// listed leaves.
-__host__ __device__ inline uint32_t pipe_rollout_smem(int L, int threads) {
-    return (uint32_t)(64 * threads + 4 * L + 16 * L + 4 * L + 4 * L + 16 + 32 * L);
 }
 
 }  // namespace dvc

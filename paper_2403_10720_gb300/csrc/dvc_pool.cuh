@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     if constexpr (FAST2) fill_select12(s_lut12, tid, blockDim.x);
     __syncthreads();
 
-    unsigned long long words = 0ull, nsteps = 0ull;
+    uint32_t words = 0u, nsteps = 0u;  // per lane; summed in 64 bits per warp at the end
     for (int iter = 0;; ++iter) {
         int32_t* cnt = s_cnt + 4 * (iter & 1);
         if (iter % kDetAhead == 0) {
@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(MAXT, 1)
         }
     }
     if (F.words) {  // F.words[0]: random words, F.words[1]: game steps (guesses)
-        const unsigned long long sum = warp_sum_u64(words);
-        const unsigned long long st = warp_sum_u64(nsteps);
+        const unsigned long long sum = warp_sum_u64((unsigned long long)words);
+        const unsigned long long st = warp_sum_u64((unsigned long long)nsteps);
         if (lane == 0 && sum) atomicAdd(F.words, sum);
         if (lane == 0 && st) atomicAdd(F.words + 1, st);
     }

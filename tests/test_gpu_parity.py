@@ -288,6 +288,43 @@ def test_uneven_workload_sampled(dvc):
     _check_forest(forest, stats, want, sample)
 
 
+def test_uneven_workload_full_budgets_sampled(dvc):
+    """The whole uneven forest -- 16,384 four-player joker trees, budgets
+    log-uniform in 1k-100k -- searched to the end of every budget under the
+    library's schedule (the autotuned pipeline shape, then the fused
+    one-tree-per-CTA engine from the iteration at which at most 12 trees per
+    SM still run), then trees replayed by the oracle at their real budgets:
+    the largest (about 100k iterations, so the largest arenas and child
+    blocks), two that end just before and just after the engine switch, and
+    three more.  Node tables and decisions bit-exact."""
+    from paper_2403_10720_gb300 import autotune
+    w = UNEVEN
+    kw = w.config_kwargs()
+    ocfg = oracle.OracleConfig(**kw)
+    ctx = _ctx(dvc, **kw)
+    n = w.n_trees
+    budgets = w.budgets(n)
+    roots = ctx.dvc_init_states(w.root_seed, n)
+    forest = dvc.Forest(ctx, roots, budgets, w.seed)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cut = autotune.tail_start(budgets, sms)
+    assert cut is not None and 0 < cut < int(budgets.max())
+    autotune.step_with_tail(forest, budgets, (2, 1, 1, 16), sms)
+    stats = forest.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    assert (stats[:, 6] == budgets).all()
+    order = np.argsort(budgets)
+    sample = [int(order[-1])]                                           # the longest budget
+    sample += [int(order[np.searchsorted(budgets[order], cut) - 1]),   # ends just before the switch
+               int(order[np.searchsorted(budgets[order], cut, side="right")])]  # just after it
+    rng = np.random.default_rng(9)
+    sample += [int(t) for t in rng.choice(n, size=3, replace=False)]
+    oroots = oracle.init_states(ocfg, w.root_seed, n)
+    want = _oracle_trees(ocfg, oroots, w.seed, budgets, sample)
+    _check_forest(forest, stats, want, sample)
+    forest.close()
+
+
 @pytest.mark.parametrize("variant,shape", [
     ("4p26j", (1, 3, 2, 0)), ("4p26j", (1, 5, 8, 0)), ("4p26j", (1, 2, 1, 0)), ("4p26j", (1, 7, 3, 0)),
     ("4p26j", (2, 3, 2, 1)), ("4p26j", (2, 5, 32, 2)), ("4p26j", (2, 1, 4, 4)), ("4p26j", (2, 2, 2, 3)),
@@ -445,3 +482,35 @@ def test_forest_work_counters_match_oracle(dvc, variant, P, budgets, extra, engi
     assert int(work[0]) == sum(w for w, _ in out.values())
     assert int(work[1]) == sum(s for _, s in out.values())
     assert (forest.dvc_forest_work().cpu().numpy() == 0).all()   # read-and-zero
+
+
+@pytest.mark.parametrize("shape,receivers,donate_at", [
+    ((2, 2, 16, 3), 4, 8), ((2, 2, 16, 3), 1, 31), ((2, 4, 8, 2), 2, 16), ((2, 11, 4, 1), 1, 4),
+    ((2, 3, 16, 4), 15, 1),
+])
+def test_lane_compaction_bit_exact(dvc, shape, receivers, donate_at):
+    """Lane compaction (running games handed between warps once a CTA's pool
+    is empty) leaves every tree, decision and work counter unchanged; trees
+    sampled against the oracle too."""
+    kw = dict(VARIANTS["2p24"], playouts=64)
+    ctx = _ctx(dvc, **kw)
+    n, budget = 700, 70
+    roots = ctx.dvc_init_states(41, n)
+    out = []
+    for comp in (False, True):
+        f = dvc.Forest(ctx, roots, [budget] * n, 12)
+        f.dvc_forest_tune(*shape)
+        if comp:
+            f.dvc_forest_compaction(receivers, donate_at)
+        f.dvc_mcts_step(budget)
+        out.append((f.dvc_root_stats().cpu().numpy(), [f.dvc_tree_export(t).cpu().numpy() for t in (0, 350, 699)],
+                    f.dvc_forest_work().cpu().numpy()))
+        f.close()
+    ctx.dvc_check()
+    (s0, t0, w0), (s1, t1, w1) = out
+    assert (s0 == s1).all() and (w0 == w1).all()
+    assert all((a == b).all() for a, b in zip(t0, t1))
+    ocfg = oracle.OracleConfig(**kw)
+    oroots = oracle.init_states(ocfg, 41, n)
+    nodes, best = oracle.mcts(ocfg, oroots[350], 12, 350, budget)
+    assert (t1[1][: len(nodes)] == nodes).all()

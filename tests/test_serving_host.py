@@ -67,7 +67,7 @@ class _Ctx:
         self.deals += n
         return s
 
-    def dvc_play_move(self, st, acts, seed, turn, ids):
+    def dvc_play_move(self, st, acts, seed, turn, ids, stream=None):
         assert (st[:, 29] == self.v).all()           # each game's moves go to its own variant
         st[:, 30] += 1
         st[st[:, 30] >= 3, 28] = 0
@@ -81,9 +81,11 @@ def test_game_serving_run_routes_moves_and_redeals():
                                    value_frac=0.5, seed=2, device="cpu")
     assert out["queries"] == len(srv.order) and out["queries"] > 0
     assert out["moves_played"] == out["queries"]
+    # every re-deal takes exactly three moves of one game; at most two moves
+    # per game are not yet followed by one
+    assert 3 * out["games_redealt"] <= out["moves_played"] <= 3 * out["games_redealt"] + 2 * 30
     assert sorted(out["by_variant"]) == ["2p24", "3p24", "4p26"]
     assert sum(v["queries"] for v in out["by_variant"].values()) == out["queries"]
     assert sum(v["queries"] for v in out["by_mode"].values()) == out["queries"]
-    # a game finishes after three moves and is dealt afresh
     if out["queries"] >= 90:
-        assert sum(c.deals for c in ctxs) > 30
+        assert out["games_redealt"] > 0
