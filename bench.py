@@ -31,6 +31,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# More hardware work queues than CUDA's default 8, before any CUDA call: the
+# serving workload runs a dozen lane streams side by side, and the pipeline
+# up to 24 chains.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
@@ -982,8 +986,8 @@ def run_serve(args):
                    "arrival_window_s": args.window, "budget_range": out["budget_range"],
                    "value_frac": out["value_frac"], "playouts_per_leaf": 32, "hbm_gb": args.hbm_gb,
                    "iterations_per_poll": args.poll_iters},
-        **{k: out[k] for k in ("queries", "wall_s", "moves_played", "p50_ms", "p99_ms", "by_mode", "by_variant",
-                               "lanes")}}), flush=True)
+        **{k: out[k] for k in ("queries", "wall_s", "moves_played", "games_redealt", "p50_ms", "p99_ms", "by_mode",
+                               "by_variant", "lanes", "polls", "host_s")}}), flush=True)
 
 
 def main():

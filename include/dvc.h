@@ -426,8 +426,11 @@ int dvc_gemm_timeout_probe(dvc_ctx* ctx, const void* d_A, const void* d_B, float
  * context each: its slots are split into lanes, one per (context, leaf mode),
  * each a forest of that variant with its own stream, so the searches of
  * different variants and modes run side by side on the GPU.  A submitted
- * root goes to the lane of its variant and mode.  The paper searches one
- * game at a time; serving many games is not part of its method.
+ * root goes to the lane of its variant and mode.  CUDA maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 by default): for the lanes
+ * of a larger server to run side by side, raise it (e.g. to 32) before the
+ * process's first CUDA call.  The paper searches one game at a time; serving
+ * many games is not part of its method.
  */
 typedef struct dvc_server dvc_server;
 typedef struct dvc_result {

@@ -151,7 +151,15 @@ struct GemmArgs {
     int32_t* flags;
     uint64_t wait_ns;  // limit of every mbarrier wait (global time)
     int starve;        // test hook: the producer issues no copy, so every consumer wait runs out
+    // Optional 4-output head folded into the epilogue (N = 512, BN = 256):
+    // head_out[row][part][o] = sum over the part's columns c of
+    // act(acc + bias)[row][c] * head_w[o][c], one part per (N tile, column
+    // group), 8 parts per row, summed in a fixed order by the consumer.
+    const __nv_bfloat16* head_w;  // 4 (or more) x N BF16, row-major; null: no head
+    float* head_out;              // M x 8 x 4 FP32
 };
+
+constexpr int kHeadParts = 8;
 
 // Stage geometry for a BN-column tile: A 128 x 64 and B BN x 64 BF16 per
 // stage, as many stages as fit in 192 KB (at most 6); two accumulator
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     __shared__ uint64_t s_full[S], s_empty[S], s_accf[2], s_acce[2], s_done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail, s_issued, s_consumed;
+    __shared__ float4 s_head[512];  // head weights per column (outputs 0..3), when a.head_w is set
     volatile int* fail = &s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntn = a.N / BN;
@@ -203,6 +212,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (a.head_w)
+        for (int c = tid; c < a.N && c < 512; c += blockDim.x)
+            s_head[c] = make_float4(__bfloat162float(a.head_w[c]), __bfloat162float(a.head_w[a.N + c]),
+                                    __bfloat162float(a.head_w[2 * a.N + c]), __bfloat162float(a.head_w[3 * a.N + c]));
     if (warp == 0) tc_alloc(&s_tmem, Cfg::kCols);
     tc_fence_before();
     __syncthreads();
@@ -288,6 +301,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int row = m0 + quarter * 32 + lane;
             const bool live = row < a.M;
             const uint32_t acc = tmem + (uint32_t)b * Cfg::kAccCols + ((uint32_t)(quarter * 32) << 16);
+            float4 head = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 1
             for (int c0 = cbeg; c0 < cbeg + cw && c0 < BN; c0 += 16) {  // cw is a multiple of 16
                 float v[16];
@@ -305,6 +319,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = gelu_erf(v[i]);
                     }
+                    if (a.head_out) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float4 hw = s_head[nb + i];
+                            head.x += v[i] * hw.x;
+                            head.y += v[i] * hw.y;
+                            head.z += v[i] * hw.z;
+                            head.w += v[i] * hw.w;
+                        }
+                    }
                     if (a.C) {
                         uint32_t w[8];
 #pragma unroll
@@ -318,6 +342,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     }
                 }
             }
+            if (a.head_out && live && group < kGroups)
+                reinterpret_cast<float4*>(a.head_out)[(size_t)row * kHeadParts + (t % ntn) * kGroups + group] = head;
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_acce[b]);

@@ -1492,6 +1492,7 @@ struct ServerLane {
     uint32_t* d_tid = nullptr;
     int32_t* d_stats = nullptr;
     int32_t* h_stats = nullptr;
+    int32_t* h_stage = nullptr;  // pinned admission staging: slots, budgets, tree ids, roots
     int resident = 0;
     cudaEvent_t begin = nullptr;  // recorded before a step's search
     cudaEvent_t done = nullptr;   // recorded after the step's statistics reach h_stats
@@ -1531,6 +1532,7 @@ void lane_free(ServerLane& L) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (L.h_stats) cudaFreeHost(L.h_stats);
+    if (L.h_stage) cudaFreeHost(L.h_stage);
     if (L.done) cudaEventDestroy(L.done);
     if (L.begin) cudaEventDestroy(L.begin);
     if (L.st) cudaStreamDestroy(L.st);
@@ -1549,7 +1551,8 @@ int lane_create(ServerLane& L, dvc_ctx* c, int ctx_index, int mode, int n, int m
         cudaMalloc(&L.d_tid, 4 * (size_t)n) != cudaSuccess ||
         cudaMalloc(&L.d_root, sizeof(dvc_state) * (size_t)n) != cudaSuccess ||
         cudaMalloc(&L.d_stats, 32 * (size_t)n) != cudaSuccess ||
-        cudaMallocHost(&L.h_stats, 32 * (size_t)n) != cudaSuccess) {
+        cudaMallocHost(&L.h_stats, 32 * (size_t)n) != cudaSuccess ||
+        cudaMallocHost(&L.h_stage, (12 + sizeof(dvc_state)) * (size_t)n) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, DVC_E_OOM, "dvc_server_create: staging buffers");
     }
@@ -1602,12 +1605,20 @@ int lane_admit(dvc_server* sv, int li) {
     L.resident += k;
     if (k == 0) return DVC_OK;
     dvc_ctx* c = L.ctx;
-    // pageable sources: each copy is staged before cudaMemcpyAsync returns
-    cudaError_t e = cudaMemcpyAsync(L.d_slot, slot.data(), 4 * k, cudaMemcpyHostToDevice, L.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_budget, budget.data(), 4 * k, cudaMemcpyHostToDevice, L.st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_tid, tid.data(), 4 * k, cudaMemcpyHostToDevice, L.st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.d_root, root.data(), sizeof(dvc_state) * k, cudaMemcpyHostToDevice, L.st);
+    // pinned staging (the lane is idle: its previous step and copies are done)
+    const size_t n = L.slots.size();
+    int32_t* hs = L.h_stage;
+    int32_t* hb = hs + n;
+    uint32_t* ht = (uint32_t*)(hb + n);
+    dvc_state* hr = (dvc_state*)(ht + n);
+    std::memcpy(hs, slot.data(), 4 * (size_t)k);
+    std::memcpy(hb, budget.data(), 4 * (size_t)k);
+    std::memcpy(ht, tid.data(), 4 * (size_t)k);
+    std::memcpy(hr, root.data(), sizeof(dvc_state) * (size_t)k);
+    cudaError_t e = cudaMemcpyAsync(L.d_slot, hs, 4 * k, cudaMemcpyHostToDevice, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_budget, hb, 4 * k, cudaMemcpyHostToDevice, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_tid, ht, 4 * k, cudaMemcpyHostToDevice, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.d_root, hr, sizeof(dvc_state) * k, cudaMemcpyHostToDevice, L.st);
     if (e != cudaSuccess) return cuda_fail(c, e, "dvc_server admit");
     forest_admit_kernel<<<(k * 32 + 127) / 128, 128, 0, L.st>>>(dev_of(L.f), k, L.d_slot, L.d_root, L.d_budget,
                                                                 L.d_tid, L.f->plans, L.f->tables, L.f->table_cap,

@@ -27,6 +27,9 @@ using namespace dvc_host;
 namespace {
 
 constexpr int VF = 640, VH = 512, VO = 16;
+// floats per row of the logit buffers: VO logits (training) or kHeadParts x 4
+// partial logits (inference with the output layer folded into layer 3)
+constexpr int kLogitFloats = kHeadParts * 4 > VO ? kHeadParts * 4 : VO;
 constexpr size_t OFF_W1 = 0, OFF_B1 = OFF_W1 + (size_t)VH * VF, OFF_W2 = OFF_B1 + VH, OFF_B2 = OFF_W2 + (size_t)VH * VH,
                  OFF_W3 = OFF_B2 + VH, OFF_B3 = OFF_W3 + (size_t)VH * VH, OFF_W4 = OFF_B3 + VH,
                  OFF_B4 = OFF_W4 + 4 * VH, NPARAM = OFF_B4 + 4;
@@ -56,7 +59,6 @@ __device__ __forceinline__ uint32_t unknown_mask(const G& g) { return g.tmask & 
 __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X,
                                                        float* Xf) {
     __shared__ uint32_t s_bits[8][VF / 32];
-    __shared__ uint8_t s_row[8][3][12];  // per warp: the opponents' rows (tile ids, 0xFF past the end)
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
     if (row >= npad) return;
@@ -77,47 +79,32 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
             if ((uint32_t)lane == g.drawn) set(7 * lane + 6);
         }
         const uint32_t U = unknown_mask(g);
-        // each lane places one (opponent, slot) of the rows, then reads its
-        // neighbours from shared memory
-        uint8_t(*rows)[12] = s_row[w];
-        for (int pair = lane; pair < 33; pair += 32) {
-            const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
-            uint32_t t = 0xFFu;
-            if (k < g.np) {
-                const uint32_t q = (g.cur + k) % g.np;
-                if (s < (uint32_t)__popc(g.hand(q))) t = seq_tile(g, q, s);
-            }
-            rows[k - 1u][s] = (uint8_t)t;
-        }
-        __syncwarp();
+        // each lane takes one (opponent, slot); numbered tiles ascend by id
+        // along a row, so the slot's face-up numbered neighbours are the
+        // nearest face-up numbered tiles below and above a threshold id: the
+        // slot's own tile, or for a joker the first numbered tile to its right
+        // (its gap counts the numbered tiles to its left)
         for (int pair = lane; pair < 33; pair += 32) {
             const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
             if (k >= g.np) continue;
             const uint32_t q = (g.cur + k) % g.np;
-            const uint32_t len = __popc(g.hand(q));
-            if (s >= len) continue;
+            const uint32_t hq = g.hand(q);
+            if (s >= (uint32_t)__popc(hq)) continue;
             const int base = 182 + (int)(((k - 1u) * 11u + s) * 13u);
-            const uint8_t* seq = rows[k - 1u];
-            const uint32_t t = seq[s];
+            const uint32_t t = seq_tile(g, q, s);
             if ((g.rev >> t) & 1u) {
                 set(base + (t < 24u ? (int)(t >> 1) : 12));
                 continue;
             }
-            int lo = -1, hi = 24;
-            for (int j = (int)s - 1; j >= 0; --j) {
-                const uint32_t u = seq[j];
-                if (((g.rev >> u) & 1u) && u < 24u) {
-                    lo = (int)u;
-                    break;
-                }
+            const uint32_t num = hq & kNumMask, R = num & g.rev;
+            uint32_t thr = t;
+            if (t >= 24u) {
+                const uint32_t jg = t == 24u ? g.jg0 : g.jg1;
+                thr = jg < (uint32_t)__popc(num) ? nth_set(num, jg) : 24u;
             }
-            for (uint32_t j = s + 1; j < len; ++j) {
-                const uint32_t u = seq[j];
-                if (((g.rev >> u) & 1u) && u < 24u) {
-                    hi = (int)u;
-                    break;
-                }
-            }
+            const uint32_t left = R & ((1u << thr) - 1u), right = R & ~((1u << thr) - 1u);
+            const int lo = left ? 31 - __clz(left) : -1;
+            const int hi = right ? __ffs(right) - 1 : 24;
             // unknown numbered tiles strictly between lo and hi, as values:
             // bit v of the 12-bit field <- tile bits 2v | 2v+1 (even bits
             // gathered by halving shifts), bit 12 <- an unknown joker; the
@@ -159,19 +146,32 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
     }
 }
 
-// Softmax over relative seats 0..P-1, written per absolute seat.
-__global__ void softmax_out_kernel(const float* L, const dvc_state* states, int n, float* out) {
+
+// Softmax over relative seats 0..P-1, written per absolute seat, of logits
+// given as 8 partial sums per row (the output layer folded into layer 3):
+// z[r] = b4[r] + parts[0][r] + ... + parts[7][r].
+__global__ void softmax_head_kernel(const float* parts, const float* b4, const dvc_state* states, int n, float* out) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n) return;
     const dvc_state& s = states[row];
     const int P = (s.nplayers >= 2 && s.nplayers <= 4) ? s.nplayers : 2;
     const int cur = s.cur < P ? s.cur : 0;
-    const float* z = L + (size_t)row * VO;
-    float mx = z[0];
-    for (int r = 1; r < P; ++r) mx = fmaxf(mx, z[r]);
+    const float4* pp = reinterpret_cast<const float4*>(parts) + (size_t)row * kHeadParts;
+    float4 z = make_float4(b4[0], b4[1], b4[2], b4[3]);
+#pragma unroll
+    for (int p = 0; p < kHeadParts; ++p) {
+        const float4 q = pp[p];
+        z.x += q.x;
+        z.y += q.y;
+        z.z += q.z;
+        z.w += q.w;
+    }
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    float mx = zz[0];
+    for (int r = 1; r < P; ++r) mx = fmaxf(mx, zz[r]);
     float e[4], sum = 0.0f;
     for (int r = 0; r < P; ++r) {
-        e[r] = expf(z[r] - mx);
+        e[r] = expf(zz[r] - mx);
         sum += e[r];
     }
     float* o = out + (size_t)row * 4;
@@ -406,12 +406,20 @@ constexpr uint64_t kGemmWaitNs = 2000000000ull;  // 2 s: far beyond any wait of 
 
 cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, __nv_bfloat16* C, float* Cf, int M,
                  int N, int K, int act, int32_t* flags, cudaStream_t st) {
-    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0};
+    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0, nullptr, nullptr};
     if (N % 256 == 0) return launch_gemm<256>(a, st);
     if (N % 128 == 0) return launch_gemm<128>(a, st);
     if (N % 64 == 0) return launch_gemm<64>(a, st);
     if (N % 32 == 0) return launch_gemm<32>(a, st);
     return launch_gemm<16>(a, st);
+}
+
+// Layer 3 with the 512 -> 4 output layer folded into its epilogue: no H3
+// written; 8 partial logit vectors per row into `parts` (rows x 8 x 4).
+cudaError_t gemm_head(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* Cf, int M,
+                      const __nv_bfloat16* W4, float* parts, int32_t* flags, cudaStream_t st) {
+    GemmArgs a{A, B, bias, nullptr, Cf, M, VH, VH, kActGelu, flags, kGemmWaitNs, 0, W4, parts};
+    return launch_gemm<256>(a, st);  // N = 512: two 256-column tiles x four column groups = kHeadParts
 }
 
 int net_alloc(dvc_ctx* c) {
@@ -458,7 +466,7 @@ int ensure_work(dvc_ctx* c, int npad) {
                     al((void**)&v->H2T, r * VH * 2) && al((void**)&v->H3T, r * VH * 2) &&
                     al((void**)&v->dZ, r * VH * 2) && al((void**)&v->dZT, r * VH * 2) && al((void**)&v->dZ4, r * 64 * 2) &&
                     al((void**)&v->dZ4T, r * VO * 2) && al((void**)&v->Z1, r * VH * 4) && al((void**)&v->Z2, r * VH * 4) &&
-                    al((void**)&v->Z3, r * VH * 4) && al((void**)&v->L, r * VO * 4) && al((void**)&v->dH, r * VH * 4) &&
+                    al((void**)&v->Z3, r * VH * 4) && al((void**)&v->L, r * kLogitFloats * 4) && al((void**)&v->dH, r * VH * 4) &&
                     al((void**)&v->dZ4f, r * VO * 4) && al((void**)&v->tmp, (size_t)VO * VH * 4) &&
                     al((void**)&v->part, ((r + 255) / 256) * (size_t)VF * 4) && al((void**)&v->loss, (r + 1) * 4);
     if (!ok) {
@@ -485,16 +493,25 @@ int need_net(dvc_ctx* c) {
 // keeps pre-activations and transposed activations for the backward pass.
 // Features and the four layers of npad rows (n live) into the given
 // activation buffers; Z1..Z3 (pre-activation FP32, training) may be null.
+// With head = true (inference) the output layer is folded into layer 3's
+// epilogue: L receives 8 partial logit vectors per row (softmax_head_kernel
+// sums them) and H3 is not written; with head = false (training) layer 4 is
+// a GEMM of its own and L holds the logits (16 columns per row).
 int forward_into(dvc_ctx* c, const dvc_state* states, int n, int npad, __nv_bfloat16* X, __nv_bfloat16* H1,
-                 __nv_bfloat16* H2, __nv_bfloat16* H3, float* L, float* Z1, float* Z2, float* Z3, cudaStream_t st) {
+                 __nv_bfloat16* H2, __nv_bfloat16* H3, float* L, float* Z1, float* Z2, float* Z3, bool head,
+                 cudaStream_t st) {
     dvc_value_net* v = c->vnet;
     int32_t* fl = c->d_flags;
     features_kernel<<<(npad * 32 + 255) / 256, 256, 0, st>>>(states, n, npad, X, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = gemm(X, v->W1, v->master + OFF_B1, H1, Z1, npad, VH, VF, kActGelu, fl, st);
     if (e == cudaSuccess) e = gemm(H1, v->W2, v->master + OFF_B2, H2, Z2, npad, VH, VH, kActGelu, fl, st);
-    if (e == cudaSuccess) e = gemm(H2, v->W3, v->master + OFF_B3, H3, Z3, npad, VH, VH, kActGelu, fl, st);
-    if (e == cudaSuccess) e = gemm(H3, v->W4, v->b4p, nullptr, L, npad, VO, VH, kActNone, fl, st);
+    if (head) {
+        if (e == cudaSuccess) e = gemm_head(H2, v->W3, v->master + OFF_B3, Z3, npad, v->W4, L, fl, st);
+    } else {
+        if (e == cudaSuccess) e = gemm(H2, v->W3, v->master + OFF_B3, H3, Z3, npad, VH, VH, kActGelu, fl, st);
+        if (e == cudaSuccess) e = gemm(H3, v->W4, v->b4p, nullptr, L, npad, VO, VH, kActNone, fl, st);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "value forward");
     return DVC_OK;
 }
@@ -502,7 +519,7 @@ int forward_into(dvc_ctx* c, const dvc_state* states, int n, int npad, __nv_bflo
 int forward(dvc_ctx* c, const dvc_state* states, int n, int npad, bool train, cudaStream_t st) {
     dvc_value_net* v = c->vnet;
     return forward_into(c, states, n, npad, v->X, v->H1, v->H2, v->H3, v->L, train ? v->Z1 : nullptr,
-                        train ? v->Z2 : nullptr, train ? v->Z3 : nullptr, st);
+                        train ? v->Z2 : nullptr, train ? v->Z3 : nullptr, !train, st);
 }
 
 int transpose(dvc_ctx* c, const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C, cudaStream_t st) {
@@ -582,8 +599,8 @@ int dvc_value_eval(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_winpro
     if (int rc = ensure_work(c, npad)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
-    softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, d_leaves, n, d_winprob);
-    return check_launch(c, "softmax_out_kernel");
+    softmax_head_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, c->vnet->b4p, d_leaves, n, d_winprob);
+    return check_launch(c, "softmax_head_kernel");
 }
 
 int dvc_value_train_step(dvc_ctx* c, const dvc_state* d_states, const float* d_labels, int n, float lr, float* d_loss,
@@ -717,7 +734,7 @@ int dvc_gemm_timeout_probe(dvc_ctx* c, const void* d_A, const void* d_B, float* 
         return fail(c, DVC_E_INVALID, "dvc_gemm_timeout_probe: device pointers");
     if (int rc = set_device(c)) return rc;
     GemmArgs a{(const __nv_bfloat16*)d_A, (const __nv_bfloat16*)d_B, nullptr, nullptr, d_Cf, M, N, K, kActNone,
-               c->d_flags, (uint64_t)wait_ms * 1000000ull, 1};
+               c->d_flags, (uint64_t)wait_ms * 1000000ull, 1, nullptr, nullptr};
     cudaError_t e;
     if (N % 256 == 0) e = launch_gemm<256>(a, (cudaStream_t)stream);
     else if (N % 128 == 0) e = launch_gemm<128>(a, (cudaStream_t)stream);
@@ -748,8 +765,8 @@ int dvc_value_forward_probs(dvc_ctx* c, const dvc_state* d_leaves, int n, float*
     const int npad = (n + 127) / 128 * 128;
     if (int rc = ensure_work(c, npad)) return rc;
     if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
-    softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, d_leaves, n, d_probs);
-    return check_launch(c, "softmax_out_kernel");
+    softmax_head_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, c->vnet->b4p, d_leaves, n, d_probs);
+    return check_launch(c, "softmax_head_kernel");
 }
 
 int dvc_value_rows_alloc(dvc_ctx* c, dvc_value_rows* r, int rows) {
@@ -757,7 +774,7 @@ int dvc_value_rows_alloc(dvc_ctx* c, dvc_value_rows* r, int rows) {
     const size_t n = (size_t)rows;
     const bool ok = cudaMalloc(&r->X, n * VF * 2) == cudaSuccess && cudaMalloc(&r->H1, n * VH * 2) == cudaSuccess &&
                     cudaMalloc(&r->H2, n * VH * 2) == cudaSuccess && cudaMalloc(&r->H3, n * VH * 2) == cudaSuccess &&
-                    cudaMalloc(&r->L, n * VO * 4) == cudaSuccess;
+                    cudaMalloc(&r->L, n * kLogitFloats * 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         dvc_value_rows_free(r);
@@ -790,13 +807,13 @@ int dvc_value_forward_rows(dvc_ctx* c, const dvc_state* d_leaves, int n, dvc_val
     const int npad = (n + 127) / 128 * 128;
     if (row0 < 0 || row0 + npad > r->rows) return fail(c, DVC_E_INVALID, "value network: activation rows");
     const size_t o = (size_t)row0;
-    float* L = r->L + o * VO;
+    float* L = r->L + o * kLogitFloats;
     if (int rc = forward_into(c, d_leaves, n, npad, (__nv_bfloat16*)r->X + o * VF, (__nv_bfloat16*)r->H1 + o * VH,
                               (__nv_bfloat16*)r->H2 + o * VH, (__nv_bfloat16*)r->H3 + o * VH, L, nullptr, nullptr,
-                              nullptr, st))
+                              nullptr, true, st))
         return rc;
-    softmax_out_kernel<<<(n + 127) / 128, 128, 0, st>>>(L, d_leaves, n, d_probs);
-    return check_launch(c, "softmax_out_kernel");
+    softmax_head_kernel<<<(n + 127) / 128, 128, 0, st>>>(L, c->vnet->b4p, d_leaves, n, d_probs);
+    return check_launch(c, "softmax_head_kernel");
 }
 
 void dvc_value_free(dvc_ctx* c) {

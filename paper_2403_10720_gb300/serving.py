@@ -136,10 +136,12 @@ def game_serving_run(server, ctxs, n_games, rate, duration_s, budget_lo=1000, bu
     polls = 0
     moves = 0
     redeals = 0
+    t_poll = t_move = t_submit = 0.0
     while True:
         now = time.perf_counter() - t0
         if now > max_seconds:
             raise TimeoutError(f"{len(lat)} queries done after {max_seconds} s")
+        ts = time.perf_counter()
         while next_arrival <= min(now, duration_s) and idle:
             k = int(rng.integers(0, len(idle)))
             g = idle[k]
@@ -152,9 +154,13 @@ def game_serving_run(server, ctxs, n_games, rate, duration_s, budget_lo=1000, bu
             busy[g] = True
             qid += 1
             next_arrival += rng.exponential(1.0 / rate)
+        tp = time.perf_counter()
+        t_submit += tp - ts
         if now >= duration_s and not busy.any():
             break
         done = server.dvc_server_poll(iterations_per_poll) if info else []
+        tm = time.perf_counter()
+        t_poll += tm - tp
         polls += 1
         by_variant = {}
         for r in done:
@@ -177,6 +183,7 @@ def game_serving_run(server, ctxs, n_games, rate, duration_s, budget_lo=1000, bu
             moves += len(gs)
             busy[gs] = False
             idle.extend(int(g) for g in gs)
+        t_move += time.perf_counter() - tm
         if not done and not info and now < duration_s:
             time.sleep(max(0.0, min(next_arrival - (time.perf_counter() - t0), 0.002)))
     wall = time.perf_counter() - t0
@@ -194,6 +201,7 @@ def game_serving_run(server, ctxs, n_games, rate, duration_s, budget_lo=1000, bu
         "moves_played": moves,
         "games_redealt": redeals,
         "polls": polls,
+        "host_s": {"poll": t_poll, "moves": t_move, "submit": t_submit},
         "p50_ms": _pct(lat_s, 50),
         "p99_ms": _pct(lat_s, 99),
         "by_mode": {},

@@ -102,7 +102,12 @@ def test_gradient_matches_oracle(dvc):
             512 * 643 + 2 * 512 * 512, 512 * 647 + 2 * 512 * 512, 855556]
     for a, b in zip(offs, offs[1:]):
         rel = np.linalg.norm(g[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-12)
-        assert rel < 5e-2, (a, b, rel)
+        # each gradient element sums products of BF16-rounded factors (relative
+        # 2^-9 each); the first layer's passes through up to six such
+        # roundings (activations, transposes, dZ of three GELU layers), so
+        # sqrt(6) x 2^-9 = 4.8e-3 relative; measured 2.7e-3 to 4.5e-3 on three
+        # seeds; the bound is three times the estimate
+        assert rel < 1.5e-2, (a, b, rel)
 
 
 def _read_checkpoint(path):
