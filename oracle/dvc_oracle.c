@@ -1197,7 +1197,7 @@ int or_mcts_value(const or_config* cfg, const uint8_t* root_packed, uint64_t see
  *              fits between the slot's face-up numbered neighbours, plus the
  *              joker if an unknown joker exists;
  *   [611, 640) zero padding.
- * Network: 640 -> 512 -> 512 -> 512 (GELU, exact erf) -> 4 logits over
+ * Network: 640 -> 512 -> 512 -> 512 (GELU, tanh form) -> 4 logits over
  * relative seats; softmax over the seats in play; output per absolute seat.
  * Parameter layout (floats): W1[512][640], b1[512], W2[512][512], b2[512],
  * W3[512][512], b3[512], W4[4][512], b4[4].  Computed in double. */
@@ -1248,9 +1248,17 @@ int or_value_features(const uint8_t* packed, float* out) {
     return 0;
 }
 
-static double gelu_d(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+/* GELU in its tanh form (Hendrycks and Gimpel, 2016):
+ * 0.5 x (1 + tanh(u)), u = sqrt(2/pi) (x + 0.044715 x^3), and its derivative
+ * 0.5 (1 + t) + 0.5 x (1 - t^2) sqrt(2/pi) (1 + 3 * 0.044715 x^2), t = tanh(u). */
+static double gelu_d(double x) {
+    const double k = sqrt(2.0 / 3.14159265358979323846);
+    return 0.5 * x * (1.0 + tanh(k * (x + 0.044715 * x * x * x)));
+}
 static double gelu_grad_d(double x) {
-    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * 3.14159265358979323846);
+    const double k = sqrt(2.0 / 3.14159265358979323846);
+    const double t = tanh(k * (x + 0.044715 * x * x * x));
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * k * (1.0 + 3.0 * 0.044715 * x * x);
 }
 
 typedef struct {

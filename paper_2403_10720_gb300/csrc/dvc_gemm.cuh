@@ -138,7 +138,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU in its tanh form (Hendrycks and Gimpel, "Gaussian Error Linear Units",
+// 2016): 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), with the hardware
+// tanh (tanh.approx.f32).
+__device__ __forceinline__ float tanh_hw(float u) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    return t;
+}
+__device__ __forceinline__ float gelu(float x) {
+    return 0.5f * x * (1.0f + tanh_hw(0.79788456080286536f * (x + 0.044715f * x * x * x)));
+}
 
 struct GemmArgs {
     const __nv_bfloat16* A;  // M x K
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     }
                     if (a.act == kActGelu) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) v[i] = gelu_erf(v[i]);
+                        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
                     }
                     if (a.head_out) {
 #pragma unroll

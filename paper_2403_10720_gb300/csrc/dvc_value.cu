@@ -224,8 +224,12 @@ __global__ void transpose_bf16_kernel(const __nv_bfloat16* in, __nv_bfloat16* ou
         out[(size_t)(c0 + i) * R + r0 + threadIdx.x] = tile[threadIdx.x][i];
 }
 
+// Derivative of the tanh-form GELU (dvc_gemm.cuh): with u = k (z + a z^3),
+// t = tanh(u): 0.5 (1 + t) + 0.5 z (1 - t^2) k (1 + 3 a z^2).
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    const float k = 0.79788456080286536f, a = 0.044715f;
+    const float t = tanh_hw(k * (z + a * z * z * z));
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * a * z * z);
 }
 
 // dZ = dH * GELU'(Z): FP32 in place in dH, BF16 copy in dZ.

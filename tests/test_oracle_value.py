@@ -80,10 +80,12 @@ def test_forward_closed_form_and_seat_mapping():
     assert got[2] == pytest.approx(soft[1], rel=1e-12)
     assert got[0] == pytest.approx(soft[2], rel=1e-12)
     assert got[3] == 0.0
-    # W4 row 0 = 1: logit 0 gains 512 * GELU(0.7)
+    # W4 row 0 = 1: logit 0 gains 512 * GELU(0.7), GELU in its tanh form,
+    # which stays within 1e-3 of the exact 0.5 x (1 + erf(x / sqrt 2))
     p[OFF_W4:OFF_W4 + VH] = 1.0
     c = float(np.float32(0.7))
-    g07 = 0.5 * c * (1 + math.erf(c / math.sqrt(2)))
+    g07 = 0.5 * c * (1 + math.tanh(math.sqrt(2 / math.pi) * (c + 0.044715 * c ** 3)))
+    assert abs(g07 - 0.5 * c * (1 + math.erf(c / math.sqrt(2)))) < 1e-3
     z = b4 + np.array([VH * g07, 0.0, 0.0])
     e = np.exp(z - z.max())
     assert oracle.value_forward(p, s)[1] == pytest.approx(e[0] / e.sum(), rel=1e-9)
