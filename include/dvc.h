@@ -394,7 +394,8 @@ int dvc_value_load(dvc_ctx* ctx, const char* path);
 /* The tensor-core GEMM used by the network: C = act(A B^T + bias), A M x K and
  * B N x K row-major BF16, bias N FP32 (optional), C M x N BF16 (optional),
  * Cf M x N FP32 before the activation (optional); N % 16 == 0, K % 64 == 0;
- * act 0 none, 1 GELU. */
+ * act 0 none, 1 GELU (tanh form); all pointers 16-byte aligned
+ * (DVC_E_INVALID otherwise). */
 int dvc_gemm_bf16(dvc_ctx* ctx, const void* d_A, const void* d_B, const float* d_bias, void* d_C, float* d_Cf, int M,
                   int N, int K, int act, void* stream);
 /* Test hook of the GEMM's failure path (not part of the method): the same

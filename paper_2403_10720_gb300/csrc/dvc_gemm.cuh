@@ -167,7 +167,15 @@ struct GemmArgs {
     // group), 8 parts per row, summed in a fixed order by the consumer.
     const __nv_bfloat16* head_w;  // 4 (or more) x N BF16, row-major; null: no head
     float* head_out;              // M x 8 x 4 FP32
+    int wide;  // C and Cf 32-byte aligned: 256-bit stores (half the store instructions)
 };
+
+// 32 bytes to global memory in one instruction (p 32-byte aligned).
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t* w) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
 
 constexpr int kHeadParts = 8;
 
@@ -321,9 +329,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += a.bias ? __ldg(a.bias + nb + i) : 0.0f;
                     if (a.Cf) {
-                        float4* f = reinterpret_cast<float4*>(a.Cf + (size_t)row * a.N + nb);
+                        float* cf = a.Cf + (size_t)row * a.N + nb;
+                        if (a.wide) {
+                            st_global_v8(cf, reinterpret_cast<const uint32_t*>(v));
+                            st_global_v8(cf + 8, reinterpret_cast<const uint32_t*>(v + 8));
+                        } else {
+                            float4* f = reinterpret_cast<float4*>(cf);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) f[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                            for (int i = 0; i < 4; ++i)
+                                f[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        }
                     }
                     if (a.act == kActGelu) {
 #pragma unroll
@@ -346,9 +361,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                             __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
                             w[i] = *reinterpret_cast<uint32_t*>(&p);
                         }
-                        uint4* dst = reinterpret_cast<uint4*>(a.C + (size_t)row * a.N + nb);
-                        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        if (a.wide) {
+                            st_global_v8(a.C + (size_t)row * a.N + nb, w);
+                        } else {
+                            uint4* dst = reinterpret_cast<uint4*>(a.C + (size_t)row * a.N + nb);
+                            dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
                     }
                 }
             }

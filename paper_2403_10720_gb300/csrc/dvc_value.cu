@@ -410,7 +410,8 @@ constexpr uint64_t kGemmWaitNs = 2000000000ull;  // 2 s: far beyond any wait of 
 
 cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, __nv_bfloat16* C, float* Cf, int M,
                  int N, int K, int act, int32_t* flags, cudaStream_t st) {
-    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0, nullptr, nullptr};
+    const int wide = ((uintptr_t)C % 32 == 0 && (uintptr_t)Cf % 32 == 0) ? 1 : 0;  // null counts as aligned
+    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0, nullptr, nullptr, wide};
     if (N % 256 == 0) return launch_gemm<256>(a, st);
     if (N % 128 == 0) return launch_gemm<128>(a, st);
     if (N % 64 == 0) return launch_gemm<64>(a, st);
@@ -422,7 +423,7 @@ cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bi
 // written; 8 partial logit vectors per row into `parts` (rows x 8 x 4).
 cudaError_t gemm_head(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* Cf, int M,
                       const __nv_bfloat16* W4, float* parts, int32_t* flags, cudaStream_t st) {
-    GemmArgs a{A, B, bias, nullptr, Cf, M, VH, VH, kActGelu, flags, kGemmWaitNs, 0, W4, parts};
+    GemmArgs a{A, B, bias, nullptr, Cf, M, VH, VH, kActGelu, flags, kGemmWaitNs, 0, W4, parts, (uintptr_t)Cf % 32 == 0};
     return launch_gemm<256>(a, st);  // N = 512: two 256-column tiles x four column groups = kHeadParts
 }
 
@@ -738,7 +739,7 @@ int dvc_gemm_timeout_probe(dvc_ctx* c, const void* d_A, const void* d_B, float* 
         return fail(c, DVC_E_INVALID, "dvc_gemm_timeout_probe: device pointers");
     if (int rc = set_device(c)) return rc;
     GemmArgs a{(const __nv_bfloat16*)d_A, (const __nv_bfloat16*)d_B, nullptr, nullptr, d_Cf, M, N, K, kActNone,
-               c->d_flags, (uint64_t)wait_ms * 1000000ull, 1, nullptr, nullptr};
+               c->d_flags, (uint64_t)wait_ms * 1000000ull, 1, nullptr, nullptr, 0};
     cudaError_t e;
     if (N % 256 == 0) e = launch_gemm<256>(a, (cudaStream_t)stream);
     else if (N % 128 == 0) e = launch_gemm<128>(a, (cudaStream_t)stream);
@@ -756,6 +757,8 @@ int dvc_gemm_bf16(dvc_ctx* c, const void* d_A, const void* d_B, const float* d_b
     if (!is_device_ptr(d_A, c->device) || !is_device_ptr(d_B, c->device) || (d_bias && !is_device_ptr(d_bias, c->device)) ||
         (d_C && !is_device_ptr(d_C, c->device)) || (d_Cf && !is_device_ptr(d_Cf, c->device)) || (!d_C && !d_Cf))
         return fail(c, DVC_E_INVALID, "dvc_gemm_bf16: device pointers, at least one output");
+    if ((uintptr_t)d_C % 16 || (uintptr_t)d_Cf % 16 || (uintptr_t)d_A % 16 || (uintptr_t)d_B % 16)
+        return fail(c, DVC_E_INVALID, "dvc_gemm_bf16: A, B, C and Cf must be 16-byte aligned");
     if (int rc = set_device(c)) return rc;
     const cudaError_t e = gemm((const __nv_bfloat16*)d_A, (const __nv_bfloat16*)d_B, d_bias, (__nv_bfloat16*)d_C, d_Cf,
                                M, N, K, act, c->d_flags, (cudaStream_t)stream);

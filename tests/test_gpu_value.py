@@ -50,6 +50,32 @@ def test_tensor_core_gemm(dvc, M, N, K):
         assert torch.allclose(C.cpu().double(), post, rtol=1e-2, atol=1e-2)
 
 
+def test_gemm_output_alignment(dvc):
+    """Outputs 32-byte aligned take 256-bit stores, 16-byte aligned ones
+    16-byte stores: same results; an 8-byte offset is refused on the host."""
+    import ctypes
+    ctx = dvc.Context(dvc.Config(), 0)
+    g = torch.Generator().manual_seed(11)
+    M, N, K = 300, 64, 128
+    A = torch.randn((M, K), generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn((N, K), generator=g).to(torch.bfloat16).cuda()
+    bias = torch.randn(N, generator=g).cuda()
+    C0, F0 = ctx.dvc_gemm_bf16(A, B, bias, act=1)
+    cbuf = torch.zeros(M * N + 16, dtype=torch.bfloat16, device="cuda")
+    fbuf = torch.zeros(M * N + 8, dtype=torch.float32, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = dvc.lib().dvc_gemm_bf16(ctx.h, A.data_ptr(), B.data_ptr(), bias.data_ptr(), cbuf.data_ptr() + 16,
+                                 fbuf.data_ptr() + 16, M, N, K, 1, st)
+    assert rc == 0
+    torch.cuda.synchronize()
+    ctx.dvc_check()
+    assert torch.equal(cbuf[8:8 + M * N].view(M, N), C0)
+    assert torch.equal(fbuf[4:4 + M * N].view(M, N), F0)
+    rc = dvc.lib().dvc_gemm_bf16(ctx.h, A.data_ptr(), B.data_ptr(), bias.data_ptr(), cbuf.data_ptr() + 8,
+                                 None, M, N, K, 1, st)
+    assert rc == -1
+
+
 @pytest.mark.parametrize("variant", sorted(VARIANTS))
 def test_features_exact(dvc, variant):
     kw = VARIANTS[variant]
