@@ -302,6 +302,22 @@ int dvc_forest_leaves(dvc_forest* f, dvc_state** d_leaves, uint32_t** d_tree_ids
  */
 int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream);
 
+/*
+ * Root-parallel merge (Sec. III-B: independent searches of one position
+ * whose root statistics are summed, the paper's "amalgamated" trees).  The
+ * forest's trees form n / K groups of K consecutive trees; the trees of a
+ * group must share their root (their streams differ through their tree ids;
+ * a group whose roots differ latches DVC_E_INVALID).  Per group, 8 int32:
+ * the action with the most visits summed over the group (for vanilla trees
+ * summed over every plausible set as well), ties to the lowest canonical
+ * action (-1 if none); its summed visits; its summed wins (the searching
+ * seat's); the summed root visits; the number of distinct root actions; K;
+ * the summed iterations done; 1 if any tree failed.  d_out: n / K x 8
+ * int32.  DVC_E_INVALID unless K divides the number of trees;
+ * DVC_E_UNSUPPORTED if K x budget x playouts could exceed 2^31.
+ */
+int dvc_root_merge(dvc_forest* f, int K, int32_t* d_out, void* stream);
+
 /* Work counters of the forest since creation or the last call: d_out[0] =
  * random words consumed by its playouts (each word is one uniform choice of
  * the method: a draw, a joker position, a guess or a continue coin).  Copies

@@ -40,6 +40,9 @@ Pin status per function:
   value_features .... pinned (hand-made positions with features written out)
   value_forward ..... pinned (closed form with zero hidden weights)
   value_loss_grad ... pinned (central finite differences in double)
+  root_merge ........ pinned (one table reproduces or_mcts's own decision,
+                      plain and vanilla; hand-made tables: sums that change
+                      the winner, a tie to the lowest canonical rank)
   adamw_step ........ pinned (closed forms of the definition: the first step
                       from zero moments, a constant gradient over many steps,
                       weight decay on matrices only)
@@ -148,6 +151,8 @@ def lib():
         L.or_adamw_step.argtypes = [f64p, f64p, f64p, f64p, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.or_adamw_step.restype = ctypes.c_int
+        L.or_root_merge.argtypes = [u8p, ctypes.c_int, i32p, i32p, ctypes.c_int, i32p]
+        L.or_root_merge.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -338,3 +343,16 @@ def mcts_work(cfg: OracleConfig, root, seed: int, tree: int, budget: int):
     if rc:
         raise ValueError(f"or_mcts_work rc={rc}")
     return int(out[0]), int(out[1])
+
+
+def root_merge(root, tables, vanilla: int = 0):
+    """Root-parallel merge (Sec. III-B) of K node tables of searches of one
+    root: [action, visits, wins, root visits] of the summed decision."""
+    s = _state(root)
+    counts = np.array([len(t) for t in tables], dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.int32).reshape(-1, 4) for t in tables]))
+    out = np.zeros(4, dtype=np.int32)
+    rc = lib().or_root_merge(_u8(s), len(tables), _i32(flat), _i32(counts), int(vanilla), _i32(out))
+    if rc:
+        raise ValueError("or_root_merge")
+    return out

@@ -1408,3 +1408,47 @@ int or_adamw_step(double* w, double* m, double* v, const double* g, long long t,
     }
     return 0;
 }
+
+/* Root-parallel merge (Sec. III-B): the decision of K searches of one root,
+ * given their node tables (rows [action, parent, visits, wins] in creation
+ * order, row 0 the root), concatenated, counts[k] rows each.  Each action's
+ * root-child visits and wins are summed over the K tables (vanilla: the
+ * children of every plausible-set node, the root's children there); the
+ * decision is the action with most visits, ties to the lowest canonical rank.
+ * out[4]: action (-1 if none), its visits, its wins, the summed root visits. */
+int or_root_merge(const uint8_t* root_packed, int K, const int32_t* tables, const int32_t* counts, int vanilla,
+                  int32_t* out) {
+    ost root;
+    unpack(root_packed, &root);
+    static _Thread_local int32_t av[4096], aw[4096];
+    memset(av, 0, sizeof(av));
+    memset(aw, 0, sizeof(aw));
+    int32_t root_visits = 0;
+    const int32_t* t = tables;
+    for (int k = 0; k < K; k++) {
+        const int n = counts[k];
+        if (n < 1) return -1;
+        root_visits += t[2];
+        for (int i = 1; i < n; i++) {
+            const int32_t action = t[4 * i], parent = t[4 * i + 1];
+            const int counted = vanilla ? (parent > 0 && t[4 * parent + 1] == 0) : parent == 0;
+            if (!counted) continue;
+            if (action < 0 || action >= 4096) return -1;
+            av[action] += t[4 * i + 2];
+            aw[action] += t[4 * i + 3];
+        }
+        t += 4 * n;
+    }
+    int best = -1;
+    for (int a = 0; a < 4096; a++) {
+        if (av[a] == 0) continue;
+        if (best < 0 || av[a] > av[best] ||
+            (av[a] == av[best] && canon_rank(a, root.cur, root.P) < canon_rank(best, root.cur, root.P)))
+            best = a;
+    }
+    out[0] = best;
+    out[1] = best < 0 ? 0 : av[best];
+    out[2] = best < 0 ? 0 : aw[best];
+    out[3] = root_visits;
+    return 0;
+}

@@ -119,6 +119,7 @@ def lib():
             "dvc_root_stats": ([vp, vp, vp], i),
             "dvc_forest_counters": ([vp, vp, vp], i),
             "dvc_forest_work": ([vp, vp, vp], i),
+            "dvc_root_merge": ([vp, i, vp, vp], i),
             "dvc_forest_compaction": ([vp, i, i], i),
             "dvc_tree_export": ([vp, i, vp, vp], i),
             "dvc_philox": ([vp, i, vp, vp, vp, i, vp], i),
@@ -354,6 +355,12 @@ class Forest:
 
     def dvc_forest_compaction(self, receivers, donate_at=8):
         self.ctx._rc(lib().dvc_forest_compaction(self.h, receivers, donate_at), "dvc_forest_compaction")
+
+    def dvc_root_merge(self, K, out=None, stream=None):
+        """Root-parallel merge over groups of K consecutive trees: (n / K, 8) int32."""
+        out = torch.empty((self.n // K, 8), dtype=torch.int32, device=self.ctx.dev()) if out is None else out
+        self.ctx._rc(lib().dvc_root_merge(self.h, K, _ptr(out), _stream(stream)), "dvc_root_merge")
+        return out
 
     def dvc_forest_work(self, out=None, stream=None):
         """(random words, game steps) of the forest's playouts since the last call."""

@@ -456,6 +456,90 @@ __global__ void __launch_bounds__(256) root_stats_vanilla_kernel(ForestDev F, in
 // iteration that created them; at most one node is created per iteration, so
 // a node's row is 1 + the number of iterations before its own that created a
 // node.  iter_rank holds one int per iteration of the tree's budget.
+// Root-parallel merge (Sec. III-B): group g is trees g*K .. g*K+K-1, all
+// searched from one root with their own streams; each action's root visits
+// and wins are summed over the group's trees (for vanilla trees over every
+// plausible set of each tree too) and the decision is the action with most
+// visits, ties to the lowest canonical rank.  One CTA per group.
+__global__ void __launch_bounds__(256) root_merge_kernel(ForestDev F, int K, int groups, int vanilla, int32_t* out) {
+    __shared__ int32_t s_v[4096], s_w[4096];
+    __shared__ unsigned long long s_best;
+    __shared__ int32_t s_tot[4];  // root visits, iterations done, failed, distinct actions
+    const int g = blockIdx.x;
+    if (g >= groups) return;
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t a = tid; a < 4096u; a += blockDim.x) s_v[a] = s_w[a] = 0;
+    if (tid < 4) s_tot[tid] = 0;
+    if (tid == 0) s_best = 0ull;
+    __syncthreads();
+    const dvc_state r0 = F.roots[g * K];
+    for (int k = 0; k < K; ++k) {
+        const int t = g * K + k;
+        const TreeMeta tm = F.meta[t];
+        const Node* nodes = F.nodes + tm.node_off;
+        const int32_t* link = F.link + tm.node_off;
+        const Node r = nodes[0];
+        if (tid == 0) {
+            const dvc_state rt = F.roots[t];
+            bool same = true;
+            for (int i = 0; i < 8; ++i)
+                same &= reinterpret_cast<const uint32_t*>(&rt)[i] == reinterpret_cast<const uint32_t*>(&r0)[i];
+            if (!same) latch(F.flags, DVC_E_INVALID);  // a group must share its root
+            s_tot[0] += r.visits;
+            s_tot[1] += tm.done;
+            s_tot[2] |= tm.failed;
+        }
+        // the nodes whose children are summed: the root, or every set node of a vanilla root
+        const uint32_t nparents = vanilla ? (r.meta >> 12) : 1u;
+        for (uint32_t pi = 0; pi < nparents; ++pi) {
+            const Node pn = vanilla ? nodes[r.child + (int32_t)pi] : r;
+            const uint32_t nchild = pn.meta >> 12;
+            int32_t blk = pn.child;
+            uint32_t seen = 0, kb = 0;
+            while (seen < nchild) {
+                const uint32_t size = block_size(kb, !vanilla, (uint32_t)tm.root_legal);
+                const uint32_t cnt = min(size, nchild - seen);
+                for (uint32_t e = tid; e < cnt; e += blockDim.x) {
+                    const Node c = nodes[blk + (int32_t)e];
+                    const uint32_t code = c.meta & 0xFFFu;
+                    atomicAdd(&s_v[code], c.visits);
+                    atomicAdd(&s_w[code], c.wins);
+                }
+                seen += cnt;
+                ++kb;
+                if (seen < nchild) blk = link[blk];
+            }
+        }
+    }
+    __syncthreads();
+    const G root = load_state(r0);
+    unsigned long long best = 0ull;
+    int32_t distinct = 0;
+    for (uint32_t a = tid; a < 4096u; a += blockDim.x) {
+        if (s_v[a] <= 0) continue;
+        ++distinct;
+        const unsigned long long key = (unsigned long long)(uint32_t)s_v[a] << 32 |
+                                       (unsigned long long)(0x1FFFu - canon_rank(a, root.cur, root.np)) << 12 | a;
+        best = key > best ? key : best;
+    }
+    if (best) atomicMax(&s_best, best);
+    if (distinct) atomicAdd(&s_tot[3], distinct);
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned long long b = s_best;
+        const int32_t code = b ? (int32_t)(b & 0xFFFu) : -1;
+        int32_t* o = out + 8 * g;
+        o[0] = code;
+        o[1] = b ? s_v[code] : 0;
+        o[2] = b ? s_w[code] : 0;
+        o[3] = s_tot[0];
+        o[4] = s_tot[3];
+        o[5] = K;
+        o[6] = s_tot[1];
+        o[7] = s_tot[2];
+    }
+}
+
 __global__ void export_flag_kernel(ForestDev F, int t, int32_t* iter_rank) {
     const TreeMeta tm = F.meta[t];
     const int32_t* created = F.created + tm.node_off;
@@ -1421,6 +1505,20 @@ int dvc_root_stats(dvc_forest* f, int32_t* d_out, void* stream) {
     }
     root_stats_kernel<<<(f->n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(dev_of(f), f->n, d_out);
     return check_launch(f->ctx, "root_stats_kernel");
+}
+
+int dvc_root_merge(dvc_forest* f, int K, int32_t* d_out, void* stream) {
+    if (!f) return DVC_E_INVALID;
+    if (K < 1 || f->n % K) return fail(f->ctx, DVC_E_INVALID, "dvc_root_merge: K must divide the number of trees");
+    long long maxb = 0;
+    for (int t = 0; t < f->n; ++t) maxb = std::max<long long>(maxb, f->h_budgets[t]);
+    if ((long long)K * maxb * f->ctx->cfg.playouts >= (1LL << 31))
+        return fail(f->ctx, DVC_E_UNSUPPORTED, "dvc_root_merge: K x budget x playouts must stay below 2^31");
+    if (!is_device_ptr(d_out, f->ctx->device)) return fail(f->ctx, DVC_E_INVALID, "dvc_root_merge: d_out must be device memory");
+    if (int rc = set_device(f->ctx)) return rc;
+    root_merge_kernel<<<f->n / K, 256, 0, (cudaStream_t)stream>>>(dev_of(f), K, f->n / K, f->ctx->cfg.vanilla ? 1 : 0,
+                                                                   d_out);
+    return check_launch(f->ctx, "root_merge_kernel");
 }
 
 int dvc_tree_export(dvc_forest* f, int tree, int32_t* d_out, void* stream) {

@@ -514,3 +514,45 @@ def test_lane_compaction_bit_exact(dvc, shape, receivers, donate_at):
     oroots = oracle.init_states(ocfg, 41, n)
     nodes, best = oracle.mcts(ocfg, oroots[350], 12, 350, budget)
     assert (t1[1][: len(nodes)] == nodes).all()
+
+
+@pytest.mark.parametrize("variant,P,K,groups,extra,engine", [
+    ("2p24", 32, 4, 3, {}, 1),
+    ("4p26j", 16, 3, 2, {}, 2),
+    ("2p24", 16, 5, 2, dict(vanilla=1), 1),
+])
+def test_root_parallel_merge_bit_exact(dvc, variant, P, K, groups, extra, engine):
+    """Root-parallel merge (Sec. III-B): groups of K trees searched from one
+    root with their own streams; the summed decision equals the oracle's
+    merge of the K oracle trees."""
+    kw = dict(VARIANTS[variant], playouts=P, **extra)
+    ocfg = oracle.OracleConfig(**kw)
+    ctx = _ctx(dvc, **kw)
+    base = ctx.dvc_init_states(17, groups)
+    obase = oracle.init_states(ocfg, 17, groups)
+    roots = base.repeat_interleave(K, dim=0).contiguous()
+    budgets = [60 + 7 * t for t in range(groups * K)]
+    forest = dvc.Forest(ctx, roots, budgets, 5)
+    forest.dvc_forest_tune(engine)
+    forest.dvc_mcts_step(max(budgets))
+    got = forest.dvc_root_merge(K).cpu().numpy()
+    ctx.dvc_check()
+    for g in range(groups):
+        tables = [oracle.mcts(ocfg, obase[g], 5, g * K + k, budgets[g * K + k])[0] for k in range(K)]
+        want = oracle.root_merge(obase[g], tables, extra.get("vanilla", 0))
+        assert got[g][:4].tolist() == want.tolist(), g
+        assert got[g][5] == K and got[g][6] == sum(budgets[g * K:(g + 1) * K]) and got[g][7] == 0
+
+
+def test_root_merge_refuses_groups_of_other_roots(dvc):
+    kw = dict(VARIANTS["2p24"], playouts=8)
+    ctx = _ctx(dvc, **kw)
+    roots = ctx.dvc_init_states(3, 4)               # four different roots
+    forest = dvc.Forest(ctx, roots, [20] * 4, 1)
+    forest.dvc_mcts_step(20)
+    with pytest.raises(dvc.DvcError):
+        forest.dvc_root_merge(3)                    # 3 does not divide 4: refused on the host
+    forest.dvc_root_merge(2)
+    with pytest.raises(dvc.DvcError) as e:
+        ctx.dvc_check()                             # groups whose roots differ
+    assert e.value.code == -1

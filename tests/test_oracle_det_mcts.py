@@ -211,3 +211,29 @@ def test_mcts_work_counts_one_step_per_guess():
         assert leaf[22] & 2
         want += sum(len(oracle.playout_trace(cfg_c, leaf, seed, tree, j, it)) for j in range(P))
     assert oracle.mcts_work(cfg_c, ms, seed, tree, budget)[1] == want
+
+
+@pytest.mark.parametrize("vanilla", [0, 1])
+def test_root_merge_of_one_tree_is_its_decision(vanilla):
+    # Sec. III-B: merging a single search reproduces its own decision
+    cfg = oracle.OracleConfig(nplayers=2, ntiles=24, deal=4, max_predraw=10, playouts=3, vanilla=vanilla)
+    for t, r in enumerate(oracle.init_states(cfg, seed=12, n=3)):
+        nodes, best = oracle.mcts(cfg, r, seed=4, tree=t, budget=150)
+        assert oracle.root_merge(r, [nodes], vanilla).tolist() == best.tolist()
+
+
+def test_root_merge_sums_over_trees_hand_made():
+    root = _toy_root()                                  # seat 0 to move, 2 players
+    a1, a2 = (1 << 10) | (2 << 5) | 3, (1 << 10) | (0 << 5) | 5
+    # rows [action, parent, visits, wins]; row 0 the root; a grandchild (parent 1) is not a root action
+    A = [[0, -1, 10, 4], [a1, 0, 6, 1], [a2, 0, 4, 3], [a2, 1, 99, 0]]
+    B = [[0, -1, 10, 2], [a2, 0, 7, 2], [a1, 0, 3, 0]]
+    assert oracle.root_merge(root, [A]).tolist() == [a1, 6, 1, 10]
+    assert oracle.root_merge(root, [B]).tolist() == [a2, 7, 2, 10]
+    assert oracle.root_merge(root, [A, B]).tolist() == [a2, 11, 5, 20]     # 4 + 7 against 6 + 3
+    # a tie in summed visits goes to the lower canonical rank: a2 (slot 0) before a1 (slot 2)
+    C = [[0, -1, 10, 0], [a1, 0, 5, 5], [a2, 0, 5, 0]]
+    assert oracle.root_merge(root, [C]).tolist() == [a2, 5, 0, 10]
+    # vanilla tables: the set nodes (children of the root) are summed over
+    V = [[0, -1, 12, 3], [0xFFE, 0, 8, 2], [a1, 1, 5, 2], [a2, 1, 3, 0], [0xFFE, 0, 4, 1], [a2, 4, 4, 1]]
+    assert oracle.root_merge(root, [V], vanilla=1).tolist() == [a2, 7, 1, 12]
