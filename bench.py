@@ -418,9 +418,14 @@ def run_ours(args, w):
         del flush
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
-        line["uneven"] = measure_uneven(UNEVEN, steps=1, warmup=1)
-        line["serve"] = serve_games(10_000, 400.0, 10.0, 64.0, 100_000, 256)
-        line["value_vs_rollout"] = value_vs_rollout()
+        for key, fn in (("uneven", lambda: measure_uneven(UNEVEN, steps=1, warmup=1)),
+                        ("serve", lambda: serve_games(10_000, 400.0, 10.0, 64.0, 100_000, 256)),
+                        ("value_vs_rollout", value_vs_rollout)):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # the main measurement above stands; record what failed
+                line[key] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+            torch.cuda.empty_cache()
         line["extras_wall_s"] = time.perf_counter() - t0
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
