@@ -288,7 +288,10 @@ def run_ours(args, w):
         step()
     torch.cuda.synchronize()
     ctx.dvc_check()
-    forest.dvc_forest_work(out=work)  # zero the counters
+    # the timed steps keep no work counts (instrumentation); the counts come
+    # from one more, untimed step of the same (deterministic) search below
+    forest.dvc_forest_count_work(False)
+    step()
 
     E = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     ev = [(E(), E(), E(), E()) for _ in range(args.steps)]
@@ -310,9 +313,6 @@ def run_ours(args, w):
     ctx.dvc_check()
     step_ms = [a.elapsed_time(b) for a, _, _, b in ev]
     kern_ms = [a.elapsed_time(b) for _, a, b, _ in ev]
-    forest.dvc_forest_work(out=work)
-    words_per_step = int(work[0].item()) / args.steps
-    game_steps_per_step = int(work[1].item()) / args.steps
     total_s = sum(step_ms) / 1e3
     if world > 1:
         total_s = max_over_ranks(total_s, dist, dev)
@@ -341,6 +341,15 @@ def run_ours(args, w):
     e2e_value = playouts_per_step * world * len(e2e_ms) / e2e_s
     ctx.dvc_check()
     decisions = host_stats.numpy()
+    # work of one step: the same search with the counters kept
+    forest.dvc_forest_count_work(True)
+    forest.dvc_forest_work(out=work)
+    step()
+    forest.dvc_forest_work(out=work)
+    torch.cuda.synchronize()
+    ctx.dvc_check()
+    words_per_step = int(work[0].item())
+    game_steps_per_step = int(work[1].item())
 
     traffic = None
     if (chains, trees_per_cta, warps) == PROFILED_SHAPE and n == 4096 and not args.compact:

@@ -119,6 +119,7 @@ def lib():
             "dvc_root_stats": ([vp, vp, vp], i),
             "dvc_forest_counters": ([vp, vp, vp], i),
             "dvc_forest_work": ([vp, vp, vp], i),
+            "dvc_forest_count_work": ([vp, i], i),
             "dvc_root_merge": ([vp, i, vp, vp], i),
             "dvc_forest_compaction": ([vp, i, i], i),
             "dvc_tree_export": ([vp, i, vp, vp], i),
@@ -361,6 +362,10 @@ class Forest:
         out = torch.empty((self.n // K, 8), dtype=torch.int32, device=self.ctx.dev()) if out is None else out
         self.ctx._rc(lib().dvc_root_merge(self.h, K, _ptr(out), _stream(stream)), "dvc_root_merge")
         return out
+
+    def dvc_forest_count_work(self, on):
+        """Keep (True, the default) or skip the work counters in the playout kernels."""
+        self.ctx._rc(lib().dvc_forest_count_work(self.h, 1 if on else 0), "dvc_forest_count_work")
 
     def dvc_forest_work(self, out=None, stream=None):
         """(random words, game steps) of the forest's playouts since the last call."""

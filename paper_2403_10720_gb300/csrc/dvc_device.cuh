@@ -254,8 +254,10 @@ __device__ __forceinline__ void store_state(const G& g, dvc_state& s) {
     s.pad[0] = s.pad[1] = s.pad[2] = 0;
 }
 
-// Sequence position of joker j (0 black, 1 white) within its owner's hand hp.
-__device__ __forceinline__ uint32_t joker_pos(const G& g, uint32_t hp, uint32_t j) {
+// Sequence position of joker j (0 black, 1 white) within its owner's hand hp
+// (S: any state with the joker fields jg0, jg1, jflag).
+template <class S>
+__device__ __forceinline__ uint32_t joker_pos(const S& g, uint32_t hp, uint32_t j) {
     const uint32_t gj = j ? g.jg1 : g.jg0, go = j ? g.jg0 : g.jg1;
     const bool other_here = (hp >> (24u + (j ^ 1u))) & 1u;
     // the other joker is first in a shared gap iff (flag ? other is white : other is black)
@@ -291,9 +293,9 @@ __device__ __forceinline__ uint32_t seq_pos(const G& g, uint32_t p, uint32_t t) 
     return pos;
 }
 
-// Tile in the h-th face-down slot (left to right) of hand p.
-__device__ __forceinline__ uint32_t hidden_slot(const G& g, uint32_t p, uint32_t h) {
-    const uint32_t hp = g.hand(p);
+// Tile in the h-th face-down slot (left to right) of the hand with tiles hp.
+template <class S>
+__device__ __forceinline__ uint32_t hidden_in(const S& g, uint32_t hp, uint32_t h) {
     const uint32_t hid = hp & ~g.rev;
     const uint32_t hj = hid & kJokerMask;
     const uint32_t hn = hid & kNumMask;
@@ -316,12 +318,15 @@ __device__ __forceinline__ uint32_t hidden_slot(const G& g, uint32_t p, uint32_t
     return nth_set(hn, h - skip);
 }
 
-// Sorted insertion of tile t into hand p (Sec. II-A).  Numbered: immediately
-// before the first larger numbered tile, so jokers of that gap stay left.
-// Joker: uniform over the len+1 insertion points (one word).
-template <class R>
-__device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, R& r) {
-    const uint32_t hp = g.hand(p);
+// Tile in the h-th face-down slot (left to right) of hand p.
+__device__ __forceinline__ uint32_t hidden_slot(const G& g, uint32_t p, uint32_t h) {
+    return hidden_in(g, g.hand(p), h);
+}
+
+// The joker-gap part of a sorted insertion of tile t into the hand with
+// tiles hp (before t is added); a joker takes one word for its position.
+template <class S, class R>
+__device__ __forceinline__ void insert_gaps(S& g, uint32_t hp, uint32_t t, R& r) {
     if (t < 24u) {
         const uint32_t k = __popc(hp & kNumMask & ((1u << t) - 1u));
         if ((hp >> 24) & 1u) g.jg0 += g.jg0 > k;
@@ -340,6 +345,14 @@ __device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, R& r) 
         if (j) g.jg1 = gap; else g.jg0 = gap;
         g.jflag = flag;
     }
+}
+
+// Sorted insertion of tile t into hand p (Sec. II-A).  Numbered: immediately
+// before the first larger numbered tile, so jokers of that gap stay left.
+// Joker: uniform over the len+1 insertion points (one word).
+template <class R>
+__device__ __forceinline__ void insert_tile(G& g, uint32_t p, uint32_t t, R& r) {
+    insert_gaps(g, g.hand(p), t, r);
     g.add(p, 1u << t);
 }
 
@@ -504,6 +517,129 @@ __device__ __forceinline__ uint32_t playout(G g, R& r, uint32_t cont_thr, const 
         if (res == kTurnOver) next_turn(g, r);
     }
     return kNone;
+}
+
+// The playout state with hands held relative to the mover: a0 is the hand of
+// seat cur, a1, a2, a3 those of seats cur + 1, cur + 2, cur + 3 (modulo np);
+// positions from np on hold 0.  The opponents are then visited in the
+// canonical order (from cur + 1) with no selection of hands by seat, and a
+// new turn rotates the four words once.  alive and winner stay by seat.
+struct GR {
+    uint32_t a0, a1, a2, a3;
+    uint32_t rev, jg0, jg1, jflag;
+    uint32_t cur, drawn, alive, winner, np, tmask;
+};
+
+__device__ __forceinline__ GR to_gr(const G& g) {
+    GR r;
+    uint32_t q1 = g.cur + 1u, q2 = g.cur + 2u, q3 = g.cur + 3u;
+    q1 = q1 >= g.np ? q1 - g.np : q1;
+    q2 = q2 >= g.np ? q2 - g.np : q2;
+    q3 = q3 >= g.np ? q3 - g.np : q3;
+    r.a0 = g.hand(g.cur);
+    r.a1 = g.hand(q1);
+    r.a2 = g.np > 2u ? g.hand(q2) : 0u;
+    r.a3 = g.np > 3u ? g.hand(q3) : 0u;
+    r.rev = g.rev;
+    r.jg0 = g.jg0;
+    r.jg1 = g.jg1;
+    r.jflag = g.jflag;
+    r.cur = g.cur;
+    r.drawn = g.drawn;
+    r.alive = g.alive;
+    r.winner = g.winner;
+    r.np = g.np;
+    r.tmask = g.tmask;
+    return r;
+}
+
+// One playout step in the relative form: random_guess, then next_turn if the
+// turn passes -- the same rules, the same words in the same order.
+template <class R>
+__device__ __forceinline__ int step_gen(GR& g, R& r, uint32_t cont_thr, const uint32_t* magic) {
+    r.ensure(4);
+    // the guess: opponent slots in canonical order times unknown identities
+    const uint32_t U = g.tmask & ~g.a0 & ~g.rev;
+    const uint32_t nid = __popc(U);
+    const uint32_t c1 = __popc(g.a1 & ~g.rev), c2 = __popc(g.a2 & ~g.rev), c3 = __popc(g.a3 & ~g.rev);
+    const uint32_t k = pick(r.next(), (c1 + c2 + c3) * nid);
+    uint32_t s = div_small(k, nid, magic);
+    const uint32_t i = k - s * nid;
+    uint32_t off = 1u, hq = g.a1;
+    if (s >= c1) {
+        s -= c1;
+        off = 2u;
+        hq = g.a2;
+        if (s >= c2) {
+            s -= c2;
+            off = 3u;
+            hq = g.a3;
+        }
+    }
+    const uint32_t target = hidden_in(g, hq, s);
+    const uint32_t tb = 1u << target;
+    if (__popc(U & (tb - 1u)) == i) {  // correct: the target is revealed
+        g.rev |= tb;
+        if (!(hq & ~g.rev)) {
+            uint32_t q = g.cur + off;
+            q = q >= g.np ? q - g.np : q;
+            g.alive &= ~(1u << q);
+        }
+        if (__popc(g.alive) == 1) {
+            g.winner = g.cur;
+            return kGameOver;
+        }
+        if (cont_thr != 0u && r.next() < cont_thr) return kGuessAgain;
+    } else {  // wrong: the mover reveals its drawn tile, else its leftmost face-down one
+        const uint32_t t = g.drawn != kNone ? g.drawn : hidden_in(g, g.a0, 0u);
+        g.rev |= 1u << t;
+        if (!(g.a0 & ~g.rev)) g.alive &= ~(1u << g.cur);
+        if (__popc(g.alive) == 1) {
+            g.winner = (uint32_t)__ffs(g.alive) - 1u;
+            return kGameOver;
+        }
+    }
+    // the next live seat moves: rotate the hands by d = its distance (1 .. np-1)
+    const uint32_t nc = next_alive(g.alive, g.cur, g.np);
+    const uint32_t d = nc > g.cur ? nc - g.cur : nc + g.np - g.cur;
+    if (g.np == 4u) {
+        if (d & 1u) {
+            const uint32_t t = g.a0;
+            g.a0 = g.a1;
+            g.a1 = g.a2;
+            g.a2 = g.a3;
+            g.a3 = t;
+        }
+        if (d & 2u) {
+            uint32_t t = g.a0;
+            g.a0 = g.a2;
+            g.a2 = t;
+            t = g.a1;
+            g.a1 = g.a3;
+            g.a3 = t;
+        }
+    } else if (g.np == 3u) {
+        const uint32_t b0 = d == 1u ? g.a1 : g.a2, b1 = d == 1u ? g.a2 : g.a0, b2 = d == 1u ? g.a0 : g.a1;
+        g.a0 = b0;
+        g.a1 = b1;
+        g.a2 = b2;
+    } else {
+        const uint32_t t = g.a0;
+        g.a0 = g.a1;
+        g.a1 = t;
+    }
+    g.cur = nc;
+    // ... and draws
+    const uint32_t pool = g.tmask & ~(g.a0 | g.a1 | g.a2 | g.a3);
+    if (!pool) {
+        g.drawn = kNone;
+        return kTurnOver;
+    }
+    const uint32_t t = nth_set(pool, pick(r.next(), __popc(pool)));
+    insert_gaps(g, g.a0, t, r);
+    g.a0 |= 1u << t;
+    g.drawn = t;
+    return kTurnOver;
 }
 
 // Words for the playout loop of the pooled kernel: a short queue that is

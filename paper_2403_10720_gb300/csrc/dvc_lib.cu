@@ -88,6 +88,7 @@ struct dvc_forest {
     int active_prefix;        // fused engine: only trees [0, active_prefix) of the order run (servers)
     int cmp_receivers;        // lane compaction in the pipeline's two-player playouts: receiver warps (0 = off)
     int cmp_donate_at;        // ... and the running games at or below which a donor warp hands its games over
+    int no_count;             // work counters off (dvc_forest_count_work)
 };
 
 namespace {
@@ -238,18 +239,24 @@ __global__ void rollout_kernel(const dvc_state* leaves, int n_leaves, int P, uin
             r.open(seed, tree_ids[l], (uint32_t)j, leaf_ids[l], kTagRoll);
             playout_begin(g, r, cont_thr);
             winner = kNone;
-            for (int guard = 0; guard < 128; ++guard) {
-                r.ensure(4);
-                int res;
-                if constexpr (ORD)
-                    res = random_guess_ordered(g, r, cont_thr);
-                else
-                    res = random_guess(g, r, cont_thr, s_magic);
-                if (res == kGameOver) {
-                    winner = g.winner;
-                    break;
+            if constexpr (ORD) {
+                for (int guard = 0; guard < 128; ++guard) {
+                    r.ensure(4);
+                    const int res = random_guess_ordered(g, r, cont_thr);
+                    if (res == kGameOver) {
+                        winner = g.winner;
+                        break;
+                    }
+                    if (res == kTurnOver) next_turn(g, r);
                 }
-                if (res == kTurnOver) next_turn(g, r);
+            } else {
+                GR gr = to_gr(g);
+                for (int guard = 0; guard < 128; ++guard) {
+                    if (step_gen(gr, r, cont_thr, s_magic) == kGameOver) {
+                        winner = gr.winner;
+                        break;
+                    }
+                }
             }
             // at most |T| guesses per game: no winner after 128 is a broken invariant
             if (winner == kNone) latch_error(flags, DVC_E_INTERNAL);
@@ -681,7 +688,7 @@ ForestDev dev_of(dvc_forest* f) {
     d.ucb = f->ucb;
     d.csl = f->csl;
     d.flags = f->ctx->d_flags;
-    d.words = f->d_words;
+    d.words = f->no_count ? nullptr : f->d_words;
     d.set_key = f->set_key;
     d.set_slot = f->set_slot;
     return d;
@@ -1100,24 +1107,28 @@ int enqueue_pipe_iteration(dvc_forest* f, int b0, int b1, cudaStream_t st) {
     // may-stop leaves possible: the full tree, or leaves that can be the root itself
     const bool pend = c->cfg.tree_continue || c->cfg.d_max == 0 || c->cfg.vanilla;
     const uint32_t smem = pipe_rollout_smem(L, threads);
+    unsigned long long* words = f->no_count ? nullptr : f->d_words;
     if (fast2 && !sp.policy && !pend && f->cmp_receivers > 0 && f->cmp_receivers < threads / 32)
         pipe_rollout_compact_kernel<<<b1 - b0, threads, pipe_compact_smem(L, threads, f->cmp_receivers), st>>>(
-            sp, n, L, b0, f->order, f->meta, f->pipe, f->d_words, f->cmp_receivers, f->cmp_donate_at);
+            sp, n, L, b0, f->order, f->meta, f->pipe, words, f->cmp_receivers, f->cmp_donate_at);
+    else if (fast2 && !sp.policy && !pend && f->no_count)
+        pipe_rollout_kernel<true, false, false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order,
+                                                                                      f->meta, f->pipe, nullptr);
     else if (fast2 && !sp.policy && !pend)
         pipe_rollout_kernel<true, false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta,
-                                                                               f->pipe, f->d_words);
+                                                                               f->pipe, words);
     else if (fast2 && !sp.policy)
         pipe_rollout_kernel<true, false, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta,
-                                                                              f->pipe, f->d_words);
+                                                                              f->pipe, words);
     else if (fast2)
         pipe_rollout_kernel<true, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
-                                                                       f->d_words);
+                                                                       words);
     else if (!sp.policy)
         pipe_rollout_kernel<false, false><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
-                                                                         f->d_words);
+                                                                         words);
     else
         pipe_rollout_kernel<false, true><<<b1 - b0, threads, smem, st>>>(sp, n, L, b0, f->order, f->meta, f->pipe,
-                                                                        f->d_words);
+                                                                        words);
     return check_launch(c, "pipeline kernels");
 }
 
@@ -1216,9 +1227,9 @@ int launch_pipeline(dvc_forest* f, int n_iterations, cudaStream_t st) {
         const int sm = (int)pipe_rollout_smem(f->trees_per_cta, threads);
         cudaError_t e = cudaSuccess;
         // several rollout CTAs per SM need the largest shared-memory carveout
-        for (auto k : {pipe_rollout_kernel<true, false, false>, pipe_rollout_kernel<true, false, true>,
-                       pipe_rollout_kernel<true, true, true>, pipe_rollout_kernel<false, false, true>,
-                       pipe_rollout_kernel<false, true, true>}) {
+        for (auto k : {pipe_rollout_kernel<true, false, false>, pipe_rollout_kernel<true, false, false, false>,
+                       pipe_rollout_kernel<true, false, true>, pipe_rollout_kernel<true, true, true>,
+                       pipe_rollout_kernel<false, false, true>, pipe_rollout_kernel<false, true, true>}) {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1473,6 +1484,18 @@ int dvc_forest_compaction(dvc_forest* f, int receivers, int donate_at) {
     }
     f->cmp_receivers = receivers;
     f->cmp_donate_at = receivers ? donate_at : 0;
+    return DVC_OK;
+}
+
+int dvc_forest_count_work(dvc_forest* f, int on) {
+    if (!f) return DVC_E_INVALID;
+    const int no = on ? 0 : 1;
+    if (no != f->no_count) {  // the captured pipeline graphs hold the other kernels
+        if (f->chunk_exec) cudaGraphExecDestroy(f->chunk_exec);
+        if (f->value_exec) cudaGraphExecDestroy(f->value_exec);
+        f->chunk_exec = f->value_exec = nullptr;
+    }
+    f->no_count = no;
     return DVC_OK;
 }
 

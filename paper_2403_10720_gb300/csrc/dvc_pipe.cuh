@@ -159,10 +159,12 @@ __global__ void __launch_bounds__(128)
 // PEND: leaves may begin where the mover may stop (the full game tree, or
 // d_max = 0); without it that check is compiled out of the playout loop,
 // since an in-tree action always clears the may-stop bit otherwise.
+// CNT: keep the work counters (random words, game steps) in words_out;
+// compiled out for forests that switched counting off.
 // Registers: 32 for the two-player path (two 1024-thread or three
 // 512-thread CTAs per SM, with room left in the register file for the
 // other chains' tree walks), up to 64 for the general path.
-template <bool FAST2, bool ORD = false, bool PEND = true>
+template <bool FAST2, bool ORD = false, bool PEND = true, bool CNT = true>
 __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     pipe_rollout_kernel(SearchParams sp, int n, int L, int b0, const int32_t* order, const TreeMeta* meta, PipeBufs P,
                         unsigned long long* words_out) {
@@ -214,7 +216,8 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     RingQueue r;
     r.ring = s_ring + tid;
     r.stride = blockDim.x;
-    G g;
+    G g;    // general path, ordering-aware policy
+    GR gr;  // general path, uniform policy
     uint32_t h0 = 0, h1 = 0, rev = 0, cur = 0, drawn = kNone, winner = kNone;
     auto start = [&](uint32_t p) {
         k = Pp > 1u ? __umulhi(p, mP) : p;
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         } else {
             g = load_state(ls);
             playout_begin(g, r, sp.cont_thr);
+            if constexpr (!ORD) gr = to_gr(g);
         }
         // a may-stop leaf's first continue coin is a game step of its own
         // (the fast path counts it as an iteration of its loop)
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
     for (;;) {
         const unsigned running = __ballot_sync(0xFFFFFFFFu, busy);
         if (!running) break;
-        wsteps += __popc(running);
+        if constexpr (CNT) wsteps += __popc(running);
         bool ended = false;
         if (busy) {
             int res;
@@ -264,14 +268,14 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
                     res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);
                 else
                     res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
-            } else {
+            } else if constexpr (ORD) {
                 r.ensure(4);
-                if constexpr (ORD)
-                    res = random_guess_ordered(g, r, sp.cont_thr);
-                else
-                    res = random_guess(g, r, sp.cont_thr, s_magic);
+                res = random_guess_ordered(g, r, sp.cont_thr);
                 if (res == kTurnOver) next_turn(g, r);
                 winner = g.winner;
+            } else {
+                res = step_gen(gr, r, sp.cont_thr, s_magic);
+                winner = gr.winner;
             }
             ++steps;
             if (res == kGameOver || steps >= 128u) {
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
                 // leaf's wins fall short of P (checked below)
                 const uint32_t w = res == kGameOver ? winner : kNone;
                 if (w < 4u) atomicAdd(&s_wins[4 * k + w], 1);
-                words += r.used();
+                if constexpr (CNT) words += r.used();
                 ended = true;
             }
         }
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         if (s_wins[4 * e] + s_wins[4 * e + 1] + s_wins[4 * e + 2] + s_wins[4 * e + 3] != (int32_t)Pp)
             latch_error(P.flags, DVC_E_INTERNAL);
     }
-    if (words_out) {  // words_out[0]: random words, words_out[1]: game steps (guesses)
+    if (CNT && words_out) {  // words_out[0]: random words, words_out[1]: game steps (guesses)
         const unsigned long long sum = warp_sum_u64((unsigned long long)words);
         if (lane == 0 && sum) atomicAdd(words_out, sum);
         if (lane == 0 && wsteps) atomicAdd(words_out + 1, (unsigned long long)wsteps);

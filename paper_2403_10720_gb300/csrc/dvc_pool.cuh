@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(MAXT, 1)
             int slot = 0, steps = 0;
             WordQueue r;
             // state of the lane's current game
-            G g;
+            G g;    // general path, ordering-aware policy
+            GR gr;  // general path, uniform policy
             uint32_t h0 = 0, h1 = 0, rev = 0, cur = 0, drawn = kNone, winner = kNone;
             auto start = [&](int p) {
                 const int k = p / P;
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                 } else {
                     g = load_state(ls);
                     playout_begin(g, r, sp.cont_thr);
+                    if constexpr (!ORD) gr = to_gr(g);
                 }
                 // a may-stop leaf's first continue coin is a game step of its
                 // own (the fast path counts it as an iteration of its loop)
@@ -244,14 +246,14 @@ __global__ void __launch_bounds__(MAXT, 1)
                             res = step_2p24_ordered(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_lut12);
                         else
                             res = step_2p24(h0, h1, rev, cur, drawn, winner, r, sp.cont_thr, s_magic, s_lut12);
-                    } else {
+                    } else if constexpr (ORD) {
                         r.ensure(4);
-                        if constexpr (ORD)
-                            res = random_guess_ordered(g, r, sp.cont_thr);
-                        else
-                            res = random_guess(g, r, sp.cont_thr, s_magic);
+                        res = random_guess_ordered(g, r, sp.cont_thr);
                         if (res == kTurnOver) next_turn(g, r);
                         winner = g.winner;
+                    } else {
+                        res = step_gen(gr, r, sp.cont_thr, s_magic);
+                        winner = gr.winner;
                     }
                     ++steps;
                     if (res == kGameOver || steps >= 128) {

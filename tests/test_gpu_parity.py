@@ -484,6 +484,38 @@ def test_forest_work_counters_match_oracle(dvc, variant, P, budgets, extra, engi
     assert (forest.dvc_forest_work().cpu().numpy() == 0).all()   # read-and-zero
 
 
+@pytest.mark.parametrize("variant,extra,engine", [
+    ("2p24", {}, 2), ("2p24", {}, 1), ("4p26j", {}, 2), ("2p24", dict(tree_continue=1), 2),
+])
+def test_work_counting_off_changes_nothing_else(dvc, variant, extra, engine):
+    """With work counting off (the counting-free two-player playout kernel in
+    the pipeline) every tree and decision is unchanged, the counters do not
+    move, and counting resumes when switched back on."""
+    kw = dict(VARIANTS[variant], playouts=32, **extra)
+    ctx = _ctx(dvc, **kw)
+    n, budget = 600, 60
+    roots = ctx.dvc_init_states(43, n)
+    out = []
+    for on in (True, False):
+        f = dvc.Forest(ctx, roots, [budget] * n, 14)
+        f.dvc_forest_tune(engine)
+        f.dvc_forest_count_work(on)
+        f.dvc_mcts_step(budget)
+        out.append((f.dvc_root_stats().cpu().numpy(), [f.dvc_tree_export(t).cpu().numpy() for t in (0, 599)],
+                    f.dvc_forest_work().cpu().numpy()))
+        if not on:
+            f.dvc_forest_count_work(True)
+            f.dvc_forest_reset()
+            f.dvc_mcts_step(budget)
+            again = f.dvc_forest_work().cpu().numpy()
+        f.close()
+    ctx.dvc_check()
+    (s0, t0, w0), (s1, t1, w1) = out
+    assert (s0 == s1).all() and all((a == b).all() for a, b in zip(t0, t1))
+    assert w0[0] > 0 and w0[1] > 0 and (w1 == 0).all()
+    assert (again == w0).all()
+
+
 @pytest.mark.parametrize("shape,receivers,donate_at", [
     ((2, 2, 16, 3), 4, 8), ((2, 2, 16, 3), 1, 31), ((2, 4, 8, 2), 2, 16), ((2, 11, 4, 1), 1, 4),
     ((2, 3, 16, 4), 15, 1),
