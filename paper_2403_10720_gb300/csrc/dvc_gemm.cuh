@@ -167,7 +167,8 @@ struct GemmArgs {
     // group), 8 parts per row, summed in a fixed order by the consumer.
     const __nv_bfloat16* head_w;  // 4 (or more) x N BF16, row-major; null: no head
     float* head_out;              // M x 8 x 4 FP32
-    int wide;  // C and Cf 32-byte aligned: 256-bit stores (half the store instructions)
+    int wide;   // C and Cf 32-byte aligned: 256-bit stores (half the store instructions)
+    int bias4;  // bias 16-byte aligned: read four floats per load
 };
 
 // 32 bytes to global memory in one instruction (p 32-byte aligned).
@@ -327,7 +328,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (live) {
                     const int nb = n0 + c0;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += a.bias ? __ldg(a.bias + nb + i) : 0.0f;
+                    for (int i = 0; i < 16; ++i) v[i] += (a.bias && !a.bias4) ? __ldg(a.bias + nb + i) : 0.0f;
+                    if (a.bias4) {  // the 16 biases as four 16-byte loads (nb is a multiple of 16)
+                        const float4* b4 = reinterpret_cast<const float4*>(a.bias + nb);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 x = __ldg(b4 + j);
+                            v[4 * j] += x.x;
+                            v[4 * j + 1] += x.y;
+                            v[4 * j + 2] += x.z;
+                            v[4 * j + 3] += x.w;
+                        }
+                    }
                     if (a.Cf) {
                         float* cf = a.Cf + (size_t)row * a.N + nb;
                         if (a.wide) {

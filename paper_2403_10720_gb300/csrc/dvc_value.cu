@@ -53,99 +53,126 @@ namespace {
 
 __device__ __forceinline__ uint32_t unknown_mask(const G& g) { return g.tmask & ~g.hand(g.cur) & ~g.rev; }
 
-// One warp per state: X[row] = features (BF16), zero-padded to 640.  The
-// warp sets the row's 640 bits in shared memory, then writes the row with
-// 16-byte stores (8 BF16 or 4 FP32 values each).  Blocks of 256 threads.
+// One thread per state: the row's 640 feature bits are built in registers at
+// fixed positions (every loop below is unrolled), parked in the thread's own
+// shared-memory row, and then each warp writes its 32 consecutive rows -- one
+// contiguous stretch of X -- with coalesced 16-byte stores: a byte of feature
+// bits becomes 8 BF16 values through a 256-entry table (4 FP32 values per
+// nibble for Xf).  Rows n .. npad-1 are written as zeros.  Blocks of 256.
+constexpr int kFeatWords = VF / 32;         // 20
+constexpr int kFeatPitch = kFeatWords + 1;  // 21: the 32 rows of a warp start in 32 different banks
+
+// OR a field of `width` bits into the bit vector f at position pos (both
+// known at compile time once the caller's loops are unrolled).
+__device__ __forceinline__ void or_bits(uint32_t* f, int pos, uint32_t field, int width) {
+    const int w = pos >> 5, sh = pos & 31;
+    f[w] |= field << sh;
+    if (sh + width > 32) f[w + 1] |= field >> (32 - sh);
+}
+
 __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X,
                                                        float* Xf) {
-    __shared__ uint32_t s_bits[8][VF / 32];
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
-    if (row >= npad) return;
-    uint32_t* bits = s_bits[w];
-    if (lane < VF / 32) bits[lane] = 0u;
-    __syncwarp();
+    __shared__ uint32_t s_rows[256 * kFeatPitch];
+    __shared__ uint4 s_lut[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b < 256; b += blockDim.x) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            w[j] = (((b >> (2 * j)) & 1) ? 0x3F80u : 0u) | (((b >> (2 * j + 1)) & 1) ? 0x3F800000u : 0u);
+        s_lut[b] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    uint32_t f[kFeatWords];
+#pragma unroll
+    for (int k = 0; k < kFeatWords; ++k) f[k] = 0u;
+    const int row = blockIdx.x * blockDim.x + tid;
     if (row < n) {
         const G g = load_state(states[row]);
-        auto set = [&](int i) { atomicOr(&bits[i >> 5], 1u << (i & 31)); };
+        uint32_t q1 = g.cur + 1u, q2 = g.cur + 2u, q3 = g.cur + 3u;
+        q1 = q1 >= g.np ? q1 - g.np : q1;
+        q2 = q2 >= g.np ? q2 - g.np : q2;
+        q3 = q3 >= g.np ? q3 - g.np : q3;
+        const uint32_t M1 = g.hand(q1), M2 = g.np > 2u ? g.hand(q2) : 0u, M3 = g.np > 3u ? g.hand(q3) : 0u;
         const uint32_t held = g.h0 | g.h1 | g.h2 | g.h3;
-        if (lane < 26 && ((g.tmask >> lane) & 1u) && ((held >> lane) & 1u)) {
-            uint32_t owner = 0;
-            for (uint32_t p = 0; p < g.np; ++p)
-                if ((g.hand(p) >> lane) & 1u) owner = p;
-            const uint32_t rel = (owner + g.np - g.cur) % g.np;
-            set(7 * lane + (int)rel);
-            set(7 * lane + 4 + (int)((g.rev >> lane) & 1u));
-            if ((uint32_t)lane == g.drawn) set(7 * lane + 6);
+        // tiles: bit 7t + (owner seat relative to the mover), 7t + 4 + face-up,
+        // 7t + 6 if drawn this turn; tiles in the pool have none
+#pragma unroll
+        for (int t = 0; t < 26; ++t) {
+            const uint32_t r = ((M1 >> t) & 1u) | (((M2 >> t) & 1u) << 1) | (((M3 >> t) & 1u) * 3u);
+            const uint32_t grp = (1u << r) | (16u << ((g.rev >> t) & 1u)) | ((uint32_t)t == g.drawn ? 64u : 0u);
+            or_bits(f, 7 * t, ((held >> t) & 1u) ? grp : 0u, 7);
         }
         const uint32_t U = unknown_mask(g);
-        // each lane takes one (opponent, slot); numbered tiles ascend by id
-        // along a row, so the slot's face-up numbered neighbours are the
-        // nearest face-up numbered tiles below and above a threshold id: the
-        // slot's own tile, or for a joker the first numbered tile to its right
-        // (its gap counts the numbered tiles to its left)
-        for (int pair = lane; pair < 33; pair += 32) {
-            const uint32_t k = 1u + (uint32_t)pair / 11u, s = (uint32_t)pair % 11u;
-            if (k >= g.np) continue;
-            const uint32_t q = (g.cur + k) % g.np;
-            const uint32_t hq = g.hand(q);
-            if (s >= (uint32_t)__popc(hq)) continue;
-            const int base = 182 + (int)(((k - 1u) * 11u + s) * 13u);
-            const uint32_t t = seq_tile(g, q, s);
-            if ((g.rev >> t) & 1u) {
-                set(base + (t < 24u ? (int)(t >> 1) : 12));
-                continue;
-            }
-            const uint32_t num = hq & kNumMask, R = num & g.rev;
-            uint32_t thr = t;
-            if (t >= 24u) {
-                const uint32_t jg = t == 24u ? g.jg0 : g.jg1;
-                thr = jg < (uint32_t)__popc(num) ? nth_set(num, jg) : 24u;
-            }
-            const uint32_t left = R & ((1u << thr) - 1u), right = R & ~((1u << thr) - 1u);
-            const int lo = left ? 31 - __clz(left) : -1;
-            const int hi = right ? __ffs(right) - 1 : 24;
-            // unknown numbered tiles strictly between lo and hi, as values:
-            // bit v of the 12-bit field <- tile bits 2v | 2v+1 (even bits
-            // gathered by halving shifts), bit 12 <- an unknown joker; the
-            // 13-bit field is or-ed into at most two words
-            const uint32_t above = lo < 0 ? 0x00FFFFFFu : (0x00FFFFFFu & ~((2u << lo) - 1u));
-            const uint32_t below = (1u << hi) - 1u;
-            const uint32_t m = U & above & below;
-            uint32_t x = (m | (m >> 1)) & 0x00555555u;
-            x = (x | (x >> 1)) & 0x00333333u;
-            x = (x | (x >> 2)) & 0x000F0F0Fu;
-            x = ((x | (x >> 4)) & 0x000000FFu) | ((x >> 8) & 0x00000F00u);
-            const uint32_t field = x | ((U & kJokerMask) ? 1u << 12 : 0u);
-            const uint32_t w0 = (uint32_t)base >> 5, sh = (uint32_t)base & 31u;
-            if (field) {
-                atomicOr(&bits[w0], field << sh);
-                if (sh > 19u) atomicOr(&bits[w0 + 1u], field >> (32u - sh));
-            }
-        }
-    }
-    __syncwarp();
-    if (X) {
-        uint4* dst = reinterpret_cast<uint4*>(X + (size_t)row * VF);
-        for (int c = lane; c < VF / 8; c += 32) {
-            const uint32_t byte = (bits[c >> 2] >> (8 * (c & 3))) & 0xFFu;
-            uint32_t wv[4];
+        const uint32_t jok = (U & kJokerMask) ? 1u << 12 : 0u;
+        // opponent k (seat cur + k), slot s: 13 bits at 182 + ((k - 1) * 11 + s) * 13;
+        // a face-up tile sets its value (a joker 12); a face-down slot sets every
+        // value the mover cannot see strictly between its face-up numbered
+        // neighbours, plus bit 12 if a joker is unseen.  Slots are walked left
+        // to right: numbered tiles ascend by id, each joker stands where its
+        // gap puts it, and a joker's right-hand threshold is the next numbered
+        // tile of the row (or 24).
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                wv[j] = (((byte >> (2 * j)) & 1u) ? 0x3F80u : 0u) | (((byte >> (2 * j + 1)) & 1u) ? 0x3F800000u : 0u);
-            dst[c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        for (int k = 1; k < 4; ++k) {
+            const uint32_t hq = k == 1 ? M1 : (k == 2 ? M2 : M3);
+            const uint32_t len = (uint32_t)k < g.np ? (uint32_t)__popc(hq) : 0u;
+            const uint32_t num = hq & kNumMask, R = num & g.rev;
+            const uint32_t jp0 = (hq >> 24) & 1u ? joker_pos(g, hq, 0u) : 0xFFu;
+            const uint32_t jp1 = (hq >> 25) & 1u ? joker_pos(g, hq, 1u) : 0xFFu;
+            uint32_t rem = num;
+#pragma unroll
+            for (int sl = 0; sl < 11; ++sl) {
+                if ((uint32_t)sl < len) {
+                    const bool j0 = (uint32_t)sl == jp0, j1 = (uint32_t)sl == jp1;
+                    const uint32_t low = rem ? (uint32_t)__ffs(rem) - 1u : 24u;
+                    const uint32_t t = j0 ? 24u : (j1 ? 25u : low);
+                    const uint32_t thr = low;  // a numbered slot's own tile, or the tile right of a joker
+                    if (!j0 && !j1) rem &= rem - 1u;
+                    uint32_t field;
+                    if ((g.rev >> t) & 1u) {
+                        field = 1u << (t < 24u ? t >> 1 : 12u);
+                    } else {
+                        const uint32_t below_thr = thr >= 32u ? 0xFFFFFFFFu : (1u << thr) - 1u;
+                        const uint32_t left = R & below_thr, right = R & ~below_thr;
+                        const int lo = left ? 31 - __clz(left) : -1;
+                        const int hi = right ? __ffs(right) - 1 : 24;
+                        const uint32_t above = lo < 0 ? 0x00FFFFFFu : (0x00FFFFFFu & ~((2u << lo) - 1u));
+                        const uint32_t below = (1u << hi) - 1u;
+                        const uint32_t m = U & above & below;
+                        uint32_t x = (m | (m >> 1)) & 0x00555555u;
+                        x = (x | (x >> 1)) & 0x00333333u;
+                        x = (x | (x >> 2)) & 0x000F0F0Fu;
+                        x = ((x | (x >> 4)) & 0x000000FFu) | ((x >> 8) & 0x00000F00u);
+                        field = x | jok;
+                    }
+                    or_bits(f, 182 + ((k - 1) * 11 + sl) * 13, field, 13);
+                }
+            }
         }
     }
-    if (Xf) {
-        float4* dst = reinterpret_cast<float4*>(Xf + (size_t)row * VF);
-        for (int c = lane; c < VF / 4; c += 32) {
-            const uint32_t nib = (bits[c >> 3] >> (4 * (c & 7))) & 0xFu;
+    uint32_t* mine = s_rows + tid * kFeatPitch;
+#pragma unroll
+    for (int k = 0; k < kFeatWords; ++k) mine[k] = f[k];
+    __syncthreads();
+    const int row0 = blockIdx.x * blockDim.x + warp * 32;
+    const int nrows = min(32, npad - row0);
+    const uint32_t* wrows = s_rows + warp * 32 * kFeatPitch;
+    if (X && nrows > 0) {
+        uint4* dst = reinterpret_cast<uint4*>(X + (size_t)row0 * VF);
+        for (int c = lane; c < nrows * (VF / 8); c += 32) {
+            const int r = c / (VF / 8), k = c - r * (VF / 8);
+            dst[c] = s_lut[(wrows[r * kFeatPitch + (k >> 2)] >> (8 * (k & 3))) & 0xFFu];
+        }
+    }
+    if (Xf && nrows > 0) {
+        float4* dst = reinterpret_cast<float4*>(Xf + (size_t)row0 * VF);
+        for (int c = lane; c < nrows * (VF / 4); c += 32) {
+            const int r = c / (VF / 4), k = c - r * (VF / 4);
+            const uint32_t nib = (wrows[r * kFeatPitch + (k >> 3)] >> (4 * (k & 7))) & 0xFu;
             dst[c] = make_float4((float)(nib & 1u), (float)((nib >> 1) & 1u), (float)((nib >> 2) & 1u),
                                  (float)((nib >> 3) & 1u));
         }
     }
 }
-
 
 // Softmax over relative seats 0..P-1, written per absolute seat, of logits
 // given as 8 partial sums per row (the output layer folded into layer 3):
@@ -411,7 +438,8 @@ constexpr uint64_t kGemmWaitNs = 2000000000ull;  // 2 s: far beyond any wait of 
 cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, __nv_bfloat16* C, float* Cf, int M,
                  int N, int K, int act, int32_t* flags, cudaStream_t st) {
     const int wide = ((uintptr_t)C % 32 == 0 && (uintptr_t)Cf % 32 == 0) ? 1 : 0;  // null counts as aligned
-    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0, nullptr, nullptr, wide};
+    GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0, nullptr, nullptr, wide,
+               bias && (uintptr_t)bias % 16 == 0};
     if (N % 256 == 0) return launch_gemm<256>(a, st);
     if (N % 128 == 0) return launch_gemm<128>(a, st);
     if (N % 64 == 0) return launch_gemm<64>(a, st);
@@ -423,7 +451,8 @@ cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bi
 // written; 8 partial logit vectors per row into `parts` (rows x 8 x 4).
 cudaError_t gemm_head(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* Cf, int M,
                       const __nv_bfloat16* W4, float* parts, int32_t* flags, cudaStream_t st) {
-    GemmArgs a{A, B, bias, nullptr, Cf, M, VH, VH, kActGelu, flags, kGemmWaitNs, 0, W4, parts, (uintptr_t)Cf % 32 == 0};
+    GemmArgs a{A,     B,  bias, nullptr, Cf, M, VH, VH, kActGelu, flags, kGemmWaitNs, 0, W4, parts,
+               (uintptr_t)Cf % 32 == 0, bias && (uintptr_t)bias % 16 == 0};
     return launch_gemm<256>(a, st);  // N = 512: two 256-column tiles x four column groups = kHeadParts
 }
 
@@ -507,7 +536,7 @@ int forward_into(dvc_ctx* c, const dvc_state* states, int n, int npad, __nv_bflo
                  cudaStream_t st) {
     dvc_value_net* v = c->vnet;
     int32_t* fl = c->d_flags;
-    features_kernel<<<(npad * 32 + 255) / 256, 256, 0, st>>>(states, n, npad, X, nullptr);
+    features_kernel<<<(npad + 255) / 256, 256, 0, st>>>(states, n, npad, X, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = gemm(X, v->W1, v->master + OFF_B1, H1, Z1, npad, VH, VF, kActGelu, fl, st);
     if (e == cudaSuccess) e = gemm(H1, v->W2, v->master + OFF_B2, H2, Z2, npad, VH, VH, kActGelu, fl, st);
@@ -589,7 +618,7 @@ int dvc_value_features(dvc_ctx* c, const dvc_state* d_states, int n, float* d_ou
     if (n == 0) return DVC_OK;
     if (!is_device_ptr(d_out, c->device)) return fail(c, DVC_E_INVALID, "dvc_value_features: d_out must be device memory");
     if (int rc = set_device(c)) return rc;
-    features_kernel<<<(n * 32 + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_states, n, n, nullptr, d_out);
+    features_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_states, n, n, nullptr, d_out);
     return check_launch(c, "features_kernel");
 }
 
