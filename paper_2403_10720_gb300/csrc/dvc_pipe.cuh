@@ -240,7 +240,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
         // (the fast path counts it as an iteration of its loop)
         steps = (!FAST2 && (ls.flags & 2u)) ? 1u : 0u;
     };
-    // the lanes in `want` take consecutive playout indices (all lanes call)
+    // the lanes in `want` take consecutive playout indices (all lanes call);
+    // once a take comes back short the pool is empty for good (dry, warp-uniform)
+    bool dry = false;
     auto take = [&](bool want) -> uint32_t {
         const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
         uint32_t base = 0;
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
             const int leader = __ffs(m) - 1;
             if ((int)lane == leader) base = (uint32_t)atomicAdd(&s_next, __popc(m));
             base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            dry = base + (uint32_t)__popc(m) >= total;
         }
         return base + (uint32_t)__popc(m & ((1u << lane) - 1u));
     };
@@ -288,7 +291,9 @@ __global__ void __launch_bounds__(1024, FAST2 ? 2 : 1)
                 ended = true;
             }
         }
-        if (__any_sync(0xFFFFFFFFu, ended)) {
+        if (dry) {
+            busy = busy && !ended;
+        } else if (__any_sync(0xFFFFFFFFu, ended)) {
             const uint32_t q = take(ended);
             if (ended) {
                 busy = q < total;
