@@ -178,25 +178,21 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
 // given as 8 partial sums per row (the output layer folded into layer 3):
 // z[r] = b4[r] + parts[0][r] + ... + parts[7][r].
 __global__ void softmax_head_kernel(const float* parts, const float* b4, const dvc_state* states, int n, float* out) {
-    // eight lanes per row, one partial vector each (coalesced loads); the
-    // row's sum is taken in the fixed order b4 + parts[0] + ... + parts[7]
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(gid >> 3), part = (int)(gid & 7), lane = threadIdx.x & 31;
-    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (row < n) q = reinterpret_cast<const float4*>(parts)[(size_t)row * kHeadParts + part];
-    float4 z = make_float4(b4[0], b4[1], b4[2], b4[3]);
-#pragma unroll
-    for (int p = 0; p < kHeadParts; ++p) {
-        const int src = (lane & ~7) + p;
-        z.x += __shfl_sync(0xFFFFFFFFu, q.x, src);
-        z.y += __shfl_sync(0xFFFFFFFFu, q.y, src);
-        z.z += __shfl_sync(0xFFFFFFFFu, q.z, src);
-        z.w += __shfl_sync(0xFFFFFFFFu, q.w, src);
-    }
-    if (row >= n || part != 0) return;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
     const dvc_state& s = states[row];
     const int P = (s.nplayers >= 2 && s.nplayers <= 4) ? s.nplayers : 2;
     const int cur = s.cur < P ? s.cur : 0;
+    const float4* pp = reinterpret_cast<const float4*>(parts) + (size_t)row * kHeadParts;
+    float4 z = make_float4(b4[0], b4[1], b4[2], b4[3]);
+#pragma unroll
+    for (int p = 0; p < kHeadParts; ++p) {
+        const float4 q = pp[p];
+        z.x += q.x;
+        z.y += q.y;
+        z.z += q.z;
+        z.w += q.w;
+    }
     const float zz[4] = {z.x, z.y, z.z, z.w};
     float mx = zz[0];
     for (int r = 1; r < P; ++r) mx = fmaxf(mx, zz[r]);
@@ -205,13 +201,9 @@ __global__ void softmax_head_kernel(const float* parts, const float* b4, const d
         e[r] = expf(zz[r] - mx);
         sum += e[r];
     }
-    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float* o = out + (size_t)row * 4;
+    o[0] = o[1] = o[2] = o[3] = 0.0f;
     for (int r = 0; r < P; ++r) o[(cur + r) % P] = e[r] / sum;
-    float* dst = out + (size_t)row * 4;
-    dst[0] = o[0];
-    dst[1] = o[1];
-    dst[2] = o[2];
-    dst[3] = o[3];
 }
 
 // Cross-entropy against soft labels (absolute seats) and dL/dlogits / n.
@@ -641,7 +633,7 @@ int dvc_value_eval(dvc_ctx* c, const dvc_state* d_leaves, int n, float* d_winpro
     if (int rc = ensure_work(c, npad)) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
-    softmax_head_kernel<<<(int)(((long long)n * 8 + 255) / 256), 256, 0, st>>>(c->vnet->L, c->vnet->b4p, d_leaves, n, d_winprob);
+    softmax_head_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, c->vnet->b4p, d_leaves, n, d_winprob);
     return check_launch(c, "softmax_head_kernel");
 }
 
@@ -809,7 +801,7 @@ int dvc_value_forward_probs(dvc_ctx* c, const dvc_state* d_leaves, int n, float*
     const int npad = (n + 127) / 128 * 128;
     if (int rc = ensure_work(c, npad)) return rc;
     if (int rc = forward(c, d_leaves, n, npad, false, st)) return rc;
-    softmax_head_kernel<<<(int)(((long long)n * 8 + 255) / 256), 256, 0, st>>>(c->vnet->L, c->vnet->b4p, d_leaves, n, d_probs);
+    softmax_head_kernel<<<(n + 127) / 128, 128, 0, st>>>(c->vnet->L, c->vnet->b4p, d_leaves, n, d_probs);
     return check_launch(c, "softmax_head_kernel");
 }
 
@@ -856,7 +848,7 @@ int dvc_value_forward_rows(dvc_ctx* c, const dvc_state* d_leaves, int n, dvc_val
                               (__nv_bfloat16*)r->H2 + o * VH, (__nv_bfloat16*)r->H3 + o * VH, L, nullptr, nullptr,
                               nullptr, true, st))
         return rc;
-    softmax_head_kernel<<<(int)(((long long)n * 8 + 255) / 256), 256, 0, st>>>(L, c->vnet->b4p, d_leaves, n, d_probs);
+    softmax_head_kernel<<<(n + 127) / 128, 128, 0, st>>>(L, c->vnet->b4p, d_leaves, n, d_probs);
     return check_launch(c, "softmax_head_kernel");
 }
 
