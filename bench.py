@@ -68,7 +68,7 @@ DRAM_PER_LAUNCH = {"select": 400_907, "rollout": 73_456, "det": 202_752}
 # x 4,096 iterations), summed over every kernel of the step by ncu
 # (graph-level capture, instruction counts only), and lanes active per warp
 # instruction (profiles/issue_slots_2p24_4096trees_24chains.md).
-ISSUE_PROFILE = {"warp_instructions_per_step": 5.6054e11, "lanes_active_per_instruction": 22.68,
+ISSUE_PROFILE = {"warp_instructions_per_step": 5.3282e11, "lanes_active_per_instruction": 23.46,
                  "source": "ncu smsp__inst_executed.sum / smsp__thread_inst_executed.sum over every kernel and "
                            "graph of one step (profiles/issue_slots_2p24_4096trees_24chains.md)"}
 
