@@ -41,6 +41,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     return d;
 }
 
+// The same for a K-major tile without swizzle: core matrices of 8 rows x 16
+// bytes; lbo = bytes between the two 8-element halves of a 16-wide K slice,
+// sbo = bytes between 8-row groups; swizzle mode 0.
+__device__ __forceinline__ uint64_t smem_desc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    return d;
+}
+
 // Instruction descriptor for kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
@@ -128,6 +140,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// Contiguous copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) from global to shared memory, completing `bytes` of the barrier's
+// transaction count.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 2-D TMA load of box (x = K offset, y = row offset) into shared memory,
 // completing `bytes` of the barrier's transaction count.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -169,7 +190,21 @@ struct GemmArgs {
     float* head_out;              // M x 8 x 4 FP32
     int wide;   // C and Cf 32-byte aligned: 256-bit stores (half the store instructions)
     int bias4;  // bias 16-byte aligned: read four floats per load
+    // K-blocked layout (M % 128 == 0): a matrix of R rows and W columns is
+    // stored as R/128 x W/16 blocks of 4 KB in that order, block (i, j) holding
+    // rows 128i.. and columns 16j.. as two halves of 8 columns, each 128 rows x
+    // 16 bytes.  A 64-wide K slice of a row tile is then 16 KB in one piece (one
+    // bulk copy, read by the MMA without swizzle), and an epilogue warp's 32
+    // rows x 8 columns are 512 contiguous bytes (one coalesced store).
+    int a_blocked;  // A in the K-blocked layout
+    int c_blocked;  // C written in the K-blocked layout
 };
+
+// Element (r, c) of a K-blocked matrix with W columns.
+__host__ __device__ inline size_t kblocked_index(int r, int c, int W) {
+    return (((size_t)(r >> 7) * (size_t)(W >> 4) + (size_t)(c >> 4)) * 2 + (size_t)((c >> 3) & 1)) * 1024 +
+           (size_t)(r & 127) * 8 + (size_t)(c & 7);
+}
 
 // 32 bytes to global memory in one instruction (p 32-byte aligned).
 __device__ __forceinline__ void st_global_v8(void* p, const uint32_t* w) {
@@ -257,7 +292,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     }
                     const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
                     mbar_expect_tx(&s_full[s], Cfg::kStage);
-                    tma_load_2d(sa, &tA, kc * kGemmBK, m0, &s_full[s]);
+                    if (a.a_blocked)  // the four 4 KB blocks of K slice kc of row tile m0 / 128
+                        bulk_load(sa, a.A + kblocked_index(m0, kc * kGemmBK, a.K), Cfg::kA, &s_full[s]);
+                    else
+                        tma_load_2d(sa, &tA, kc * kGemmBK, m0, &s_full[s]);
                     tma_load_2d(sa + Cfg::kA, &tB, kc * kGemmBK, n0, &s_full[s]);
                 }
             }
@@ -289,7 +327,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     const uint32_t sa = base + (uint32_t)s * Cfg::kStage;
 #pragma unroll
                     for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-                        const uint64_t ad = smem_desc_sw128(sa + (uint32_t)kk * 32u);
+                        const uint64_t ad = a.a_blocked ? smem_desc_noswz(sa + (uint32_t)kk * 4096u, 2048u, 128u)
+                                                        : smem_desc_sw128(sa + (uint32_t)kk * 32u);
                         const uint64_t bd = smem_desc_sw128(sa + Cfg::kA + (uint32_t)kk * 32u);
                         tc_mma(acc, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
                     }
@@ -373,7 +412,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                             __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
                             w[i] = *reinterpret_cast<uint32_t*>(&p);
                         }
-                        if (a.wide) {
+                        if (a.c_blocked) {
+                            __nv_bfloat16* blk = a.C + kblocked_index(m0, nb, a.N) + (size_t)(quarter * 32 + lane) * 8;
+                            *reinterpret_cast<uint4*>(blk) = make_uint4(w[0], w[1], w[2], w[3]);
+                            *reinterpret_cast<uint4*>(blk + 1024) = make_uint4(w[4], w[5], w[6], w[7]);
+                        } else if (a.wide) {
                             st_global_v8(a.C + (size_t)row * a.N + nb, w);
                         } else {
                             uint4* dst = reinterpret_cast<uint4*>(a.C + (size_t)row * a.N + nb);

@@ -71,7 +71,7 @@ __device__ __forceinline__ void or_bits(uint32_t* f, int pos, uint32_t field, in
 }
 
 __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, int n, int npad, __nv_bfloat16* X,
-                                                       float* Xf) {
+                                                       float* Xf, int blocked) {
     __shared__ uint32_t s_rows[256 * kFeatPitch];
     __shared__ uint4 s_lut[256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -148,6 +148,19 @@ __global__ void __launch_bounds__(256) features_kernel(const dvc_state* states, 
                 }
             }
         }
+    }
+    if (blocked) {
+        // K-blocked X (npad a multiple of 128): each thread writes its own row,
+        // 16 bytes per 8 features; the warp's 32 rows are contiguous in a block
+        __syncthreads();  // the table
+        if (X && row < npad) {
+            __nv_bfloat16* xr = X + kblocked_index(row, 0, VF);
+#pragma unroll
+            for (int b = 0; b < VF / 8; ++b)
+                *reinterpret_cast<uint4*>(xr + (size_t)(b >> 1) * 2048 + (size_t)(b & 1) * 1024) =
+                    s_lut[(f[b >> 2] >> (8 * (b & 3))) & 0xFFu];
+        }
+        return;
     }
     uint32_t* mine = s_rows + tid * kFeatPitch;
 #pragma unroll
@@ -435,11 +448,14 @@ cudaError_t launch_gemm(const GemmArgs& a, cudaStream_t st) {
 
 constexpr uint64_t kGemmWaitNs = 2000000000ull;  // 2 s: far beyond any wait of a working GEMM
 
+// a_blocked / c_blocked: A read / C written in the K-blocked layout (M a
+// multiple of 128; the inference path's activations).
 cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, __nv_bfloat16* C, float* Cf, int M,
-                 int N, int K, int act, int32_t* flags, cudaStream_t st) {
+                 int N, int K, int act, int32_t* flags, cudaStream_t st, bool a_blocked = false,
+                 bool c_blocked = false) {
     const int wide = ((uintptr_t)C % 32 == 0 && (uintptr_t)Cf % 32 == 0) ? 1 : 0;  // null counts as aligned
     GemmArgs a{A, B, bias, C, Cf, M, N, K, act, flags, kGemmWaitNs, 0, nullptr, nullptr, wide,
-               bias && (uintptr_t)bias % 16 == 0};
+               bias && (uintptr_t)bias % 16 == 0, a_blocked ? 1 : 0, c_blocked ? 1 : 0};
     if (N % 256 == 0) return launch_gemm<256>(a, st);
     if (N % 128 == 0) return launch_gemm<128>(a, st);
     if (N % 64 == 0) return launch_gemm<64>(a, st);
@@ -450,9 +466,9 @@ cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bi
 // Layer 3 with the 512 -> 4 output layer folded into its epilogue: no H3
 // written; 8 partial logit vectors per row into `parts` (rows x 8 x 4).
 cudaError_t gemm_head(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* Cf, int M,
-                      const __nv_bfloat16* W4, float* parts, int32_t* flags, cudaStream_t st) {
+                      const __nv_bfloat16* W4, float* parts, int32_t* flags, cudaStream_t st, bool a_blocked) {
     GemmArgs a{A,     B,  bias, nullptr, Cf, M, VH, VH, kActGelu, flags, kGemmWaitNs, 0, W4, parts,
-               (uintptr_t)Cf % 32 == 0, bias && (uintptr_t)bias % 16 == 0};
+               (uintptr_t)Cf % 32 == 0, bias && (uintptr_t)bias % 16 == 0, a_blocked ? 1 : 0, 0};
     return launch_gemm<256>(a, st);  // N = 512: two 256-column tiles x four column groups = kHeadParts
 }
 
@@ -536,12 +552,14 @@ int forward_into(dvc_ctx* c, const dvc_state* states, int n, int npad, __nv_bflo
                  cudaStream_t st) {
     dvc_value_net* v = c->vnet;
     int32_t* fl = c->d_flags;
-    features_kernel<<<(npad + 255) / 256, 256, 0, st>>>(states, n, npad, X, nullptr);
+    // inference (head folded in): X, H1 and H2 in the K-blocked layout; training keeps them row-major
+    const bool kb = head;
+    features_kernel<<<(npad + 255) / 256, 256, 0, st>>>(states, n, npad, X, nullptr, kb ? 1 : 0);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = gemm(X, v->W1, v->master + OFF_B1, H1, Z1, npad, VH, VF, kActGelu, fl, st);
-    if (e == cudaSuccess) e = gemm(H1, v->W2, v->master + OFF_B2, H2, Z2, npad, VH, VH, kActGelu, fl, st);
+    if (e == cudaSuccess) e = gemm(X, v->W1, v->master + OFF_B1, H1, Z1, npad, VH, VF, kActGelu, fl, st, kb, kb);
+    if (e == cudaSuccess) e = gemm(H1, v->W2, v->master + OFF_B2, H2, Z2, npad, VH, VH, kActGelu, fl, st, kb, kb);
     if (head) {
-        if (e == cudaSuccess) e = gemm_head(H2, v->W3, v->master + OFF_B3, Z3, npad, v->W4, L, fl, st);
+        if (e == cudaSuccess) e = gemm_head(H2, v->W3, v->master + OFF_B3, Z3, npad, v->W4, L, fl, st, kb);
     } else {
         if (e == cudaSuccess) e = gemm(H2, v->W3, v->master + OFF_B3, H3, Z3, npad, VH, VH, kActGelu, fl, st);
         if (e == cudaSuccess) e = gemm(H3, v->W4, v->b4p, nullptr, L, npad, VO, VH, kActNone, fl, st);
@@ -618,7 +636,7 @@ int dvc_value_features(dvc_ctx* c, const dvc_state* d_states, int n, float* d_ou
     if (n == 0) return DVC_OK;
     if (!is_device_ptr(d_out, c->device)) return fail(c, DVC_E_INVALID, "dvc_value_features: d_out must be device memory");
     if (int rc = set_device(c)) return rc;
-    features_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_states, n, n, nullptr, d_out);
+    features_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_states, n, n, nullptr, d_out, 0);
     return check_launch(c, "features_kernel");
 }
 
