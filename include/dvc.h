@@ -131,7 +131,7 @@ typedef struct dvc_config {
     int32_t max_predraw;      /* root generation: post-deal draws uniform in 0..max_predraw */
     int32_t max_revealed;     /* root generation: reject histories with more face-up tiles per player */
     uint32_t cont_thr;        /* see above */
-    double c_uct;             /* sqrt(2) */
+    double c_uct;             /* sqrt(2); UCB1 runs in IEEE single precision with c rounded to float */
     int32_t d_max;            /* 8 */
     int32_t playouts;         /* playouts per leaf in dvc_mcts_step (leaf parallelism) */
     int32_t policy;           /* playout guesses: 0 uniform (default), 1 ordering-aware (see above) */
@@ -214,8 +214,8 @@ int dvc_play_move(dvc_ctx* ctx, dvc_state* d_states, int n, const int32_t* d_act
  * h_budgets[t] iterations (one node per iteration at most; 0..2^24) and
  * streams keyed (seed, h_tree_ids ? h_tree_ids[t] : t).  d_roots is copied
  * on `stream`; h_budgets and h_tree_ids are host arrays read during the call.
- * Device memory per tree: a node arena of 641 + 4 * budget 48-byte slots
- * (node 16 B, cached UCB1 terms 24 B, child link 4 B, creation stamp 4 B;
+ * Device memory per tree: a node arena of 641 + 4 * budget 36-byte slots
+ * (node 16 B, cached UCB1 terms 12 B, child link 4 B, creation stamp 4 B;
  * vanilla: 1 + 5 * budget slots, plus a plausible-set table of 2 * budget
  * 20-byte cells), a
  * determinization table of 2,048 cells (2 players) or 32,768 cells (3-4

@@ -108,8 +108,8 @@ def lib():
         cfgp = ctypes.POINTER(_Cfg)
         L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.or_philox4x32_10.restype = None
-        L.or_ln.argtypes = [ctypes.c_double]
-        L.or_ln.restype = ctypes.c_double
+        L.or_lnf.argtypes = [ctypes.c_float]
+        L.or_lnf.restype = ctypes.c_float
         L.or_init_states.argtypes = [cfgp, ctypes.c_uint64, ctypes.c_int, u8p]
         L.or_init_states.restype = ctypes.c_int
         L.or_legal_count.argtypes = [u8p]
@@ -178,8 +178,9 @@ def philox4x32_10(ctr, key):
     return [int(v) for v in o]
 
 
-def ln(x: float) -> float:
-    return lib().or_ln(float(x))
+def lnf(x: float) -> float:
+    """The UCT logarithm, in IEEE single precision (argument rounded to float)."""
+    return lib().or_lnf(float(x))
 
 
 def init_states(cfg: OracleConfig, seed: int, n: int) -> np.ndarray:

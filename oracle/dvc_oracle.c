@@ -26,7 +26,7 @@
  *   root-parallel merge .......... Sec. III-B
  *   Philox-4x32-10 ............... Salmon, Moraes, Dror, Shaw, "Parallel Random
  *                                  Numbers: As Easy as 1, 2, 3", SC'11
- *   ln for UCT ................... argument reduction to [sqrt(1/2), sqrt(2))
+ *   ln for UCT (float) ........... argument reduction to [sqrt(1/2), sqrt(2))
  *                                  and ln m = 2 atanh((m-1)/(m+1)) by its
  *                                  Taylor series (classic Cody-Waite style)
  *
@@ -919,33 +919,36 @@ int or_legal_actions(const uint8_t* state, int policy, int32_t* codes) {
 
 /* --------------------------------------------------------------------- UCT */
 
-/* Natural log: x = m * 2^e with m in [sqrt(1/2), sqrt(2)); ln x = e ln 2 +
- * 2 atanh(z), z = (m-1)/(m+1), the series z + z^3/3 + ... evaluated by Horner
- * from the 23rd power down.  Plain IEEE double operations in a fixed order. */
-double or_ln(double x) {
-    union { double d; uint64_t u; } v;
-    v.d = x;
-    int e = (int)((v.u >> 52) & 0x7FF) - 1023;
-    v.u = (v.u & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
-    double m = v.d;
-    if (m > 1.4142135623730951) {
-        m = m * 0.5;
+/* Natural log in IEEE single precision: x = m * 2^e with m in
+ * [sqrt(1/2), sqrt(2)); ln x = e ln 2 + 2 atanh(z), z = (m-1)/(m+1), the
+ * series z + z^3/3 + ... + z^11/11 (|z| <= 0.1716, so the next term is below
+ * 2^-30 of the sum) evaluated by Horner from the 11th power down.  Plain
+ * float operations in a fixed order; ln 2 is the float nearest to it. */
+float or_lnf(float x) {
+    union { float f; uint32_t u; } v;
+    v.f = x;
+    int e = (int)((v.u >> 23) & 0xFF) - 127;
+    v.u = (v.u & 0x007FFFFFu) | 0x3F800000u;
+    float m = v.f;
+    if (m > 1.41421354f) {
+        m = m * 0.5f;
         e = e + 1;
     }
-    double z = (m - 1.0) / (m + 1.0);
-    double z2 = z * z;
-    double p = 1.0 / 23.0;
-    for (int k = 10; k >= 0; k--) p = p * z2 + 1.0 / (double)(2 * k + 1);
-    double lnm = 2.0 * (z * p);
-    return (double)e * 0.6931471805599453 + lnm;
+    float z = (m - 1.0f) / (m + 1.0f);
+    float z2 = z * z;
+    float p = 1.0f / 11.0f;
+    for (int k = 4; k >= 0; k--) p = p * z2 + 1.0f / (float)(2 * k + 1);
+    float lnm = 2.0f * (z * p);
+    return (float)e * 0.693147182f + lnm;
 }
 
-/* Score of a child (UCB1 with visits counted in playouts):
+/* Score of a child (UCB1 with visits counted in playouts), in IEEE single
+ * precision:
  *   mean = wins / n;  explore = (c * sqrt(ln N)) * (1 / sqrt(n));  score = mean + explore
  * with N the parent's visits, evaluated in exactly this order. */
-static double uct_score(double c_sqrt_lnN, int32_t w, int32_t n) {
-    double mean = (double)w / (double)n;
-    double rs = 1.0 / sqrt((double)n);
+static float uct_score(float c_sqrt_lnN, int32_t w, int32_t n) {
+    float mean = (float)w / (float)n;
+    float rs = 1.0f / sqrtf((float)n);
     return mean + c_sqrt_lnN * rs;
 }
 
@@ -1069,14 +1072,14 @@ static int mcts_run(const or_config* cfg, const uint8_t* root_packed, uint64_t s
                 mover[np++] = who;
                 break;
             }
-            double lnN = or_ln((double)t.visits[node]);
-            double csl = cfg->c_uct * sqrt(lnN);
+            float lnN = or_lnf((float)t.visits[node]);
+            float csl = (float)cfg->c_uct * sqrtf(lnN);
             int best = -1, best_rank = 0;
-            double best_score = 0.0;
+            float best_score = 0.0f;
             for (int c = t.child[node]; c >= 0; c = t.sib[c]) {
                 int code = t.action[c];
                 if (!action_is_legal(&s, code)) continue;
-                double sc = uct_score(csl, t.wins[c], t.visits[c]);
+                float sc = uct_score(csl, t.wins[c], t.visits[c]);
                 int rank = canon_rank(code, s.cur, s.P);
                 if (best < 0 || sc > best_score || (sc == best_score && rank < best_rank)) {
                     best = c; best_score = sc; best_rank = rank;

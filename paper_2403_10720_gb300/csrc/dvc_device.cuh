@@ -940,35 +940,29 @@ __device__ __forceinline__ void playout_begin(G& g, R& r, uint32_t cont_thr) {
 }
 
 // ------------------------------------------------------------------- UCT
-// ln(x), x >= 1: x = m 2^e with m in [sqrt(1/2), sqrt(2)); ln x = e ln2 +
-// 2 atanh(z), z = (m-1)/(m+1), by the atanh series up to z^23 in Horner form.
-// Every operation is an explicitly rounded IEEE double op (no contraction).
-__device__ __forceinline__ double ln_series(double x) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    int e = (int)((bits >> 52) & 0x7FFull) - 1023;
-    double m = __longlong_as_double((long long)((bits & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
-    if (m > 1.4142135623730951) {
-        m = __dmul_rn(m, 0.5);
+// ln(x), x >= 1, in IEEE single precision: x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)); ln x = e ln2 + 2 atanh(z), z = (m-1)/(m+1), by the
+// atanh series up to z^11 in Horner form (|z| <= 0.1716: the next term is
+// below 2^-30 of the sum).  Every operation is an explicitly rounded IEEE
+// float op (no contraction); ln2 is the float nearest to it.
+__device__ __forceinline__ float ln_series(float x) {
+    const uint32_t bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421354f) {
+        m = __fmul_rn(m, 0.5f);
         e += 1;
     }
-    const double z = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
-    const double z2 = __dmul_rn(z, z);
+    const float z = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float z2 = __fmul_rn(z, z);
     // 1/(2k+1) as compile-time constants: the compiler rounds each quotient
     // correctly, exactly as the runtime IEEE division would
-    constexpr double inv[12] = {1.0 / 1.0,  1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0,  1.0 / 11.0,
-                                1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0, 1.0 / 23.0};
-    double p = inv[11];
+    constexpr float inv[6] = {1.0f / 1.0f, 1.0f / 3.0f, 1.0f / 5.0f, 1.0f / 7.0f, 1.0f / 9.0f, 1.0f / 11.0f};
+    float p = inv[5];
 #pragma unroll
-    for (int k = 10; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, z2), inv[k]);
-    const double lnm = __dmul_rn(2.0, __dmul_rn(z, p));
-    return __dadd_rn(__dmul_rn((double)e, 0.6931471805599453), lnm);
-}
-
-// UCB1 score: wins/n + (c sqrt(ln N)) * (1/sqrt(n)).
-__device__ __forceinline__ double uct_score(double c_sqrt_lnN, int32_t w, int32_t n) {
-    const double mean = __ddiv_rn((double)w, (double)n);
-    const double rs = __ddiv_rn(1.0, __dsqrt_rn((double)n));
-    return __dadd_rn(mean, __dmul_rn(c_sqrt_lnN, rs));
+    for (int k = 4; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, z2), inv[k]);
+    const float lnm = __fmul_rn(2.0f, __fmul_rn(z, p));
+    return __fadd_rn(__fmul_rn((float)e, 0.693147182f), lnm);
 }
 
 }  // namespace dvc

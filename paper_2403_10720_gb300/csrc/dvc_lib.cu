@@ -72,8 +72,8 @@ struct dvc_forest {
     int trees_per_cta;       // trees per CTA (fused kernel and pipeline rollouts)
     int warps_per_cta;       // 0: default
     int engine;              // 1: fused lockstep kernel, 2: three-kernel pipeline
-    double2* ucb;
-    double* csl;
+    float2* ucb;
+    float* csl;
     uint4* set_key;      // vanilla: plausible-set tables (2 * budget cells per tree)
     int32_t* set_slot;
     PipeBufs pipe;
@@ -697,7 +697,7 @@ ForestDev dev_of(dvc_forest* f) {
 SearchParams params_of(const dvc_forest* f) {
     SearchParams sp;
     sp.seed = f->seed;
-    sp.c_uct = f->ctx->cfg.c_uct;
+    sp.c_uct = (float)f->ctx->cfg.c_uct;  // rounded to nearest, as the UCB1 arithmetic is single precision
     sp.d_max = f->ctx->cfg.d_max;
     sp.playouts = f->ctx->cfg.playouts;
     sp.cont_thr = f->ctx->cfg.cont_thr;
@@ -988,7 +988,7 @@ int dvc_forest_create(dvc_ctx* c, int n, const dvc_state* d_roots, const int32_t
         alloc((void**)&f->tables, sizeof(unsigned long long) * (size_t)f->table_cap * n) &&
         alloc((void**)&f->nodes, sizeof(Node) * (size_t)slots) && alloc((void**)&f->link, sizeof(int32_t) * (size_t)slots) &&
         alloc((void**)&f->created, sizeof(int32_t) * (size_t)slots) && alloc((void**)&f->order, sizeof(int32_t) * n) &&
-        alloc((void**)&f->ucb, sizeof(double2) * (size_t)slots) && alloc((void**)&f->csl, sizeof(double) * (size_t)slots) &&
+        alloc((void**)&f->ucb, sizeof(float2) * (size_t)slots) && alloc((void**)&f->csl, sizeof(float) * (size_t)slots) &&
         alloc((void**)&f->pipe.leaf, sizeof(dvc_state) * n) && alloc((void**)&f->pipe.path, sizeof(int32_t) * kPathMax * n) &&
         alloc((void**)&f->pipe.mover, (size_t)kPathMax * n) && alloc((void**)&f->pipe.np, sizeof(int32_t) * n) &&
         alloc((void**)&f->pipe.wins, sizeof(int32_t) * 4 * n) && alloc((void**)&f->pipe.step_end, sizeof(int32_t) * n) &&
@@ -1623,11 +1623,11 @@ struct ServerLane {
 };
 
 // Device bytes of one search slot of context c sized for max_budget
-// iterations: node arena (48 B per slot: node, UCB terms, link, creation
+// iterations: node arena (36 B per slot: node, UCB terms, link, creation
 // stamp), counting table, plan, meta and pipeline buffers (determinizations
 // sampled ahead included), plus the lane's staging per slot.
 size_t server_slot_bytes(const dvc_ctx* c, int max_budget) {
-    const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 48;
+    const size_t arena = (size_t)(1 + kRootReserve + 4LL * max_budget) * 36;
     const size_t table = (size_t)(c->cfg.nplayers == 2 ? kDetMaxCells2p : kDetMaxCells) * 8;
     return arena + table + sizeof(DetPlan) + sizeof(TreeMeta) + sizeof(Descent) +
            (sizeof(dvc_state) + sizeof(uint4)) * kDetAhead + 256;

@@ -32,8 +32,8 @@ struct ForestDev {
     Node* nodes;
     int32_t* link;
     int32_t* created;
-    double2* ucb;  // per slot: wins/n, 1/sqrt(n)
-    double* csl;   // per slot: c * sqrt(ln n)
+    float2* ucb;  // per slot: wins/n, 1/sqrt(n)
+    float* csl;   // per slot: c * sqrt(ln n)
     int32_t* flags;
     unsigned long long* words;
     uint4* set_key;    // vanilla: plausible-set tables of all trees (TreeMeta::set_off)

@@ -108,7 +108,7 @@ constexpr int32_t kRootReserve = 640;
 
 struct SearchParams {
     uint64_t seed;
-    double c_uct;
+    float c_uct;  // UCB1 exploration constant, rounded to float
     int32_t d_max;
     int32_t playouts;
     uint32_t cont_thr;
@@ -150,7 +150,7 @@ struct Descent {
 // node is the first step below the root; a set not seen before is this
 // iteration's expansion (act = kSet) and its leaf is the determinized root.
 __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* nodes, const int32_t* link,
-                                        const double2* ucb, const double* csl_of, const TreeMeta& tm,
+                                        const float2* ucb, const float* csl_of, const TreeMeta& tm,
                                         const SearchParams& sp, uint32_t it, int32_t* path, uint8_t* mover,
                                         uint32_t* E, Descent& d, const uint4* tree0 = nullptr,
                                         const SetTable& st = SetTable{nullptr, nullptr, 0u}) {
@@ -197,14 +197,14 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         // node and its exploration term; below, each child with its UCB1
         // terms, and the next block's start before this block is scanned
         const Node nd = nodes[d.node];
-        const double csl_node = csl_of[d.node];  // any slot's entry exists; used only if it has children
+        const float csl_node = csl_of[d.node];  // any slot's entry exists; used only if it has children
         const uint32_t nchild = nd.meta >> 12;
         const uint32_t cur = d.s.cur;
         const uint32_t U = d.s.tmask & ~d.s.hand(cur) & ~d.s.rev;
         for (uint32_t e = lane; e < 104u; e += 32u) E[e] = 0u;
         __syncwarp();
-        const double csl = nchild ? csl_node : 0.0;
-        double best_sc = -1.0;
+        const float csl = nchild ? csl_node : 0.0f;
+        float best_sc = -1.0f;
         uint32_t best_rank = 0xFFFFFFFFu;
         int32_t best_slot = -1;
         uint32_t best_code = 0;
@@ -220,13 +220,13 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
             const int32_t next_blk = seen + cnt < nchild ? link[blk] : -1;
             for (uint32_t e = lane; e < cnt; e += 32u) {
                 const Node ch = nodes[blk + (int32_t)e];
-                const double2 u = ucb[blk + (int32_t)e];  // set by the child's first backprop
+                const float2 u = ucb[blk + (int32_t)e];  // set by the child's first backprop
                 const uint32_t code = ch.meta & 0xFFFu;
                 const uint32_t q = code >> 10, sl = (code >> 5) & 31u, x = code & 31u;
                 stop_child |= code == kStop;
                 if (code != kStop && sl < 26u) atomicOr(&E[q * 26u + sl], 1u << x);
                 if (action_legal(d.s, code)) {
-                    const double sc = __dadd_rn(u.x, __dmul_rn(csl, u.y));
+                    const float sc = __fadd_rn(u.x, __fmul_rn(csl, u.y));
                     const uint32_t rk = canon_rank(code, cur, d.s.np);
                     if (best_slot < 0 || sc > best_sc || (sc == best_sc && rk < best_rank)) {
                         best_sc = sc;
@@ -284,7 +284,7 @@ __device__ __forceinline__ void descend(const G& det, uint32_t obs, const Node* 
         // UCB1 argmax over lanes: higher score, then lower canonical rank
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double osc = __shfl_xor_sync(0xFFFFFFFFu, best_sc, o);
+            const float osc = __shfl_xor_sync(0xFFFFFFFFu, best_sc, o);
             const uint32_t ork = __shfl_xor_sync(0xFFFFFFFFu, best_rank, o);
             const int32_t osl = __shfl_xor_sync(0xFFFFFFFFu, best_slot, o);
             const uint32_t ocd = __shfl_xor_sync(0xFFFFFFFFu, best_code, o);
@@ -365,9 +365,9 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 
 // Backpropagation (Sec. II-B): every node on the path gains `playouts` visits
 // and the playouts won by the seat that moved into it.
-__device__ __forceinline__ void backprop(Node* nodes, double2* ucb, double* csl, const int32_t* path,
+__device__ __forceinline__ void backprop(Node* nodes, float2* ucb, float* csl, const int32_t* path,
                                          const uint8_t* mover, int32_t np, const int32_t* wins, int32_t playouts,
-                                         double c_uct) {
+                                         float c_uct) {
     const uint32_t lane = threadIdx.x & 31u;
     for (int32_t e = (int32_t)lane; e < np; e += 32) {
         const int32_t slot = path[e];
@@ -376,9 +376,9 @@ __device__ __forceinline__ void backprop(Node* nodes, double2* ucb, double* csl,
         const int32_t w = n->wins + wins[mover[e]];
         n->visits = v;
         n->wins = w;
-        const double dv = (double)v;
-        ucb[slot] = make_double2(__ddiv_rn((double)w, dv), __ddiv_rn(1.0, __dsqrt_rn(dv)));
-        csl[slot] = __dmul_rn(c_uct, __dsqrt_rn(ln_series(dv)));
+        const float dv = __int2float_rn(v);
+        ucb[slot] = make_float2(__fdiv_rn(__int2float_rn(w), dv), __fdiv_rn(1.0f, __fsqrt_rn(dv)));
+        csl[slot] = __fmul_rn(c_uct, __fsqrt_rn(ln_series(dv)));
     }
 }
 

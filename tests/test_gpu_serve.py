@@ -60,7 +60,7 @@ def test_result_same_alone_and_in_the_mix(dvc):
 def test_admission_by_memory(dvc):
     ctx = dvc.Context(dvc.Config(**KW), 0)
     roots = ctx.dvc_init_states(3, 50).cpu().numpy()
-    per_slot = (1 + 640 + 4 * 256) * 48 + 2048 * 8 + 1024
+    per_slot = (1 + 640 + 4 * 256) * 36 + 2048 * 8 + 1024
     sv = dvc.Server(ctx, 10 * per_slot, 256, seed=2)
     st = sv.dvc_server_stats()
     assert 5 <= st["rollout_slots"] <= 10

@@ -39,19 +39,28 @@ def test_philox_words_uniform():
     assert chisquare(bins).pvalue > 1e-4
 
 
+def _f32(x):
+    return struct.unpack("<f", struct.pack("<f", x))[0]
+
+
 def _ulp_diff(a, b):
-    ia = struct.unpack("<q", struct.pack("<d", a))[0]
-    ib = struct.unpack("<q", struct.pack("<d", b))[0]
+    ia = struct.unpack("<i", struct.pack("<f", a))[0]
+    ib = struct.unpack("<i", struct.pack("<f", b))[0]
     return abs(ia - ib)
 
 
 def test_ln_against_libm():
-    xs = list(range(1, 5000)) + [int(v) for v in np.geomspace(5000, 4e9, 3000)]
-    worst = max(_ulp_diff(oracle.ln(float(x)), math.log(float(x))) for x in xs if x > 1)
-    assert oracle.ln(1.0) == 0.0
-    assert worst <= 2, worst
+    # the UCT logarithm works in IEEE single precision: within 1 ulp of the
+    # correctly rounded libm value at every visit count tried
+    xs = list(range(1, 20000)) + [int(v) for v in np.geomspace(20000, 4e9, 5000)]
+    worst = max(_ulp_diff(oracle.lnf(_f32(float(x))), _f32(math.log(_f32(float(x))))) for x in xs if x > 1)
+    assert oracle.lnf(1.0) == 0.0
+    assert worst <= 1, worst
 
 
 def test_ln_reduction_boundaries():
-    for x in [math.sqrt(2.0), 2.0 * math.sqrt(2.0), 3.0, 1.5, 1e6 + 1.0, 2.0 ** 40 + 7]:
-        assert abs(oracle.ln(x) - math.log(x)) <= 4e-16 * max(1.0, abs(math.log(x)))
+    # both sides of the sqrt(2) switch of the mantissa, powers of two, large counts
+    for x in [math.sqrt(2.0), 1.4142135, 1.4142137, 2.0 * math.sqrt(2.0), 2.0, 4.0, 3.0, 1.5, 1e6 + 1.0,
+              2.0 ** 40 + 7]:
+        xf = _f32(x)
+        assert _ulp_diff(oracle.lnf(xf), _f32(math.log(xf))) <= 1, x
