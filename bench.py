@@ -63,12 +63,12 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # rollout CTA), from ncu captures (cold cache) summarised under profiles/
 # (dram_per_launch_2p24_4096trees_24chains.md).
 PROFILED_SHAPE = (24, 2, 16)
-DRAM_PER_LAUNCH = {"select": 400_907, "rollout": 73_456, "det": 202_752}
+DRAM_PER_LAUNCH = {"select": 346_507, "rollout": 74_384, "det": 200_512}
 # Warp instructions per step of the same workload at that shape (4,096 trees
 # x 4,096 iterations), summed over every kernel of the step by ncu
 # (graph-level capture, instruction counts only), and lanes active per warp
 # instruction (profiles/issue_slots_2p24_4096trees_24chains.md).
-ISSUE_PROFILE = {"warp_instructions_per_step": 5.3282e11, "lanes_active_per_instruction": 23.46,
+ISSUE_PROFILE = {"warp_instructions_per_step": 5.2416e11, "lanes_active_per_instruction": 23.73,
                  "source": "ncu smsp__inst_executed.sum / smsp__thread_inst_executed.sum over every kernel and "
                            "graph of one step (profiles/issue_slots_2p24_4096trees_24chains.md)"}
 
