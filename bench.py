@@ -5,8 +5,10 @@ One step = one full decision batch of the 2-player/24-tile workload: 4,096
 mid-game roots, each searched with 4,096 UCT iterations x 256 leaf playouts
 (1,048,576 playouts per decision, 4.29e9 per step).  The step runs
 dvc_forest_reset (re-plan and re-fill the determinization tables, reset the
-trees), dvc_mcts_step (the fused select/expand/rollout/backprop kernel) and
-dvc_root_stats (decisions).
+trees), dvc_mcts_step (the CUDA-graph pipeline of determinization, select and
+rollout kernels over overlapping chains) and dvc_root_stats (decisions).  The
+timed steps keep no work counts; one more, untimed step of the same search
+counts the random words and game steps.
 
 Prints one JSON line.  `value` is playouts/s over all ranks (device-timed,
 roots resident in HBM); `e2e` is the same metric through the public API with
