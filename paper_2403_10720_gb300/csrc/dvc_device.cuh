@@ -591,7 +591,11 @@ __device__ __forceinline__ int step_gen(GR& g, R& r, uint32_t cont_thr, const ui
         }
         if (cont_thr != 0u && r.next() < cont_thr) return kGuessAgain;
     } else {  // wrong: the mover reveals its drawn tile, else its leftmost face-down one
-        const uint32_t t = g.drawn != kNone ? g.drawn : hidden_in(g, g.a0, 0u);
+        uint32_t t = g.drawn;
+        if (t == kNone) {  // the leftmost face-down tile: the lowest one unless a joker is face down
+            const uint32_t hid = g.a0 & ~g.rev;
+            t = (hid & kJokerMask) ? hidden_in(g, g.a0, 0u) : (uint32_t)__ffs(hid) - 1u;
+        }
         g.rev |= 1u << t;
         if (!(g.a0 & ~g.rev)) g.alive &= ~(1u << g.cur);
         if (__popc(g.alive) == 1) {
