@@ -48,8 +48,7 @@ from paper_2403_10720_gb300.workloads import BATCHED, UNEVEN  # noqa: E402
 # unseen set and two population counts, the (slot, identity) split by one
 # multiply-high and a reciprocal multiply, the slot's tile by a 12-bit
 # select; the check, the reveal and the game-over test; the next seat's draw:
-# pool, count, multiply-high, select, insert).  Each step is listed in
-# the design doc section 7.
+# pool, count, multiply-high, select, insert).
 OPS_PER_WORD = {"alu": 15, "mul": 10, "popc": 0}
 OPS_PER_STEP_2P24 = {"alu": 48, "mul": 5, "popc": 6}
 # Per-SM, per-clock throughput of each class (CUDA C++ Programming Guide,
@@ -62,17 +61,17 @@ VALUE_MACS_PER_LEAF = 640 * 512 + 2 * 512 * 512 + 512 * 4  # dense layers of the
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # DRAM bytes per launch of the pipeline's kernels at the default shape of the
 # 4,096-tree workload (24 chains of 170 or 171 trees; 2 trees x 16 warps per
-# rollout CTA), from ncu captures (cold cache) summarised under profiles/
-# (dram_per_launch_2p24_4096trees_24chains.md).
+# rollout CTA), from ncu captures (cold cache) of the counting-free kernels,
+# summarised under profiles/ with their commands.
 PROFILED_SHAPE = (24, 2, 16)
 DRAM_PER_LAUNCH = {"select": 346_507, "rollout": 74_384, "det": 200_512}
 # Warp instructions per step of the same workload at that shape (4,096 trees
 # x 4,096 iterations), summed over every kernel of the step by ncu
 # (graph-level capture, instruction counts only), and lanes active per warp
-# instruction (profiles/issue_slots_2p24_4096trees_24chains.md).
+# instruction; the capture is summarised under profiles/ with its command.
 ISSUE_PROFILE = {"warp_instructions_per_step": 5.2416e11, "lanes_active_per_instruction": 23.73,
                  "source": "ncu smsp__inst_executed.sum / smsp__thread_inst_executed.sum over every kernel and "
-                           "graph of one step (profiles/issue_slots_2p24_4096trees_24chains.md)"}
+                           "graph of one counting-free step at this shape (ncu summary under profiles/)"}
 
 
 def _env_int(k, d):
