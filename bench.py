@@ -449,7 +449,8 @@ def run_ours(args, w):
 
 
 def measure_uneven(w, steps=1, warmup=1, trees=0, iterations=0, shape=None, warmup_cap=64):
-    """The uneven forest (config 3): every tree searches its whole budget; one
+    """The uneven forest (16,384 four-player joker trees, budgets 1k-100k):
+    every tree searches its whole budget; one
     step = all trees.  The launch shape comes from the autotuner unless given;
     the tail of long budgets runs on the fused engine (autotune.step_with_tail).
     Warm-up steps run with budgets capped at warmup_cap iterations (graph
@@ -468,7 +469,8 @@ def measure_uneven(w, steps=1, warmup=1, trees=0, iterations=0, shape=None, warm
     if shape is None:
         shape = autotune.tune(dvc, ctx, roots, budgets, w.seed, scale=0.02)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    cut = autotune.tail_start(budgets, sms)
+    cut = autotune.tail_start(budgets, sms, autotune.PACK_TREES_PER_SM)
+    cut_tail = autotune.tail_start(budgets, sms)
     if warmup:
         capped = np.minimum(budgets, warmup_cap).astype(np.int32)
         f0 = dvc.Forest(ctx, roots, capped, w.seed)
@@ -490,7 +492,7 @@ def measure_uneven(w, steps=1, warmup=1, trees=0, iterations=0, shape=None, warm
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         forest.dvc_forest_reset()
-        # the tuned shape while many trees run, one tree per fused CTA for the tail
+        # the tuned shape while many trees run, then packed fused CTAs, then one tree per CTA
         autotune.step_with_tail(forest, budgets, shape, sms)
         forest.dvc_root_stats(out=stats)
         b.record()
@@ -513,12 +515,15 @@ def measure_uneven(w, steps=1, warmup=1, trees=0, iterations=0, shape=None, warm
             "words_per_playout": int(work[0].item()) / playouts, "trees": n,
             "iterations_total": int(budgets.sum()), "budget_range": [int(budgets.min()), int(budgets.max())],
             "playouts_per_leaf": w.playouts, "players": w.nplayers, "tiles": w.ntiles,
-            "launch_shape": list(shape), "tail": {"from_iteration": cut, "launch_shape": list(autotune.TAIL_SHAPE)},
+            "launch_shape": list(shape),
+            "tail": {"from_iteration": cut, "launch_shape": list(autotune.PACK_SHAPE),
+                     "repacked_every": autotune.PACK_CHUNK,
+                     "then": {"from_iteration": cut_tail, "launch_shape": list(autotune.TAIL_SHAPE)}},
             "clocks": clk}
 
 
 def run_uneven(args, w):
-    """Config 3 on its own (one JSON line)."""
+    """The uneven forest on its own (one JSON line)."""
     m = measure_uneven(w, steps=args.steps, warmup=args.warmup, trees=args.trees, iterations=args.iterations,
                        shape=(args.engine or 2, args.trees_per_cta, args.warps, args.chains)
                        if (args.engine or args.chains or args.trees_per_cta or args.warps) else None)
@@ -546,7 +551,7 @@ def _crossing(xs, ys, level=0.5):
 
 def value_vs_rollout(train_states=10_000_000, epochs=4, games=2000, rollout_budget=256,
                      value_budgets=(128, 192, 256, 384), hbm_gb=4.0):
-    """Config 4: the value network trained on the GPU (states of the 2-player
+    """Value network against playouts: the network trained on the GPU (states of the 2-player
     24-tile root generator labelled by 1,024 playouts each), its held-out
     win-probability error against rollout estimates, then games of the value
     agent at several iteration budgets against the playout agent (32 playouts
@@ -947,7 +952,7 @@ def run_scaling(args):
           flush=True)
 
 
-SERVE_VARIANTS = [  # config 5: 2-4 players, 24- and 26-tile games (26 tiles: with the two jokers)
+SERVE_VARIANTS = [  # the serving workload: 2-4 players, 24- and 26-tile games (26 tiles: with the two jokers)
     dict(nplayers=2, ntiles=24, deal=4, max_predraw=10, max_revealed=5),
     dict(nplayers=3, ntiles=24, deal=4, max_predraw=6, max_revealed=3),
     dict(nplayers=4, ntiles=24, deal=3, max_predraw=6, max_revealed=3),
@@ -958,7 +963,7 @@ SERVE_VARIANTS = [  # config 5: 2-4 players, 24- and 26-tile games (26 tiles: wi
 
 
 def serve_games(games, rate, window_s, hbm_gb, max_budget, poll_iters, value_frac=0.5, value_share_pct=35):
-    """Serving (config 5): one server over six game variants sharing an HBM
+    """Serving: one server over six game variants sharing an HBM
     budget, Poisson arrivals of move queries from `games` concurrent games,
     value and rollout modes mixed per query.  Returns the driver's dict plus
     the server's slot layout."""
@@ -991,7 +996,7 @@ def serve_games(games, rate, window_s, hbm_gb, max_budget, poll_iters, value_fra
 
 
 def run_serve(args):
-    """Config 5 on its own: Poisson arrivals of move queries from concurrent
+    """The serving workload on its own: Poisson arrivals of move queries from concurrent
     games of six variants into one device-resident server (one JSON line)."""
     out = serve_games(args.games_live, args.rate, args.window, args.hbm_gb, args.max_budget, args.poll_iters)
     print(json.dumps({

@@ -279,6 +279,21 @@ int dvc_mcts_step(dvc_forest* f, int n_iterations, int mode, void* stream);
 int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_cta, int chains);
 
 /*
+ * Which trees share a CTA, set by the caller: h_order (host, n_trees int32)
+ * is a permutation of 0 .. n_trees-1; CTA b of either engine takes the trees
+ * h_order[b * trees_per_cta ..].  n_active (0 .. n_trees; 0 = all) limits the
+ * fused engine's launches to the first n_active trees of the order -- a caller
+ * that knows which trees still have iterations left lists those first and
+ * packs trees of similar remaining budgets together; the other trees must have
+ * no iterations left in the steps that follow (they are not visited).  Results
+ * are identical for every order.  The next dvc_forest_tune that changes
+ * trees_per_cta replaces the order and, like dvc_forest_reset, clears
+ * n_active (all trees run).  Synchronises the device once.
+ * DVC_E_INVALID if h_order is not a permutation or n_active is out of range.
+ */
+int dvc_forest_order(dvc_forest* f, const int32_t* h_order, int n_active);
+
+/*
  * The same iteration split into launches, for callers that score leaves
  * themselves: dvc_mcts_select determinizes and descends, dvc_mcts_expand adds
  * the new child and writes each tree's leaf state (dvc_forest_leaves gives

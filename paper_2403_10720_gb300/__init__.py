@@ -120,6 +120,7 @@ def lib():
             "dvc_forest_counters": ([vp, vp, vp], i),
             "dvc_forest_work": ([vp, vp, vp], i),
             "dvc_forest_count_work": ([vp, i], i),
+            "dvc_forest_order": ([vp, vp, i], i),
             "dvc_root_merge": ([vp, i, vp, vp], i),
             "dvc_forest_compaction": ([vp, i, i], i),
             "dvc_tree_export": ([vp, i, vp, vp], i),
@@ -362,6 +363,15 @@ class Forest:
         out = torch.empty((self.n // K, 8), dtype=torch.int32, device=self.ctx.dev()) if out is None else out
         self.ctx._rc(lib().dvc_root_merge(self.h, K, _ptr(out), _stream(stream)), "dvc_root_merge")
         return out
+
+    def dvc_forest_order(self, order, n_active=0):
+        """Trees per CTA by a caller's permutation; the fused engine runs the first n_active (0 = all)."""
+        import numpy as np
+        o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        if o.shape != (self.n,):
+            raise ValueError("order must hold one entry per tree")
+        self.ctx._rc(lib().dvc_forest_order(self.h, o.ctypes.data_as(ctypes.c_void_p), int(n_active)),
+                     "dvc_forest_order")
 
     def dvc_forest_count_work(self, on):
         """Keep (True, the default) or skip the work counters in the playout kernels."""

@@ -83,12 +83,19 @@ def tune(dvc, ctx, roots, budgets, seed, scale=0.05, candidates=None, use_cache=
     return best
 
 
-# Below this many running trees per SM the fused engine with one tree per CTA
-# finishes an iteration sooner than the pipeline (measured on four-player
-# forests: 60 against 85 us per iteration with about 1,600 trees left, 133
-# against 108 us with about 4,000).
-TAIL_TREES_PER_SM = 12
+# The tail of an uneven forest, measured on four-player forests in chunks of
+# 2,000 iterations (budgets 1k-100k): with at most 16 running trees per SM the
+# fused engine with 4 trees x 4 warps per CTA, its CTAs filled with running
+# trees of similar remaining budgets, beats the pipeline (76 against 90 us per
+# iteration with 2,438 trees left, 64 against 85 with 1,785); with at most 5
+# per SM one tree per CTA is fastest (52 against 55 us with 770 left).  Without
+# the repacking, CTAs of several trees keep their finished trees' warps and
+# lose to one tree per CTA.
+PACK_TREES_PER_SM = 16
+PACK_SHAPE = (1, 4, 4, 0)
+TAIL_TREES_PER_SM = 5
 TAIL_SHAPE = (1, 1, 1, 0)
+PACK_CHUNK = 2000
 
 
 def tail_start(budgets, sms, per_sm=TAIL_TREES_PER_SM):
@@ -102,18 +109,42 @@ def tail_start(budgets, sms, per_sm=TAIL_TREES_PER_SM):
     return int(b[k]) if b[k] < b[0] else None
 
 
-def step_with_tail(forest, budgets, shape, sms, per_sm=TAIL_TREES_PER_SM):
+def _packed_steps(forest, budgets, done, end, chunk=PACK_CHUNK):
+    """Iterations [done, end) of a fresh forest on its current fused shape, in
+    chunks; before each, the running trees go first, longest remaining budget
+    first, so that a CTA's trees finish close together and no CTA keeps
+    finished trees."""
+    b = np.asarray(budgets, dtype=np.int64)
+    while done < end:
+        n = min(chunk, end - done)
+        rem = b - done
+        live = np.nonzero(rem > 0)[0]
+        order = np.concatenate([live[np.argsort(-rem[live], kind="stable")], np.nonzero(rem <= 0)[0]])
+        forest.dvc_forest_order(order.astype(np.int32), len(live))
+        forest.dvc_mcts_step(n)
+        done += n
+
+
+def step_with_tail(forest, budgets, shape, sms, pack_per_sm=PACK_TREES_PER_SM, tail_per_sm=TAIL_TREES_PER_SM):
     """Search a fresh forest to the end of every budget: the given launch
-    shape while many trees run, then the fused one-tree-per-CTA shape for the
-    tail of long budgets.  Results are those of any shape; re-tuning
-    synchronises the device once per switch."""
+    shape while many trees run; from at most pack_per_sm running trees per SM,
+    the fused engine with several trees per CTA, repacked every PACK_CHUNK
+    iterations; from at most tail_per_sm, one tree per CTA.  Results are those
+    of any shape and order; re-tuning and repacking synchronise the device."""
     total = int(np.max(budgets))
-    cut = tail_start(budgets, sms, per_sm)
-    if cut is None or cut <= 0 or cut >= total:
+    cut = tail_start(budgets, sms, pack_per_sm)
+    if cut is None or cut >= total:
         forest.dvc_forest_tune(*shape)
         forest.dvc_mcts_step(total)
         return
-    forest.dvc_forest_tune(*shape)
-    forest.dvc_mcts_step(cut)
-    forest.dvc_forest_tune(*TAIL_SHAPE)
-    forest.dvc_mcts_step(total - cut)
+    tail = tail_start(budgets, sms, tail_per_sm)
+    tail = total if tail is None else max(cut, min(tail, total))
+    if cut > 0:
+        forest.dvc_forest_tune(*shape)
+        forest.dvc_mcts_step(cut)
+    if tail > cut:
+        forest.dvc_forest_tune(*PACK_SHAPE)
+        _packed_steps(forest, budgets, cut, tail)
+    if total > tail:
+        forest.dvc_forest_tune(*TAIL_SHAPE)
+        _packed_steps(forest, budgets, tail, total)

@@ -1037,6 +1037,7 @@ int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream) {
     if (d_roots && !is_device_ptr(d_roots, f->ctx->device))
         return fail(f->ctx, DVC_E_INVALID, "dvc_forest_reset: d_roots must be device memory");
     if (int rc = set_device(f->ctx)) return rc;
+    f->active_prefix = 0;  // every tree has its budget again
     forest_init_kernel<<<(f->n * 32 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
         dev_of(f), f->n, d_roots, f->plans, f->tables, f->table_cap, f->ctx->cfg.nplayers, f->ctx->cfg.ntiles,
         f->pipe.np);
@@ -1422,6 +1423,7 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
         const cudaError_t e = cudaMemcpy(f->order, order.data(), sizeof(int32_t) * f->n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_tune");
         f->trees_per_cta = T;
+        f->active_prefix = 0;  // a caller's active prefix referred to the order replaced here
     }
     f->engine = eng;
     const int ch = chains ? chains : dC;
@@ -1433,6 +1435,23 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     }
     f->warps_per_cta = W;
     f->chains = ch;
+    return DVC_OK;
+}
+
+int dvc_forest_order(dvc_forest* f, const int32_t* h_order, int n_active) {
+    if (!f || !h_order) return DVC_E_INVALID;
+    if (n_active < 0 || n_active > f->n) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_order: 0 <= n_active <= trees");
+    std::vector<char> seen(f->n, 0);
+    for (int i = 0; i < f->n; ++i) {
+        const int32_t t = h_order[i];
+        if (t < 0 || t >= f->n || seen[t])
+            return fail(f->ctx, DVC_E_INVALID, "dvc_forest_order: h_order must be a permutation of the trees");
+        seen[t] = 1;
+    }
+    if (int rc = set_device(f->ctx)) return rc;
+    const cudaError_t e = cudaMemcpy(f->order, h_order, sizeof(int32_t) * f->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_order");
+    f->active_prefix = n_active;
     return DVC_OK;
 }
 

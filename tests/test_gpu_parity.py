@@ -3,7 +3,7 @@
 All inputs are seeded and synthetic.  Integer game logic and the UCT
 decisions are compared exactly (the method has no tolerance to give: states,
 win counts, visit counts and decisions are integers, and the UCT score is
-computed with the same IEEE double operations on both sides).
+computed with the same IEEE single-precision operations on both sides).
 """
 import threading
 
@@ -291,12 +291,13 @@ def test_uneven_workload_sampled(dvc):
 def test_uneven_workload_full_budgets_sampled(dvc):
     """The whole uneven forest -- 16,384 four-player joker trees, budgets
     log-uniform in 1k-100k -- searched to the end of every budget under the
-    library's schedule (the autotuned pipeline shape, then the fused
-    one-tree-per-CTA engine from the iteration at which at most 12 trees per
-    SM still run), then trees replayed by the oracle at their real budgets:
-    the largest (about 100k iterations, so the largest arenas and child
-    blocks), two that end just before and just after the engine switch, and
-    three more.  Node tables and decisions bit-exact."""
+    library's schedule (the autotuned pipeline shape; from the iteration at
+    which at most 16 trees per SM still run, fused CTAs of 4 trees repacked
+    with running trees every 2,000 iterations; from at most 5 per SM, one tree
+    per CTA), then trees replayed by the oracle at their real budgets: the
+    largest (about 100k iterations, so the largest arenas and child blocks),
+    two that end just before and just after the switch to the fused engine,
+    and three more.  Node tables and decisions bit-exact."""
     from paper_2403_10720_gb300 import autotune
     w = UNEVEN
     kw = w.config_kwargs()
@@ -307,8 +308,9 @@ def test_uneven_workload_full_budgets_sampled(dvc):
     roots = ctx.dvc_init_states(w.root_seed, n)
     forest = dvc.Forest(ctx, roots, budgets, w.seed)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    cut = autotune.tail_start(budgets, sms)
+    cut = autotune.tail_start(budgets, sms, autotune.PACK_TREES_PER_SM)   # pipeline -> packed fused CTAs
     assert cut is not None and 0 < cut < int(budgets.max())
+    assert 0 < cut < autotune.tail_start(budgets, sms) < int(budgets.max())
     autotune.step_with_tail(forest, budgets, (2, 1, 1, 16), sms)
     stats = forest.dvc_root_stats().cpu().numpy()
     ctx.dvc_check()
@@ -323,6 +325,44 @@ def test_uneven_workload_full_budgets_sampled(dvc):
     want = _oracle_trees(ocfg, oroots, w.seed, budgets, sample)
     _check_forest(forest, stats, want, sample)
     forest.close()
+
+
+@pytest.mark.parametrize("variant,engine_shape", [("4p26j", (1, 4, 4, 0)), ("2p24", (1, 3, 2, 0)),
+                                                  ("4p26j", (2, 2, 1, 3))])
+def test_caller_order_and_active_prefix(dvc, variant, engine_shape):
+    """dvc_forest_order: a forest searched in chunks, its running trees
+    repacked before each chunk (running first, longest remaining budget
+    first; the fused engine visits only those), gives the same trees and
+    decisions as one step with the default order; trees sampled against the
+    oracle.  A non-permutation or an out-of-range prefix is refused."""
+    from paper_2403_10720_gb300 import autotune
+    kw = dict(VARIANTS[variant], playouts=16)
+    ctx = _ctx(dvc, **kw)
+    n = 97
+    rng = np.random.default_rng(17)
+    budgets = rng.integers(1, 160, size=n).astype(np.int32)
+    roots = ctx.dvc_init_states(23, n)
+    a = dvc.Forest(ctx, roots, budgets, 19)
+    a.dvc_mcts_step(int(budgets.max()))
+    b = dvc.Forest(ctx, roots, budgets, 19)
+    b.dvc_forest_tune(*engine_shape)
+    autotune._packed_steps(b, budgets, 0, int(budgets.max()), chunk=37)
+    sa, sb = a.dvc_root_stats().cpu().numpy(), b.dvc_root_stats().cpu().numpy()
+    ctx.dvc_check()
+    assert (sa == sb).all() and (sb[:, 6] == budgets).all()
+    for t in (0, 48, 96):
+        assert torch.equal(a.dvc_tree_export(t), b.dvc_tree_export(t))
+    ocfg = oracle.OracleConfig(**kw)
+    oroots = oracle.init_states(ocfg, 23, n)
+    want = _oracle_trees(ocfg, oroots, 19, budgets, [int(np.argmax(budgets)), 5])
+    _check_forest(b, sb, want, [int(np.argmax(budgets)), 5])
+    bad = np.arange(n, dtype=np.int32)
+    bad[3] = 4
+    for order, k in ((bad, 0), (np.arange(n, dtype=np.int32), n + 1), (np.arange(n, dtype=np.int32), -1)):
+        with pytest.raises(dvc.DvcError):
+            b.dvc_forest_order(order, k)
+    a.close()
+    b.close()
 
 
 @pytest.mark.parametrize("variant,shape", [
