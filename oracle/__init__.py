@@ -9,7 +9,7 @@ comment above pack() in dvc_oracle.c), as numpy uint8 arrays of shape (n, 32).
 
 Pin status per function:
   philox4x32_10 ..... pinned (published known-answer vectors)
-  ln ................ pinned (libm within 2 ulp)
+  lnf ............... pinned (single precision, within 1 ulp of libm)
   init_states ....... pinned (rule invariants, deal sizes, history bounds)
   legal_count ....... pinned (88 root guesses of Sec. III-A, closed form I7)
   rollout / trace ... pinned (invariants, closed-form 1/k endgame, exact
