@@ -288,7 +288,8 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
  * no iterations left in the steps that follow (they are not visited).  Results
  * are identical for every order.  The next dvc_forest_tune that changes
  * trees_per_cta replaces the order and, like dvc_forest_reset, clears
- * n_active (all trees run).  Synchronises the device once.
+ * n_active (all trees run); h_order NULL (n_active 0) restores the default
+ * order of the current CTA size.  Synchronises the device once.
  * DVC_E_INVALID if h_order is not a permutation or n_active is out of range.
  */
 int dvc_forest_order(dvc_forest* f, const int32_t* h_order, int n_active);

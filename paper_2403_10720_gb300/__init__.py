@@ -365,7 +365,11 @@ class Forest:
         return out
 
     def dvc_forest_order(self, order, n_active=0):
-        """Trees per CTA by a caller's permutation; the fused engine runs the first n_active (0 = all)."""
+        """Trees per CTA by a caller's permutation; the fused engine runs the first n_active (0 = all).
+        order None restores the default order."""
+        if order is None:
+            self.ctx._rc(lib().dvc_forest_order(self.h, None, 0), "dvc_forest_order")
+            return
         import numpy as np
         o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
         if o.shape != (self.n,):

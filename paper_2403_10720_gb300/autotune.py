@@ -148,3 +148,4 @@ def step_with_tail(forest, budgets, shape, sms, pack_per_sm=PACK_TREES_PER_SM, t
     if total > tail:
         forest.dvc_forest_tune(*TAIL_SHAPE)
         _packed_steps(forest, budgets, tail, total)
+    forest.dvc_forest_order(None)  # the next search starts from the default order again

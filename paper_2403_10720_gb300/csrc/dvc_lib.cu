@@ -1048,6 +1048,43 @@ int dvc_forest_reset(dvc_forest* f, const dvc_state* d_roots, void* stream) {
 
 namespace {
 
+// The default tree order for CTAs of T trees: longest budget first, each to
+// the least-loaded CTA (equal budgets keep index order); host work, one copy.
+// Clears a caller's active prefix (it referred to the order replaced here).
+int set_default_order(dvc_forest* f, int T) {
+    std::vector<int32_t> order(f->n);
+    const int nc = (f->n + T - 1) / T;
+    std::vector<int> idx(f->n);
+    for (int i = 0; i < f->n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return f->h_budgets[a] > f->h_budgets[b]; });
+    std::vector<std::pair<long long, int>> heap;
+    std::vector<int> fill(nc, 0), capc(nc, T);
+    capc[nc - 1] = f->n - (nc - 1) * T;
+    for (int k = 0; k < nc; ++k) heap.push_back({0, k});
+    auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    bool even = true;
+    for (int t = 1; t < f->n; ++t) even &= f->h_budgets[t] == f->h_budgets[0];
+    for (int i : idx) {
+        if (even) break;  // equal budgets: index order
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto [ld, k] = heap.back();
+        heap.pop_back();
+        order[k * T + fill[k]++] = i;
+        if (fill[k] < capc[k]) {
+            heap.push_back({ld + f->h_budgets[i], k});
+            std::push_heap(heap.begin(), heap.end(), cmp);
+        }
+    }
+    if (even)
+        for (int i = 0; i < f->n; ++i) order[i] = i;
+    if (int rc = set_device(f->ctx)) return rc;
+    const cudaError_t e = cudaMemcpy(f->order, order.data(), sizeof(int32_t) * f->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(f->ctx, e, "forest order");
+    f->active_prefix = 0;
+    return DVC_OK;
+}
+
 int launch_fused(dvc_forest* f, int n_iterations, cudaStream_t st) {
     dvc_ctx* c = f->ctx;
     const int T = f->trees_per_cta;
@@ -1392,38 +1429,8 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
     const PoolLayout L(T, W);
     if (L.bytes > 200 * 1024) return fail(f->ctx, DVC_E_UNSUPPORTED, "dvc_forest_tune: CTA state exceeds shared memory");
     if (T != f->trees_per_cta) {
-        // re-balance the tree order for the new CTA size (host work, then one copy)
-        std::vector<int32_t> order(f->n);
-        const int nc = (f->n + T - 1) / T;
-        std::vector<int> idx(f->n);
-        for (int i = 0; i < f->n; ++i) idx[i] = i;
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return f->h_budgets[a] > f->h_budgets[b]; });
-        std::vector<std::pair<long long, int>> heap;
-        std::vector<int> fill(nc, 0), capc(nc, T);
-        capc[nc - 1] = f->n - (nc - 1) * T;
-        for (int k = 0; k < nc; ++k) heap.push_back({0, k});
-        auto cmp = [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a > b; };
-        std::make_heap(heap.begin(), heap.end(), cmp);
-        bool even = true;
-        for (int t = 1; t < f->n; ++t) even &= f->h_budgets[t] == f->h_budgets[0];
-        for (int i : idx) {
-            if (even) break;  // equal budgets: index order
-            std::pop_heap(heap.begin(), heap.end(), cmp);
-            auto [ld, k] = heap.back();
-            heap.pop_back();
-            order[k * T + fill[k]++] = i;
-            if (fill[k] < capc[k]) {
-                heap.push_back({ld + f->h_budgets[i], k});
-                std::push_heap(heap.begin(), heap.end(), cmp);
-            }
-        }
-        if (even)
-            for (int i = 0; i < f->n; ++i) order[i] = i;
-        if (int rc = set_device(f->ctx)) return rc;
-        const cudaError_t e = cudaMemcpy(f->order, order.data(), sizeof(int32_t) * f->n, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_fail(f->ctx, e, "dvc_forest_tune");
+        if (int rc = set_default_order(f, T)) return rc;
         f->trees_per_cta = T;
-        f->active_prefix = 0;  // a caller's active prefix referred to the order replaced here
     }
     f->engine = eng;
     const int ch = chains ? chains : dC;
@@ -1439,7 +1446,12 @@ int dvc_forest_tune(dvc_forest* f, int engine, int trees_per_cta, int warps_per_
 }
 
 int dvc_forest_order(dvc_forest* f, const int32_t* h_order, int n_active) {
-    if (!f || !h_order) return DVC_E_INVALID;
+    if (!f) return DVC_E_INVALID;
+    if (!h_order) {  // back to the default order of the current shape
+        if (n_active != 0) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_order: the default order runs every tree");
+        if (int rc = set_device(f->ctx)) return rc;
+        return set_default_order(f, f->trees_per_cta > 0 ? f->trees_per_cta : 1);
+    }
     if (n_active < 0 || n_active > f->n) return fail(f->ctx, DVC_E_INVALID, "dvc_forest_order: 0 <= n_active <= trees");
     std::vector<char> seen(f->n, 0);
     for (int i = 0; i < f->n; ++i) {

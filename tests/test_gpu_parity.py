@@ -361,6 +361,12 @@ def test_caller_order_and_active_prefix(dvc, variant, engine_shape):
     for order, k in ((bad, 0), (np.arange(n, dtype=np.int32), n + 1), (np.arange(n, dtype=np.int32), -1)):
         with pytest.raises(dvc.DvcError):
             b.dvc_forest_order(order, k)
+    b.dvc_forest_order(None)                                   # the default order again
+    assert dvc.lib().dvc_forest_order(b.h, None, 5) == -1     # the default order runs every tree
+    b.dvc_forest_reset()
+    b.dvc_mcts_step(int(budgets.max()))
+    assert (b.dvc_root_stats().cpu().numpy() == sa).all()
+    ctx.dvc_check()
     a.close()
     b.close()
 

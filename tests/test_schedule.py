@@ -27,8 +27,8 @@ class _Forest:
     def dvc_forest_tune(self, *shape):
         self.calls.append(("tune", shape))
 
-    def dvc_forest_order(self, order, n_active):
-        self.calls.append(("order", [int(t) for t in order], n_active))
+    def dvc_forest_order(self, order, n_active=0):
+        self.calls.append(("order", None if order is None else [int(t) for t in order], n_active))
 
     def dvc_mcts_step(self, n):
         self.calls.append(("step", n))
@@ -42,7 +42,8 @@ def test_step_with_tail_splits_the_iterations():
     # fused chunk first lists the running trees, longest remaining budget first
     assert f.calls == [("tune", (2, 1, 1, 8)), ("step", 20),
                        ("tune", autotune.PACK_SHAPE), ("order", [4, 3, 2, 0, 1], 3), ("step", 20),
-                       ("tune", autotune.TAIL_SHAPE), ("order", [4, 0, 1, 2, 3], 1), ("step", 10)]
+                       ("tune", autotune.TAIL_SHAPE), ("order", [4, 0, 1, 2, 3], 1), ("step", 10),
+                       ("order", None, 0)]
     g = _Forest()
     autotune.step_with_tail(g, [7] * 8, (2, 1, 1, 8), sms=1, pack_per_sm=2, tail_per_sm=1)
     assert g.calls == [("tune", (2, 1, 1, 8)), ("step", 7)]
